@@ -1,0 +1,56 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws random numbers and shapes them into Gaussian random
+fields; it holds none of the pipeline's arithmetic (no shear/convergence
+relation, no wavelet filter).  The tests and the benchmark both take their
+inputs from here.
+
+Recipe (the paper analyses 1024 x 1024 pixel maps, Sec. 5.1, and gives no
+data set; a Gaussian random field stands in for its convergence maps):
+  kappa_hat(k) = |k|^(-alpha/2) (a + i b) / sqrt(2), a, b ~ N(0, 1) iid,
+  |k| in integer frequency units, kappa_hat(0) = 0;
+  kappa = Re IFFT2(kappa_hat), rescaled to the requested RMS (default 0.02);
+  shape noise: N(0, sigma^2) per pixel per shear component (default 0.1).
+The shear of a field is obtained by the caller through a forward
+Kaiser-Squires transform (the oracle's in tests, the library's on the GPU).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def grf_kappa(n: int, alpha: float = 2.0, rms: float = 0.02, seed: int = 1) -> np.ndarray:
+    """n x n float64 Gaussian random field with P(k) proportional to k^-alpha."""
+    rng = _rng(seed)
+    f = np.fft.fftfreq(n) * n
+    k = np.sqrt(f[None, :] ** 2 + f[:, None] ** 2)
+    amp = np.zeros_like(k)
+    amp[k > 0] = k[k > 0] ** (-alpha / 2.0)
+    a = rng.standard_normal((n, n))
+    b = rng.standard_normal((n, n))
+    field = np.real(np.fft.ifft2(amp * (a + 1j * b) / np.sqrt(2.0)))
+    field -= field.mean()
+    std = field.std()
+    return field * (rms / std) if std > 0 else field
+
+
+def shape_noise(n: int, sigma: float = 0.1, seed: int = 1) -> tuple[np.ndarray, np.ndarray]:
+    """Two n x n float64 maps of iid N(0, sigma^2) shape noise."""
+    rng = _rng(seed + 0x5EED)
+    return sigma * rng.standard_normal((n, n)), sigma * rng.standard_normal((n, n))
+
+
+def delta_kappa(n: int, amplitude: float = 1.0) -> np.ndarray:
+    """A null convergence map with one central delta (the Fig. 2 input)."""
+    k = np.zeros((n, n))
+    k[n // 2, n // 2] = amplitude
+    return k
+
+
+def white(shape, seed: int = 1, scale: float = 1.0) -> np.ndarray:
+    """iid N(0, scale^2) values (generic test input)."""
+    return scale * _rng(seed).standard_normal(shape)
