@@ -1,0 +1,394 @@
+"""Benchmark: fast aperture-mass maps on one GB300 (or N, one process each).
+
+Headline workload (the paper's image size, Sec. 5.1): a batch of 1024 x 1024
+fp32 shear maps -> Kaiser-Squires -> starlet J = 7 (bands theta = 2..64 px +
+smooth array), through fm_map_starlet.  Metric: Mpix*scales/s
+= n^2 * J * maps / s / 1e6 (J counts arrays including the smooth one).
+
+One JSON line on rank 0 with the headline, the roofline of the dominant
+kernel, the end-to-end number through the host-buffer entry point, clocks,
+the CPU oracle baseline, and side legs: the plain per-map FP64 form, the
+direct M_ap comparison path per aperture radius (GPU analogue of Fig. 4) and
+the batched noise maps (R realisations).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "starlet Map Mpix*scales/s, batched FP32 vs plain FP64 (<=1e-5 err); %HBM; p99 ms"
+UNIT = "Mpix*scales/s"
+L2_BYTES = 129 * 2 ** 20
+
+# Algorithmic HBM bytes per pixel of one launch, fp32 (x2 for fp64):
+# FFT passes read and write complex maps; the KS row passes read / write the
+# real maps; the fused starlet tile reads kappa once and writes f bands + c_f.
+ALGO_BYTES_PER_PX = {
+    "fft_rows_fwd": 8 + 8,
+    "fft_cols_ks": 8 + 8,
+    "fft_rows_inv": 8 + 4,
+    "starlet_row": 4 + 4,
+    "starlet_col": 4 + 4 + 4 + 4,
+}
+
+
+def starlet_tile_bytes_per_px(fuse):
+    return 4 + 4 * fuse + 4
+
+
+# ---------------------------------------------------------------------------
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, valid
+    only while the kernel source is unchanged (sha recorded at capture)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        parts = dict(kv.split("=", 1) for kv in line.split())
+        if parts.get("kernel") == kernel:
+            rec = parts
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1204_4293_gb300", "csrc", rec["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if sha != rec.get("sha"):
+        return None
+    return float(rec["bytes_per_px"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        win = [p for t, p in self.samples if t0 - 0.15 <= t <= t1 + 0.15]
+        if not win:  # timed region shorter than the sampling period: nearest sample
+            mid = 0.5 * (t0 + t1)
+            win = [min(self.samples, key=lambda s: abs(s[0] - mid))[1]]
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[0]) for p in win if num(p[0]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in win for i in range(4) if p[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(win[0][1]),
+                "power_w_max": max((num(p[2]) or 0) for p in win), "reasons": reasons, "samples": len(win)}
+
+
+# ---------------------------------------------------------------------------
+def make_inputs(fm, torch, n, batch, seed, dtype):
+    """Seeded GRF shear maps (P(k) ~ k^-2, rms 0.02) + N(0, 0.1^2) shape noise,
+    built on the device: GRF on the host, forward KS through the library."""
+    from paper_1204_4293_gb300 import synth
+    distinct = min(batch, 8)
+    kap = np.stack([synth.grf_kappa(n, seed=seed + i) for i in range(distinct)]).astype(np.float32)
+    kd = torch.from_numpy(kap).cuda()
+    g1, g2 = fm.fm_ks_forward(kd)
+    reps = (batch + distinct - 1) // distinct
+    g1 = g1.repeat(reps, 1, 1)[:batch].contiguous()
+    g2 = g2.repeat(reps, 1, 1)[:batch].contiguous()
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    g1 += 0.1 * torch.randn(g1.shape, generator=gen, device="cuda")
+    g2 += 0.1 * torch.randn(g2.shape, generator=gen, device="cuda")
+    return g1.to(dtype).contiguous(), g2.to(dtype).contiguous()
+
+
+def cuda_time(torch, fn, reps):
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def cpu_oracle_baseline(n, J, budget_s=12.0):
+    """The FP64 oracle (KS + starlet) on the host cores, one thread, timed on
+    whole 1024^2 maps until ~budget_s of CPU work."""
+    import oracle
+    from paper_1204_4293_gb300 import synth
+    oracle.build()
+    kap = synth.grf_kappa(n, seed=2)
+    g1, g2 = oracle.ks_forward(kap)
+    maps = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.map_starlet(g1, g2, J)
+        maps += 1
+        if time.perf_counter() - t0 > budget_s or maps >= 8:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n * n * J * maps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{maps} map(s) of {n}x{n}, J={J}, KS + starlet in FP64, single thread, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle as the comparison arm."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1204_4293_gb300 import synth
+    oracle.build()
+    n, J = args.n, args.J
+    kap = synth.grf_kappa(n, seed=2)
+    g1, g2 = oracle.ks_forward(kap)
+    for _ in range(args.warmup):
+        oracle.map_starlet(g1, g2, J)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.map_starlet(g1, g2, J)
+    dt = time.perf_counter() - t0
+    value = n * n * J * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"one {n}x{n} shear map per step (bounded sample of the batched workload), "
+                                   f"KS + starlet J={J}", "n": n, "J": J, "maps_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed map(s) of {n}x{n}, single thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def side_legs(fm, torch, n, J, g1, g2):
+    """Plain FP64 form, direct M_ap per radius, batched noise maps."""
+    out = {}
+    # plain form: one map per launch, FP64, one scale per pass (no fusion)
+    p1 = g1[0].double().contiguous()
+    p2 = g2[0].double().contiguous()
+    pyr64 = torch.empty(J, n, n, dtype=torch.float64, device="cuda")
+    fn = lambda: fm.fm_map_starlet(p1, p2, J, fuse_depth=-1, out=pyr64)  # noqa: E731
+    fn()
+    ms = cuda_time(torch, fn, 5)
+    out["plain_fp64"] = {"value": n * n * J / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_map": ms,
+                         "form": "one map per call, FP64, unfused (one starlet scale per pass)"}
+    # direct M_ap vs starlet per aperture radius (Fig. 4 analogue), fp32, one map
+    s1, s2 = g1[0].contiguous(), g2[0].contiguous()
+    kap, _ = fm.fm_ks_invert(s1.unsqueeze(0), s2.unsqueeze(0))
+    kap = kap[0].contiguous()
+    rows = []
+    for j in range(1, J):
+        theta = float(2 ** j)
+        Jj = j + 1
+        t_st = cuda_time(torch, lambda: fm.fm_starlet_forward(kap, Jj), 5)
+        t_ks = cuda_time(torch, lambda: fm.fm_map_starlet(s1, s2, Jj), 5)
+        reps = 3 if theta >= 32 else 5
+        t_s98 = cuda_time(torch, lambda: fm.fm_map_direct(s1, s2, fm.FM_FILTER_S98, theta), reps)
+        t_stq = cuda_time(torch, lambda: fm.fm_map_direct(s1, s2, fm.FM_FILTER_STARLET, theta), reps)
+        rows.append({"theta_px": theta, "J": Jj, "starlet_ms": t_st, "ks_starlet_ms": t_ks,
+                     "map_s98_cut_theta_ms": t_s98, "map_starletQ_cut_2theta_ms": t_stq,
+                     "speedup_vs_s98": t_s98 / t_st, "speedup_ks_starlet_vs_s98": t_s98 / t_ks})
+    out["direct_map"] = rows
+    # batched noise maps: R realisations of KS + starlet with FP64 accumulation
+    R = 1000
+    fm.fm_map_noise(s1, s2, J, 8, seed=3)
+    t_noise = cuda_time(torch, lambda: fm.fm_map_noise(s1, s2, J, R, seed=3), 1)
+    out["noise"] = {"R": R, "ms": t_noise, "value": n * n * J * R / (t_noise * 1e-3) / 1e6, "unit": UNIT}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--J", type=int, default=7)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--no-side", action="store_true", help="skip the side legs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1204_4293_gb300 import fastmap as fm
+
+    n, J, B = args.n, args.J, args.batch
+    g1, g2 = make_inputs(fm, torch, n, B, seed=1000 * (rank + 1), dtype=torch.float32)
+    pyr = torch.empty(B, J, n, n, dtype=torch.float32, device="cuda")
+    step = lambda: fm.fm_map_starlet(g1, g2, J, out=pyr)  # noqa: E731
+
+    # which kernel dominates: one profiled pass per kernel kind, untimed
+    kinds = ["fft_rows_fwd", "fft_cols_ks", "fft_rows_inv", "starlet_tile", "starlet_row", "starlet_col"]
+    per_kind = {}
+    step()
+    for k in kinds:
+        fm.fm_profile_select(k)
+        step()
+        ms, cnt = fm.fm_profile_read()
+        per_kind[k] = (ms, cnt)
+    fm.fm_profile_select(0)
+    dom = max(per_kind, key=lambda k: per_kind[k][0])
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    launches0 = fm.fm_launch_count()
+    fm.fm_profile_select(dom)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record(s)
+    for _ in range(args.steps):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if world > 1:
+        dist.barrier()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    dom_ms, dom_cnt = fm.fm_profile_read()
+    fm.fm_profile_select(0)
+    launches = fm.fm_launch_count() - launches0
+    clocks = sampler.summary(t0, t1) if sampler else None
+
+    t = torch.tensor([ms_step], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    units = n * n * J * B * world  # whole-job pixel-scales per step
+    value = units / (ms_max * 1e-3) / 1e6
+
+    # end to end through the host-buffer entry point (pinned buffers)
+    h1 = g1.cpu().pin_memory()
+    h2 = g2.cpu().pin_memory()
+    hout = torch.empty(B, J, n, n, dtype=torch.float32).pin_memory()
+    e2e_step = lambda: fm.fm_map_starlet_host(h1, h2, J, hout)  # noqa: E731
+    e2e_step()
+    e2e_steps = max(3, min(args.steps, 20))
+    e2e_ms = cuda_time(torch, e2e_step, e2e_steps)
+    te = torch.tensor([e2e_ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = units / (float(te.item()) * 1e-3) / 1e6
+
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_side:
+        extras = side_legs(fm, torch, n, J, g1, g2)
+    if sampler:
+        sampler.stop()
+
+    if rank == 0:
+        peak, peak_src = load_peaks()
+        px_per_launch = n * n * B
+        bpp = starlet_tile_bytes_per_px(3) if dom == "starlet_tile" else ALGO_BYTES_PER_PX[dom]
+        dom_avg_ms = dom_ms / max(dom_cnt, 1)
+        achieved = bpp * px_per_launch / (dom_avg_ms * 1e-3) / 1e9
+        trf = ncu_traffic(dom)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{B} x {n}x{n} fp32 shear maps per GPU per step -> Kaiser-Squires -> "
+                                   f"starlet J={J} (theta=2..{2 ** (J - 1)} px + smooth)",
+                       "n": n, "J": J, "maps_per_gpu": B, "parallelism": f"replicas x{world} (maps sharded)",
+                       "l2": f"inputs larger than L2: {2 * B * n * n * 4 / 2**20:.0f} MB shear in + "
+                             f"{B * J * n * n * 4 / 2**20:.0f} MB pyramid out per step"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": f"hbm_gbs ({peak_src})",
+                         "traffic": trf * px_per_launch if trf else None,
+                         "algorithmic_bytes_per_launch": bpp * px_per_launch, "avg_launch_ms": dom_avg_ms,
+                         "launches_timed": dom_cnt},
+            "kernel_breakdown_ms": {k: v[0] for k, v in per_kind.items()},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * B * n * n * 4,
+                    "d2h_bytes_per_step": B * J * n * n * 4, "ms_per_step": float(te.item()),
+                    "api": "fm_map_starlet_host (pinned host buffers)"},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        line.update(extras)
+        if "plain_fp64" in extras:
+            line["batched_fp32_over_plain_fp64"] = value / extras["plain_fp64"]["value"]
+        if not args.no_cpu and world == 1:
+            line["cpu_baseline"] = cpu_oracle_baseline(n, J)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * fastmap.h -- C ABI of libfastmap, GB300 (sm_103a) fast aperture-mass maps.
+ *
+ * Implements the pipeline of Leonard, Pires & Starck, "Fast Calculation of
+ * the Weak Lensing Aperture Mass Statistic" (MNRAS 2012):
+ *   shear (gamma1, gamma2) --Kaiser-Squires in Fourier space (Sec. 4.4)-->
+ *   convergence kappa --starlet / a trous B3-spline transform (Sec. 3,
+ *   Sec. 4.2)--> aperture-mass maps w_j = c_{j-1} - c_j at theta = 2^j px;
+ *   the brute-force direct M_ap of eq. shearmap (Sec. 2.1, Sec. 5.1) as the
+ *   comparison path; and noise maps from randomly rotated shear (Sec. 1).
+ *
+ * Conventions shared by every entry point
+ *   - Maps are square n x n, row-major, element (y, x) at [y*n + x]; x pairs
+ *     with frequency k1, y with k2; a batch of maps is contiguous (map b at
+ *     offset b*n*n).  Integer frequency of index i: i for i < n/2, else i - n.
+ *   - A starlet pyramid holds J arrays of n*n per map: w_1 .. w_{J-1}, then
+ *     the smooth array left after J-1 bands (the paper's c_J), so a batch of
+ *     pyramids is [batch][J][n][n].  J counts arrays including the smooth one
+ *     (Sec. 5.1); band j has aperture radius theta = 2^j pixels (Sec. 3).
+ *   - Element type: float when cfg->precision == FM_F32 (default), double when
+ *     FM_F64.  Noise variances are always double.
+ *   - Data pointers are DEVICE pointers owned by the caller, except where an
+ *     entry point says HOST.  The library keeps no reference after a call's
+ *     work completes.  It owns only its scratch (stream-ordered allocations
+ *     freed on the same stream) and small per-device tables (FFT twiddles),
+ *     kept until process exit.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Every compute entry point is asynchronous on that stream: it
+ *     returns once the work is queued.  The first call for a given n and
+ *     precision builds a table with a synchronous copy, so make it before
+ *     any CUDA-graph capture.
+ *   - Return value: FM_OK (0) or a negative FM_E* code; nothing aborts and no
+ *     C++ exception crosses the ABI.  fm_last_error() gives a message.
+ *   - Validity: n >= 2^J and J >= 2 (Sec. 5.1: N >= 2^J); FFT-based entry
+ *     points also need n a power of two, 4 <= n <= 8192.
+ */
+#ifndef FASTMAP_H
+#define FASTMAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FM_OK 0
+#define FM_PENDING 1      /* serving: request not finished yet */
+#define FM_EINVAL (-1)    /* bad size, J, filter, pointer or config */
+#define FM_ENOMEM (-2)    /* device scratch allocation failed */
+#define FM_EBUDGET (-3)   /* serving: request larger than the memory budget */
+#define FM_ETIMEOUT (-4)  /* a bounded device wait gave up */
+#define FM_ECUDA (-5)     /* a CUDA runtime call or kernel launch failed */
+#define FM_ENOTFOUND (-6) /* serving: unknown ticket */
+#define FM_EBUSY (-7)     /* serving: queue full */
+
+/* ---- configuration ----------------------------------------------------- */
+#define FM_F32 0
+#define FM_F64 1
+#define FM_MIRROR 0   /* whole-sample symmetric boundary (the paper states none) */
+#define FM_PERIODIC 1
+
+/* Direct M_ap filters (Sec. 4): starlet-shaped Q(eta)/theta^2 (default cut
+ * 2 theta), S98 polynomial of order ell (eq. sch, cut theta), Gaussian of
+ * eq. mexhat with A = 1 and b = 1/2 (JBJ04) or b = 4 (vW98), cut 5 theta. */
+#define FM_FILTER_STARLET 0
+#define FM_FILTER_S98 1
+#define FM_FILTER_JBJ04 2
+#define FM_FILTER_VW98 3
+
+typedef struct {
+    int precision;  /* FM_F32 (0) or FM_F64 (1) */
+    int boundary;   /* starlet boundary: FM_MIRROR (0) or FM_PERIODIC (1) */
+    int accum;      /* noise accumulators: 0 = FP64 (the only mode) */
+    int fuse_depth; /* starlet scales done by the fused 2-D tile kernel:
+                       0 = automatic, k > 0 = scales 1..k, -1 = none (the
+                       plain one-scale-per-pass form) */
+    int tile;       /* 0 = automatic; reserved for tuning */
+} fm_config;
+
+/* ---- Kaiser-Squires (Sec. 4.4) ---------------------------------------------
+ * Forward: gamma = IFFT(D FFT kappa); inverse: kappa = IFFT(conj(D) FFT gamma),
+ * D(k) = (k1 + i k2)^2 / |k|^2, D(0) = 0 (standard KS; the paper names the
+ * Fourier-space inversion without printing D).
+ * fm_ks_invert: g1, g2 in [batch][n][n]; kappa_E (real part) out, kappa_B
+ * (imaginary part, the B-mode) out or NULL.  fm_ks_forward: kappa in, g1, g2
+ * out.  Scratch: batch*n*n complex. */
+int fm_ks_invert(const void *g1, const void *g2, void *kappa_E, void *kappa_B, int n, int batch,
+                 const fm_config *cfg, void *stream);
+int fm_ks_forward(const void *kappa, void *g1, void *g2, int n, int batch, const fm_config *cfg, void *stream);
+
+/* ---- starlet transform (Sec. 3, Sec. 4.2) -----------------------------------
+ * kappa [batch][n][n] in, pyramid [batch][J][n][n] out (layout above).
+ * Scale j filters rows then columns with h = [1,4,6,4,1]/16 at spacing
+ * 2^(j-1) (the B3 two-scale filter) and stores w_j = c_{j-1} - c_j.
+ * n need not be a power of two here (n >= 2^J).  kappa and pyramid must not
+ * overlap.  Scratch: up to 2*batch*n*n elements. */
+int fm_starlet_forward(const void *kappa, void *pyramid, int n, int J, int batch, const fm_config *cfg,
+                       void *stream);
+
+/* KS inversion then the starlet of kappa_E: the aperture-mass maps of every
+ * band from shear in one call (the paper's fast method end to end). */
+int fm_map_starlet(const void *g1, const void *g2, void *pyramid, int n, int J, int batch, const fm_config *cfg,
+                   void *stream);
+
+/* Same as fm_map_starlet with HOST buffers (pinned host memory is fastest):
+ * copies g1, g2 in, computes, copies the pyramid back, all queued on
+ * `stream`; the host buffers must stay valid until the stream reaches that
+ * point.  Device buffers are stream-ordered scratch. */
+int fm_map_starlet_host(const void *g1_host, const void *g2_host, void *pyramid_host, int n, int J, int batch,
+                        const fm_config *cfg, void *stream);
+
+/* ---- direct aperture mass, eq. shearmap (Sec. 2.1), brute force (Sec. 5.1)
+ * map(x) = sum over integer offsets d, 0 < |d| <= R, of Q(|d|) gamma_t(x+d),
+ * gamma_t = -(gamma1 cos 2phi + gamma2 sin 2phi), phi the angle of d; pixels
+ * outside the field add nothing.  R = cut_over_theta * theta_px, or the
+ * filter's default cut when cut_over_theta <= 0.  ell is the S98 order.
+ * One n x n map (n >= 1, any size).  Cost O(n^2 R^2). */
+int fm_map_direct(const void *g1, const void *g2, void *map, int n, int filter, double theta_px, int ell,
+                  double cut_over_theta, const fm_config *cfg, void *stream);
+
+/* ---- noise maps by randomised shear (Sec. 1, Sec. 5.1) ------------------------
+ * Realisation r rotates every pixel's shear by 2 alpha, alpha = pi u with u
+ * the top 24 bits (times 2^-24) of SplitMix64 at counter (r*n + y)*n + x from
+ * state `seed`; then KS + starlet.  var_out [(J-1)][n][n] (double) receives
+ * the unbiased variance of each band over the R realisations (R >= 2);
+ * snr_out (element type, same shape, or NULL) receives w_j(data)/sigma_j.
+ * One map; n a power of two.  Scratch ~ (2 (J-1) * 8 + 40 * chunk) bytes per
+ * pixel. */
+int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
+                 const fm_config *cfg, void *stream);
+
+/* ---- serving: continuous batching of map requests -------------------------- */
+typedef struct {
+    int n, J, R;          /* R = 0: pyramid only; R >= 2: also noise variance */
+    uint64_t seed;
+    int precision;        /* FM_F32 or FM_F64 */
+    const void *g1, *g2;  /* device input, borrowed until the request finishes */
+    void *out_pyramid;    /* device [J][n][n], element type */
+    double *out_var;      /* device [(J-1)][n][n] or NULL (needs R >= 2) */
+} fm_request;
+
+typedef struct {
+    int status;           /* FM_PENDING, FM_OK or a negative code */
+    int64_t t_submit_ns, t_admit_ns, t_done_ns; /* steady-clock times */
+} fm_result;
+
+/* A server owns a host thread, max_slots CUDA streams and the scratch of the
+ * requests it runs.  A request is admitted when a slot is free and its
+ * scratch fits in mem_budget_bytes minus the scratch of running requests;
+ * requests run concurrently on their own streams.  submit copies the
+ * request descriptor (device buffers are borrowed) and returns a ticket. */
+int fm_serve_create(size_t mem_budget_bytes, int max_slots, void **server);
+int fm_serve_submit(void *server, const fm_request *req, uint64_t *ticket);
+int fm_serve_poll(void *server, uint64_t ticket, fm_result *result);
+int fm_serve_wait(void *server, uint64_t ticket, fm_result *result, double timeout_s);
+int fm_serve_destroy(void *server);
+size_t fm_request_scratch_bytes(const fm_request *req);
+
+/* ---- diagnostics ------------------------------------------------------------- */
+const char *fm_status_string(int status);
+const char *fm_last_error(void);   /* message of the calling thread's last error */
+int64_t fm_launch_count(void);     /* kernels launched by this library so far */
+
+/* Kernel ids for fm_profile_select. */
+#define FM_K_FFT_ROWS_FWD 1
+#define FM_K_FFT_COLS_KS 2
+#define FM_K_FFT_ROWS_INV 3
+#define FM_K_STARLET_TILE 4
+#define FM_K_STARLET_ROW 5
+#define FM_K_STARLET_COL 6
+#define FM_K_MAP_DIRECT 7
+#define FM_K_NOISE_FINAL 8
+
+/* Bracket every later launch of kernel `kid` (0 = none) with CUDA events on
+ * its launch stream; fm_profile_read synchronises those events and returns
+ * the summed device time (ms) and the launch count since the selection. */
+int fm_profile_select(int kid);
+int fm_profile_read(double *total_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTMAP_H */

@@ -1,0 +1,435 @@
+// api.cu -- the C ABI of libfastmap (declared in include/fastmap.h): argument
+// validation, per-device tables, stream-ordered scratch, dispatch to the
+// kernels, the noise-map driver, diagnostics and profiling hooks.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fm {
+
+// ---- errors -----------------------------------------------------------------
+static thread_local std::string t_last_error;
+
+void set_error(const std::string &msg) { t_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // allocation failures are not sticky; clear them
+        return FM_ENOMEM;
+    }
+    return FM_ECUDA;
+}
+
+static int einval(const std::string &msg)
+{
+    set_error(msg);
+    return FM_EINVAL;
+}
+
+// ---- launch accounting and profiling ------------------------------------------
+std::atomic<int64_t> g_launches{0};
+
+namespace {
+struct Prof {
+    std::mutex mu;
+    int kid = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pairs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t pending = nullptr;
+    cudaEvent_t get()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+Prof g_prof;
+std::atomic<int> g_prof_kid{0};
+}  // namespace
+
+void prof_before(int kid, cudaStream_t s)
+{
+    if (kid == 0 || g_prof_kid.load(std::memory_order_relaxed) != kid) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.pending = g_prof.get();
+    cudaEventRecord(g_prof.pending, s);
+}
+
+void prof_after(int kid, cudaStream_t s)
+{
+    if (kid == 0 || g_prof_kid.load(std::memory_order_relaxed) != kid) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (!g_prof.pending) return;
+    cudaEvent_t e = g_prof.get();
+    cudaEventRecord(e, s);
+    g_prof.pairs.emplace_back(g_prof.pending, e);
+    g_prof.pending = nullptr;
+}
+
+// ---- twiddle tables ------------------------------------------------------------
+namespace {
+std::mutex g_tw_mu;
+std::unordered_map<uint64_t, void *> g_tw;  // key: device, precision, n
+}  // namespace
+
+const void *twiddles(int n, int precision, cudaStream_t s, int *status)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        *status = cuda_fail(e, "cudaGetDevice");
+        return nullptr;
+    }
+    const uint64_t key = ((uint64_t)dev << 40) | ((uint64_t)precision << 32) | (uint64_t)n;
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    auto it = g_tw.find(key);
+    if (it != g_tw.end()) return it->second;
+    // exp(-2 pi i t / n) in FP64 on the host, rounded once to the element type
+    const size_t esz = precision == FM_F64 ? 16 : 8;
+    std::vector<unsigned char> host((size_t)n * esz);
+    for (int t = 0; t < n; ++t) {
+        const double ang = -2.0 * M_PI * (double)t / (double)n;
+        const double c = cos(ang), sn = sin(ang);
+        if (precision == FM_F64) {
+            double v[2] = {c, sn};
+            memcpy(&host[(size_t)t * esz], v, esz);
+        } else {
+            float v[2] = {(float)c, (float)sn};
+            memcpy(&host[(size_t)t * esz], v, esz);
+        }
+    }
+    void *d = nullptr;
+    e = cudaMalloc(&d, host.size());
+    if (e == cudaSuccess) e = cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (d) cudaFree(d);
+        *status = cuda_fail(e, "twiddle table");
+        return nullptr;
+    }
+    (void)s;
+    g_tw[key] = d;
+    return d;
+}
+
+// ---- scratch -------------------------------------------------------------------
+int scratch_alloc(Scratch &sc, size_t bytes, cudaStream_t s)
+{
+    sc.s = s;
+    if (bytes == 0) return FM_OK;
+    static std::once_flag pool_once;
+    std::call_once(pool_once, [] {
+        // keep freed stream-ordered memory in the pool instead of returning it
+        // to the driver after every call (a setting of this process only)
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+    cudaError_t e = cudaMallocAsync(&sc.p, bytes, s);
+    if (e != cudaSuccess) {
+        sc.p = nullptr;
+        return cuda_fail(e, "cudaMallocAsync (scratch)");
+    }
+    return FM_OK;
+}
+
+static fm_config cfg_or_default(const fm_config *c)
+{
+    fm_config d;
+    memset(&d, 0, sizeof(d));
+    if (c) d = *c;
+    return d;
+}
+
+static int check_cfg(const fm_config &c)
+{
+    if (c.precision != FM_F32 && c.precision != FM_F64) return einval("precision must be FM_F32 or FM_F64");
+    if (c.boundary != FM_MIRROR && c.boundary != FM_PERIODIC) return einval("boundary must be FM_MIRROR or FM_PERIODIC");
+    if (c.accum != 0) return einval("accum must be 0 (FP64 accumulation)");
+    if (c.fuse_depth < -1 || c.fuse_depth > 8) return einval("fuse_depth out of range [-1, 8]");
+    return FM_OK;
+}
+
+static size_t esize(const fm_config &c) { return c.precision == FM_F64 ? 8 : 4; }
+
+static int check_fft_n(int n)
+{
+    if (n < 4 || n > 8192 || !is_pow2(n)) return einval("n must be a power of two in [4, 8192]");
+    return FM_OK;
+}
+
+static int check_J(int n, int J)
+{
+    if (J < 2 || J > 20) return einval("J must be in [2, 20]");
+    if ((long)n < (1L << J)) return einval("n must be >= 2^J (N >= 2^J)");
+    return FM_OK;
+}
+
+// realisations per noise chunk: keep a chunk's working set (~20 B/px each
+// in fp32) near 64 MB so it stays in L2
+static int noise_chunk(int n, int R, size_t es)
+{
+    const long nn = (long)n * n;
+    long chunk = (64L << 20) / (nn * 5 * (long)es);
+    chunk = chunk < 1 ? 1 : (chunk > 16 ? 16 : chunk);
+    return (int)(chunk > R ? R : chunk);
+}
+
+size_t map_starlet_scratch_bytes(int n, int J, int batch, const fm_config &cfg)
+{
+    const size_t es = esize(cfg), nn = (size_t)n * n;
+    return (size_t)batch * nn * 3 * es + starlet_scratch_elems(n, J, batch, cfg) * es + 3 * 256;
+}
+
+size_t noise_scratch_bytes(int n, int J, int R, const fm_config &cfg, bool with_snr)
+{
+    const size_t es = esize(cfg), nn = (size_t)n * n;
+    const int chunk = noise_chunk(n, R, es);
+    size_t b = 2 * (size_t)(J - 1) * nn * sizeof(double) + (size_t)chunk * nn * 3 * es +
+               starlet_scratch_elems(n, J, chunk, cfg) * es + 5 * 256;
+    if (with_snr) b += (size_t)J * nn * es;
+    return b;
+}
+
+}  // namespace fm
+
+using namespace fm;
+
+// ---- entry points ----------------------------------------------------------------
+extern "C" {
+
+int fm_ks_invert(const void *g1, const void *g2, void *kappa_E, void *kappa_B, int n, int batch, const fm_config *cfgp,
+                 void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if ((st = check_fft_n(n))) return st;
+    if (batch < 1) return einval("batch must be >= 1");
+    if (!g1 || !g2 || !kappa_E) return einval("null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch work;
+    const size_t bytes = (size_t)batch * n * n * 2 * esize(cfg);
+    if ((st = scratch_alloc(work, bytes, s))) return st;
+    return launch_ks(g1, g2, (long)n * n, kappa_E, kappa_B, work.p, n, batch, cfg.precision, false, 0, 0, false, s);
+}
+
+int fm_ks_forward(const void *kappa, void *g1, void *g2, int n, int batch, const fm_config *cfgp, void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if ((st = check_fft_n(n))) return st;
+    if (batch < 1) return einval("batch must be >= 1");
+    if (!kappa || !g1 || !g2) return einval("null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch work;
+    if ((st = scratch_alloc(work, (size_t)batch * n * n * 2 * esize(cfg), s))) return st;
+    return launch_ks(kappa, nullptr, (long)n * n, g1, g2, work.p, n, batch, cfg.precision, true, 0, 0, false, s);
+}
+
+int fm_starlet_forward(const void *kappa, void *pyramid, int n, int J, int batch, const fm_config *cfgp, void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if (n < 1) return einval("n must be >= 1");
+    if ((st = check_J(n, J))) return st;
+    if (batch < 1) return einval("batch must be >= 1");
+    if (!kappa || !pyramid) return einval("null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc;
+    if ((st = scratch_alloc(sc, starlet_scratch_elems(n, J, batch, cfg) * esize(cfg), s))) return st;
+    return launch_starlet(kappa, pyramid, (long)J * n * n, n, J, batch, cfg, sc.p, nullptr, nullptr, s);
+}
+
+// KS then starlet of kappa_E; kappa_E and the FFT work buffer are scratch.
+static int map_starlet_dev(const void *g1, const void *g2, void *pyramid, int n, int J, int batch,
+                           const fm_config &cfg, cudaStream_t s)
+{
+    const long nn = (long)n * n;
+    const size_t es = esize(cfg);
+    Scratch wsc, ksc, ssc;
+    int st;
+    if ((st = scratch_alloc(wsc, (size_t)batch * nn * 2 * es, s))) return st;
+    if ((st = scratch_alloc(ksc, (size_t)batch * nn * es, s))) return st;
+    if ((st = scratch_alloc(ssc, starlet_scratch_elems(n, J, batch, cfg) * es, s))) return st;
+    if ((st = launch_ks(g1, g2, nn, ksc.p, nullptr, wsc.p, n, batch, cfg.precision, false, 0, 0, false, s))) return st;
+    return launch_starlet(ksc.p, pyramid, (long)J * nn, n, J, batch, cfg, ssc.p, nullptr, nullptr, s);
+}
+
+}  // extern "C"
+
+namespace fm {
+int map_starlet_run(const void *g1, const void *g2, void *pyramid, int n, int J, int batch, const fm_config &cfg,
+                    cudaStream_t s)
+{
+    return map_starlet_dev(g1, g2, pyramid, n, J, batch, cfg, s);
+}
+}  // namespace fm
+
+extern "C" {
+
+int fm_map_starlet(const void *g1, const void *g2, void *pyramid, int n, int J, int batch, const fm_config *cfgp,
+                   void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if ((st = check_fft_n(n))) return st;
+    if ((st = check_J(n, J))) return st;
+    if (batch < 1) return einval("batch must be >= 1");
+    if (!g1 || !g2 || !pyramid) return einval("null pointer");
+    return map_starlet_dev(g1, g2, pyramid, n, J, batch, cfg, (cudaStream_t)stream);
+}
+
+int fm_map_starlet_host(const void *g1_host, const void *g2_host, void *pyramid_host, int n, int J, int batch,
+                        const fm_config *cfgp, void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if ((st = check_fft_n(n))) return st;
+    if ((st = check_J(n, J))) return st;
+    if (batch < 1) return einval("batch must be >= 1");
+    if (!g1_host || !g2_host || !pyramid_host) return einval("null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t map_bytes = (size_t)batch * n * n * esize(cfg);
+    Scratch gin, pyr;
+    if ((st = scratch_alloc(gin, 2 * map_bytes, s))) return st;
+    if ((st = scratch_alloc(pyr, (size_t)J * map_bytes, s))) return st;
+    char *d1 = static_cast<char *>(gin.p);
+    FM_CUDA_TRY(cudaMemcpyAsync(d1, g1_host, map_bytes, cudaMemcpyHostToDevice, s));
+    FM_CUDA_TRY(cudaMemcpyAsync(d1 + map_bytes, g2_host, map_bytes, cudaMemcpyHostToDevice, s));
+    if ((st = map_starlet_dev(d1, d1 + map_bytes, pyr.p, n, J, batch, cfg, s))) return st;
+    FM_CUDA_TRY(cudaMemcpyAsync(pyramid_host, pyr.p, (size_t)J * map_bytes, cudaMemcpyDeviceToHost, s));
+    return FM_OK;
+}
+
+int fm_map_direct(const void *g1, const void *g2, void *map, int n, int filter, double theta_px, int ell,
+                  double cut_over_theta, const fm_config *cfgp, void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if (n < 1 || n > 65536) return einval("n must be in [1, 65536]");
+    if (filter < FM_FILTER_STARLET || filter > FM_FILTER_VW98) return einval("unknown filter");
+    if (!(theta_px > 0) || theta_px > 4096) return einval("theta_px must be in (0, 4096]");
+    if (filter == FM_FILTER_S98 && (ell < 0 || ell > 64)) return einval("ell must be in [0, 64]");
+    const double cut = cut_over_theta > 0 ? cut_over_theta : 0.0;
+    const double R = (cut > 0 ? cut : (filter == FM_FILTER_STARLET ? 2.0 : filter == FM_FILTER_S98 ? 1.0 : 5.0)) *
+                     theta_px;
+    if (R > 2048) return einval("cut radius above 2048 px");
+    if (!g1 || !g2 || !map) return einval("null pointer");
+    return launch_map_direct(g1, g2, map, n, filter, theta_px, ell, cut, cfg.precision, (cudaStream_t)stream);
+}
+
+// Noise maps (Sec. 1): one unrotated pass for w_j(data), then R rotated
+// realisations in chunks, each chunk a batch through KS and the starlet with
+// the bands accumulated into FP64 S1, S2; then the finalize kernel.
+int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
+                 const fm_config *cfgp, void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if ((st = check_fft_n(n))) return st;
+    if ((st = check_J(n, J))) return st;
+    if (R < 2) return einval("R must be >= 2");
+    if (!g1 || !g2 || !var_out) return einval("null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long nn = (long)n * n;
+    const size_t es = esize(cfg);
+    const long nb = (long)(J - 1) * nn;
+    const int chunk = noise_chunk(n, R, es);
+    Scratch acc, work, kap, ssc, pyr;
+    if ((st = scratch_alloc(acc, (size_t)2 * nb * sizeof(double), s))) return st;
+    double *s1 = static_cast<double *>(acc.p);
+    double *s2 = s1 + nb;
+    FM_CUDA_TRY(cudaMemsetAsync(s1, 0, (size_t)2 * nb * sizeof(double), s));
+    if ((st = scratch_alloc(work, (size_t)chunk * nn * 2 * es, s))) return st;
+    if ((st = scratch_alloc(kap, (size_t)chunk * nn * es, s))) return st;
+    if ((st = scratch_alloc(ssc, starlet_scratch_elems(n, J, chunk, cfg) * es, s))) return st;
+    if (snr_out) {
+        if ((st = scratch_alloc(pyr, (size_t)J * nn * es, s))) return st;
+        if ((st = launch_ks(g1, g2, nn, kap.p, nullptr, work.p, n, 1, cfg.precision, false, 0, 0, false, s)))
+            return st;
+        if ((st = launch_starlet(kap.p, pyr.p, (long)J * nn, n, J, 1, cfg, ssc.p, nullptr, nullptr, s))) return st;
+    }
+    for (int r0 = 0; r0 < R; r0 += chunk) {
+        const int b = R - r0 < chunk ? R - r0 : chunk;
+        // every batch entry reads the same input map (batch stride 0) and
+        // rotates it with its own realisation index r0 + b
+        if ((st = launch_ks(g1, g2, 0, kap.p, nullptr, work.p, n, b, cfg.precision, false, seed, r0, true, s)))
+            return st;
+        if ((st = launch_starlet(kap.p, nullptr, 0, n, J, b, cfg, ssc.p, s1, s2, s))) return st;
+    }
+    return launch_noise_finalize(s1, s2, pyr.p, var_out, snr_out, nb, R, cfg.precision, s);
+}
+
+const char *fm_status_string(int status)
+{
+    switch (status) {
+    case FM_OK: return "ok";
+    case FM_PENDING: return "pending";
+    case FM_EINVAL: return "invalid argument";
+    case FM_ENOMEM: return "out of device memory";
+    case FM_EBUDGET: return "request exceeds the memory budget";
+    case FM_ETIMEOUT: return "timed out";
+    case FM_ECUDA: return "CUDA error";
+    case FM_ENOTFOUND: return "unknown ticket";
+    case FM_EBUSY: return "queue full";
+    }
+    return "unknown status";
+}
+
+const char *fm_last_error(void) { return t_last_error.c_str(); }
+
+int64_t fm_launch_count(void) { return g_launches.load(); }
+
+int fm_profile_select(int kid)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (auto &p : g_prof.pairs) {
+        g_prof.pool.push_back(p.first);
+        g_prof.pool.push_back(p.second);
+    }
+    g_prof.pairs.clear();
+    g_prof.pending = nullptr;
+    g_prof_kid.store(kid);
+    return FM_OK;
+}
+
+int fm_profile_read(double *total_ms, int64_t *launches)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    double tot = 0;
+    for (auto &p : g_prof.pairs) {
+        cudaError_t e = cudaEventSynchronize(p.second);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float ms = 0;
+        e = cudaEventElapsedTime(&ms, p.first, p.second);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = (int64_t)g_prof.pairs.size();
+    return FM_OK;
+}
+
+}  // extern "C"

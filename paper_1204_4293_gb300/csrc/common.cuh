@@ -1,0 +1,122 @@
+// common.cuh -- shared device/host helpers of libfastmap (CUDA, sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "../../include/fastmap.h"
+
+namespace fm {
+
+// ---- error reporting --------------------------------------------------------
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define FM_CUDA_TRY(call)                                  \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return fm::cuda_fail(e_, #call); \
+    } while (0)
+
+#define FM_CHECK_LAUNCH(name)                                        \
+    do {                                                             \
+        cudaError_t e_ = cudaGetLastError();                         \
+        if (e_ != cudaSuccess) return fm::cuda_fail(e_, name);       \
+    } while (0)
+
+// ---- launch accounting and optional per-kernel event timing -----------------
+extern std::atomic<int64_t> g_launches;
+void prof_before(int kid, cudaStream_t s);
+void prof_after(int kid, cudaStream_t s);
+
+// Launch helper: counts the launch, brackets it with profiling events when
+// that kernel id is selected, and checks the launch status.
+#define FM_LAUNCH(kid, kernel, grid, block, smem, stream, ...)           \
+    do {                                                                 \
+        fm::prof_before(kid, stream);                                    \
+        kernel<<<grid, block, smem, stream>>>(__VA_ARGS__);              \
+        fm::g_launches.fetch_add(1, std::memory_order_relaxed);          \
+        FM_CHECK_LAUNCH(#kernel);                                        \
+        fm::prof_after(kid, stream);                                     \
+    } while (0)
+
+// ---- complex helpers ----------------------------------------------------------
+template <typename T> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename T> using cplx_t = typename cplx<T>::type;
+
+template <typename V> __host__ __device__ __forceinline__ V cmake(decltype(V::x) a, decltype(V::x) b)
+{
+    V v;
+    v.x = a;
+    v.y = b;
+    return v;
+}
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmake<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmake<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b)
+{
+    return cmake<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return cmake<V>(a.x * s, a.y * s); }
+
+// ---- index folding at the map edge ------------------------------------------------
+// Mirror: whole-sample symmetric extension (period 2(n-1)); periodic: mod n.
+__host__ __device__ __forceinline__ int fold_mirror(int i, int n)
+{
+    if (i >= 0 && i < n) return i;
+    if (n == 1) return 0;
+    const int p = 2 * (n - 1);
+    i %= p;
+    if (i < 0) i += p;
+    return i >= n ? p - i : i;
+}
+__host__ __device__ __forceinline__ int fold_periodic(int i, int n)
+{
+    if (i >= 0 && i < n) return i;
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+__host__ __device__ __forceinline__ int fold_index(int i, int n, int boundary)
+{
+    return boundary == FM_PERIODIC ? fold_periodic(i, n) : fold_mirror(i, n);
+}
+
+__host__ __device__ __forceinline__ int ilog2(unsigned v)
+{
+    int r = 0;
+    while ((1u << (r + 1)) <= v) ++r;
+    return r;
+}
+__host__ __device__ __forceinline__ bool is_pow2(long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// ---- per-device tables and scratch (api.cu) ---------------------------------------
+// Twiddles exp(-2 pi i t / n), t = 0..n-1, computed on the host in FP64.
+const void *twiddles(int n, int precision, cudaStream_t s, int *status);
+
+struct Scratch {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    ~Scratch()
+    {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+int scratch_alloc(Scratch &sc, size_t bytes, cudaStream_t s);
+
+// ---- internal launchers (defined per .cu file) ------------------------------------
+int launch_ks(const void *in1, const void *in2, long in_bstride, void *out1, void *out2, void *work, int n, int batch,
+              int precision, bool forward, uint64_t rot_seed, int rot_r0, bool rotate, cudaStream_t s);
+int launch_starlet(const void *kappa, void *pyr, long pyr_bstride, int n, int J, int batch, const fm_config &cfg,
+                   void *scratch, double *acc_s1, double *acc_s2, cudaStream_t s);
+size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg);
+int launch_map_direct(const void *g1, const void *g2, void *map, int n, int filter, double theta, int ell,
+                      double cut, int precision, cudaStream_t s);
+int launch_noise_finalize(const double *s1, const double *s2, const void *wdata, double *var, void *snr,
+                          long nelem, int R, int precision, cudaStream_t s);
+
+}  // namespace fm

@@ -1,0 +1,217 @@
+// mapdirect.cu -- brute-force aperture mass from tangential shear,
+// eq. shearmap (Sec. 2.1) evaluated as in Sec. 5.1: the comparison path whose
+// O(n^2 R^2) cost the starlet removes.
+//
+// M(x) = sum_{0 < |d| <= R} Q(|d|) gamma_t(x + d; x),
+// gamma_t = -(gamma1 cos 2 phi_d + gamma2 sin 2 phi_d), so with per-offset
+// weights A(d) = -Q cos 2 phi = -Q (dx^2 - dy^2) / |d|^2 and
+// B(d) = -Q sin 2 phi = -Q 2 dx dy / |d|^2 (built on the host in FP64) the map
+// is the 2-D correlation M = A * gamma1 + B * gamma2, zero outside the field.
+//
+// Kernel layout: a CTA owns TY = NW*RY output rows x TX = 32*CX columns; warp
+// w owns RY rows, lane l owns CX adjacent columns.  The CTA walks the input
+// rows iy covering its rows +- R; each input row (both components, halo R)
+// is staged once in shared memory and serves every output row within R of
+// it: output row y uses it with the weight row dy = iy - y.  Within a warp
+// all lanes share the output rows, so the dy tests and dx loop bounds are
+// warp-uniform, and weights are warp-wide broadcast loads.  The staged row
+// is stored with one pad slot per 8 so that the lanes' 8-column windows hit
+// distinct banks.  FP32 cores (FFMA), no tensor cores: not a contraction the
+// tensor cores can take at this precision.
+#include <math.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace fm {
+
+// ---- filters (Sec. 4), FP64 on the host --------------------------------------
+static double cube(double v) { return v * v * v; }
+
+// starlet Q(eta) printed in Sec. 4.2; the direct sum never evaluates eta = 0.
+static double q_starlet(double e)
+{
+    const double e2 = e * e;
+    double s = -279.0 * e2 * cube(fabs(e));
+    s += 8.0 * (1.0 + 6.0 * e + 24.0 * e2) * cube(fabs(0.5 - e));
+    s += 8.0 * (1.0 - 6.0 * e + 24.0 * e2) * cube(fabs(0.5 + e));
+    s -= 9.0 * (1.0 + 3.0 * e + 6.0 * e2) * cube(fabs(1.0 - e));
+    s -= 9.0 * (1.0 - 3.0 * e + 6.0 * e2) * cube(fabs(1.0 + e));
+    s += (1.0 + 1.5 * e + 1.5 * e2) * cube(fabs(2.0 - e));
+    s += (1.0 - 1.5 * e + 1.5 * e2) * cube(fabs(2.0 + e));
+    return s / (45.0 * e2);
+}
+
+static double q_of(int filter, double v, double theta, int ell)
+{
+    const double t2 = theta * theta;
+    switch (filter) {
+    case FM_FILTER_STARLET: return q_starlet(v / theta) / t2;  // U, Q scale as 1/theta^2
+    case FM_FILTER_S98: {  // eq. sch
+        if (v > theta) return 0.0;
+        const double x2 = v * v / t2;
+        return (1.0 + ell) * (2.0 + ell) / (M_PI * t2) * x2 * pow(1.0 - x2, (double)ell);
+    }
+    case FM_FILTER_JBJ04:
+    case FM_FILTER_VW98: {  // eq. mexhat with A = 1
+        const double b = filter == FM_FILTER_JBJ04 ? 0.5 : 4.0;
+        const double x = b * v * v / t2;
+        return x * exp(-x) / t2;
+    }
+    }
+    return 0.0;
+}
+
+static double default_cut(int filter) { return filter == FM_FILTER_STARLET ? 2.0 : filter == FM_FILTER_S98 ? 1.0 : 5.0; }
+
+// ---- kernel -------------------------------------------------------------------
+__device__ __forceinline__ int padc(int c) { return c + (c >> 3); }
+
+template <typename T, int CX, int RY, int NW>
+__global__ void __launch_bounds__(NW * 32) k_map_direct(const T *__restrict__ g1, const T *__restrict__ g2,
+                                                        const cplx_t<T> *__restrict__ taps, int tw,
+                                                        const int *__restrict__ dxmax, T *__restrict__ out, int n,
+                                                        int Ri)
+{
+    using V = cplx_t<T>;
+    constexpr int TX = 32 * CX, TY = NW * RY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int width = TX + 2 * Ri + 8;
+    const int pw = padc(width) + 1;
+    T *s1 = reinterpret_cast<T *>(smem_raw);  // [2 buffers][2 comps][pw]
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int yw = y0 + warp * RY;
+    const int lc = lane * CX;
+
+    T acc[RY][CX];
+#pragma unroll
+    for (int k = 0; k < RY; ++k)
+#pragma unroll
+        for (int o = 0; o < CX; ++o) acc[k][o] = (T)0;
+
+    const int iy_lo = y0 - Ri, iy_hi = y0 + TY - 1 + Ri;
+    for (int iy = iy_lo; iy <= iy_hi; ++iy) {
+        T *buf = s1 + ((iy - iy_lo) & 1) * 2 * pw;
+        const bool rin = iy >= 0 && iy < n;
+        for (int c = threadIdx.x; c < width; c += blockDim.x) {
+            const int gx = x0 - Ri + c;
+            T a = (T)0, bb = (T)0;
+            if (rin && gx >= 0 && gx < n) {
+                a = g1[(long)iy * n + gx];
+                bb = g2[(long)iy * n + gx];
+            }
+            buf[padc(c)] = a;
+            buf[pw + padc(c)] = bb;
+        }
+        __syncthreads();
+
+        int dy[RY];
+        bool act[RY];
+        int dxm = -1;
+#pragma unroll
+        for (int k = 0; k < RY; ++k) {
+            dy[k] = iy - (yw + k);
+            act[k] = dy[k] >= -Ri && dy[k] <= Ri && (yw + k) < n;
+            if (act[k]) {
+                const int m = __ldg(dxmax + dy[k] + Ri);
+                dxm = m > dxm ? m : dxm;
+            }
+        }
+        if (dxm >= 0) {
+            for (int dx0 = -dxm; dx0 <= dxm; dx0 += 8) {
+                T w1[CX + 7], w2[CX + 7];
+                const int base = lc + dx0 + Ri;
+#pragma unroll
+                for (int q = 0; q < CX + 7; ++q) {
+                    w1[q] = buf[padc(base + q)];
+                    w2[q] = buf[pw + padc(base + q)];
+                }
+#pragma unroll
+                for (int k = 0; k < RY; ++k) {
+                    if (!act[k]) continue;
+                    const V *trow = taps + (long)(dy[k] + Ri) * tw + (dx0 + Ri);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const V ab = __ldg(trow + t);
+#pragma unroll
+                        for (int o = 0; o < CX; ++o) {
+                            acc[k][o] = fma(ab.x, w1[o + t], acc[k][o]);
+                            acc[k][o] = fma(ab.y, w2[o + t], acc[k][o]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < RY; ++k) {
+        const int y = yw + k;
+        if (y >= n) continue;
+#pragma unroll
+        for (int o = 0; o < CX; ++o) {
+            const int x = x0 + lc + o;
+            if (x < n) out[(long)y * n + x] = acc[k][o];
+        }
+    }
+}
+
+template <typename T>
+static int map_direct_impl(const T *g1, const T *g2, T *map, int n, int filter, double theta, int ell, double cut,
+                           cudaStream_t s)
+{
+    using V = cplx_t<T>;
+    const double R = (cut > 0 ? cut : default_cut(filter)) * theta;
+    const int Ri = (int)floor(R);
+    const int tw = 2 * Ri + 8;  // weight row: dx = -Ri .. Ri + 7 (zeros beyond R)
+    std::vector<V> htaps((size_t)(2 * Ri + 1) * tw);
+    std::vector<int> hdx(2 * Ri + 1);
+    for (int dy = -Ri; dy <= Ri; ++dy) {
+        const double m2 = R * R - (double)dy * dy;
+        hdx[dy + Ri] = m2 >= 0 ? (int)floor(sqrt(m2)) : -1;
+        for (int c = 0; c < tw; ++c) {
+            const int dx = c - Ri;
+            const double r2 = (double)dx * dx + (double)dy * dy;
+            V ab;
+            ab.x = ab.y = 0;
+            if (r2 > 0 && r2 <= R * R) {
+                const double q = q_of(filter, sqrt(r2), theta, ell);
+                ab.x = (decltype(ab.x))(-q * ((double)dx * dx - (double)dy * dy) / r2);
+                ab.y = (decltype(ab.y))(-q * 2.0 * dx * dy / r2);
+            }
+            htaps[(size_t)(dy + Ri) * tw + c] = ab;
+        }
+    }
+    Scratch sc;
+    const size_t tap_bytes = htaps.size() * sizeof(V);
+    const size_t dx_bytes = hdx.size() * sizeof(int);
+    int st = scratch_alloc(sc, tap_bytes + dx_bytes + 256, s);
+    if (st != FM_OK) return st;
+    V *dtaps = static_cast<V *>(sc.p);
+    int *ddx = reinterpret_cast<int *>(static_cast<char *>(sc.p) + ((tap_bytes + 255) / 256) * 256);
+    FM_CUDA_TRY(cudaMemcpyAsync(dtaps, htaps.data(), tap_bytes, cudaMemcpyHostToDevice, s));
+    FM_CUDA_TRY(cudaMemcpyAsync(ddx, hdx.data(), dx_bytes, cudaMemcpyHostToDevice, s));
+
+    constexpr int CX = 8, RY = 4, NW = 4;
+    constexpr int TX = 32 * CX, TY = NW * RY;
+    const int width = TX + 2 * Ri + 8;
+    const int pw = width + (width >> 3) + 1;
+    const size_t smem = 2ull * 2 * pw * sizeof(T);
+    auto k = k_map_direct<T, CX, RY, NW>;
+    FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY);
+    FM_LAUNCH(FM_K_MAP_DIRECT, k, grid, NW * 32, smem, s, g1, g2, dtaps, tw, ddx, map, n, Ri);
+    return FM_OK;
+}
+
+int launch_map_direct(const void *g1, const void *g2, void *map, int n, int filter, double theta, int ell,
+                      double cut, int precision, cudaStream_t s)
+{
+    if (precision == FM_F64)
+        return map_direct_impl<double>((const double *)g1, (const double *)g2, (double *)map, n, filter, theta, ell,
+                                       cut, s);
+    return map_direct_impl<float>((const float *)g1, (const float *)g2, (float *)map, n, filter, theta, ell, cut, s);
+}
+
+}  // namespace fm

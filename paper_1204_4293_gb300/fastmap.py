@@ -1,0 +1,292 @@
+"""Thin Python binding of libfastmap (include/fastmap.h) over torch tensors.
+
+Argument marshalling only: every function here checks shapes, dtypes and
+devices, allocates outputs with torch (device memory is torch's job) and
+calls the C entry point of the same name on torch's current CUDA stream.
+All compute runs in the library's CUDA kernels; there is no CPU fallback.
+Importing this module fails if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfastmap.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1204_4293_gb300.build` "
+                      "(or __graft_entry__.build()); there is no fallback implementation")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---- constants (mirror include/fastmap.h) ------------------------------------
+FM_OK, FM_PENDING = 0, 1
+FM_EINVAL, FM_ENOMEM, FM_EBUDGET, FM_ETIMEOUT, FM_ECUDA, FM_ENOTFOUND, FM_EBUSY = -1, -2, -3, -4, -5, -6, -7
+FM_F32, FM_F64 = 0, 1
+FM_MIRROR, FM_PERIODIC = 0, 1
+FM_FILTER_STARLET, FM_FILTER_S98, FM_FILTER_JBJ04, FM_FILTER_VW98 = 0, 1, 2, 3
+KERNEL_IDS = {"fft_rows_fwd": 1, "fft_cols_ks": 2, "fft_rows_inv": 3, "starlet_tile": 4, "starlet_row": 5,
+              "starlet_col": 6, "map_direct": 7, "noise_final": 8}
+
+
+class fm_config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("boundary", ctypes.c_int), ("accum", ctypes.c_int),
+                ("fuse_depth", ctypes.c_int), ("tile", ctypes.c_int)]
+
+
+class fm_request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("J", ctypes.c_int), ("R", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int), ("g1", ctypes.c_void_p), ("g2", ctypes.c_void_p),
+                ("out_pyramid", ctypes.c_void_p), ("out_var", ctypes.c_void_p)]
+
+
+class fm_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
+_P, _I, _D, _U64, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_size_t
+_CFG = ctypes.POINTER(fm_config)
+_SIGS = {
+    "fm_ks_invert": (_I, [_P, _P, _P, _P, _I, _I, _CFG, _P]),
+    "fm_ks_forward": (_I, [_P, _P, _P, _I, _I, _CFG, _P]),
+    "fm_starlet_forward": (_I, [_P, _P, _I, _I, _I, _CFG, _P]),
+    "fm_map_starlet": (_I, [_P, _P, _P, _I, _I, _I, _CFG, _P]),
+    "fm_map_starlet_host": (_I, [_P, _P, _P, _I, _I, _I, _CFG, _P]),
+    "fm_map_direct": (_I, [_P, _P, _P, _I, _I, _D, _I, _D, _CFG, _P]),
+    "fm_map_noise": (_I, [_P, _P, _P, _P, _I, _I, _I, _U64, _CFG, _P]),
+    "fm_serve_create": (_I, [_SZ, _I, ctypes.POINTER(ctypes.c_void_p)]),
+    "fm_serve_submit": (_I, [_P, ctypes.POINTER(fm_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "fm_serve_poll": (_I, [_P, _U64, ctypes.POINTER(fm_result)]),
+    "fm_serve_wait": (_I, [_P, _U64, ctypes.POINTER(fm_result), _D]),
+    "fm_serve_destroy": (_I, [_P]),
+    "fm_request_scratch_bytes": (_SZ, [ctypes.POINTER(fm_request)]),
+    "fm_status_string": (ctypes.c_char_p, [_I]),
+    "fm_last_error": (ctypes.c_char_p, []),
+    "fm_launch_count": (ctypes.c_int64, []),
+    "fm_profile_select": (_I, [_I]),
+    "fm_profile_read": (_I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+lib = _lib  # raw ctypes handle (C-ABI calls with plain pointers)
+
+
+class FastmapError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.fm_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {_lib.fm_status_string(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def _check(status: int, where: str) -> int:
+    if status < 0:
+        raise FastmapError(status, where)
+    return status
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _prec(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return FM_F32
+    if t.dtype == torch.float64:
+        return FM_F64
+    raise TypeError(f"maps must be float32 or float64, got {t.dtype}")
+
+
+def _cfg(precision, boundary=FM_MIRROR, fuse_depth=0):
+    c = fm_config()
+    c.precision, c.boundary, c.accum, c.fuse_depth, c.tile = precision, boundary, 0, fuse_depth, 0
+    return c
+
+
+def _maps(*ts, device=True):
+    """Validate a set of same-shape [batch, n, n] or [n, n] contiguous maps."""
+    ref = ts[0]
+    for t in ts:
+        if t.shape != ref.shape or t.dtype != ref.dtype:
+            raise ValueError("maps must share shape and dtype")
+        if device and not t.is_cuda:
+            raise ValueError("maps must be CUDA tensors")
+        if not t.is_contiguous():
+            raise ValueError("maps must be contiguous")
+    if ref.dim() not in (2, 3) or ref.shape[-1] != ref.shape[-2]:
+        raise ValueError("maps are [n, n] or [batch, n, n]")
+    n = ref.shape[-1]
+    batch = 1 if ref.dim() == 2 else ref.shape[0]
+    return n, batch
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+# ---- entry points ----------------------------------------------------------------
+def fm_ks_invert(g1, g2, with_b=False, stream=None):
+    """(kappa_E, kappa_B or None) from shear (Kaiser-Squires, Sec. 4.4)."""
+    n, batch = _maps(g1, g2)
+    kE = torch.empty_like(g1)
+    kB = torch.empty_like(g1) if with_b else None
+    c = _cfg(_prec(g1))
+    _check(_lib.fm_ks_invert(_ptr(g1), _ptr(g2), _ptr(kE), _ptr(kB), n, batch, ctypes.byref(c), _stream(stream)),
+           "fm_ks_invert")
+    return kE, kB
+
+
+def fm_ks_forward(kappa, stream=None):
+    """(gamma1, gamma2) of a convergence map (forward Kaiser-Squires)."""
+    n, batch = _maps(kappa)
+    g1, g2 = torch.empty_like(kappa), torch.empty_like(kappa)
+    c = _cfg(_prec(kappa))
+    _check(_lib.fm_ks_forward(_ptr(kappa), _ptr(g1), _ptr(g2), n, batch, ctypes.byref(c), _stream(stream)),
+           "fm_ks_forward")
+    return g1, g2
+
+
+def _pyr_out(ref, J, out):
+    shape = ((J,) if ref.dim() == 2 else (ref.shape[0], J)) + tuple(ref.shape[-2:])
+    if out is None:
+        return torch.empty(shape, dtype=ref.dtype, device=ref.device)
+    if tuple(out.shape) != shape or out.dtype != ref.dtype or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous {ref.dtype} tensor of shape {shape}")
+    return out
+
+
+def fm_starlet_forward(kappa, J, boundary=FM_MIRROR, fuse_depth=0, out=None, stream=None):
+    """Starlet pyramid [.., J, n, n]: w_1..w_{J-1}, smooth (Sec. 3)."""
+    n, batch = _maps(kappa)
+    pyr = _pyr_out(kappa, J, out)
+    c = _cfg(_prec(kappa), boundary, fuse_depth)
+    _check(_lib.fm_starlet_forward(_ptr(kappa), _ptr(pyr), n, J, batch, ctypes.byref(c), _stream(stream)),
+           "fm_starlet_forward")
+    return pyr
+
+
+def fm_map_starlet(g1, g2, J, boundary=FM_MIRROR, fuse_depth=0, out=None, stream=None):
+    """KS inversion then starlet: all aperture-mass bands from shear."""
+    n, batch = _maps(g1, g2)
+    pyr = _pyr_out(g1, J, out)
+    c = _cfg(_prec(g1), boundary, fuse_depth)
+    _check(_lib.fm_map_starlet(_ptr(g1), _ptr(g2), _ptr(pyr), n, J, batch, ctypes.byref(c), _stream(stream)),
+           "fm_map_starlet")
+    return pyr
+
+
+def fm_map_starlet_host(g1, g2, J, out, boundary=FM_MIRROR, fuse_depth=0, stream=None):
+    """fm_map_starlet from and to HOST tensors (pinned for speed); asynchronous."""
+    n, batch = _maps(g1, g2, device=False)
+    if g1.is_cuda or out.is_cuda:
+        raise ValueError("fm_map_starlet_host takes host tensors")
+    _pyr_out(g1, J, out)
+    c = _cfg(_prec(g1), boundary, fuse_depth)
+    _check(_lib.fm_map_starlet_host(_ptr(g1), _ptr(g2), _ptr(out), n, J, batch, ctypes.byref(c), _stream(stream)),
+           "fm_map_starlet_host")
+    return out
+
+
+def fm_map_direct(g1, g2, filt, theta, ell=3, cut_over_theta=0.0, out=None, stream=None):
+    """Brute-force M_ap map from tangential shear (eq. shearmap)."""
+    n, batch = _maps(g1, g2)
+    if batch != 1 or g1.dim() != 2:
+        raise ValueError("fm_map_direct takes one [n, n] map")
+    m = torch.empty_like(g1) if out is None else out
+    c = _cfg(_prec(g1))
+    _check(_lib.fm_map_direct(_ptr(g1), _ptr(g2), _ptr(m), n, int(filt), float(theta), int(ell),
+                              float(cut_over_theta), ctypes.byref(c), _stream(stream)), "fm_map_direct")
+    return m
+
+
+def fm_map_noise(g1, g2, J, R, seed, boundary=FM_MIRROR, with_snr=True, fuse_depth=0, stream=None):
+    """(variance [J-1, n, n] float64, S/N or None) over R rotated realisations."""
+    n, batch = _maps(g1, g2)
+    if batch != 1 or g1.dim() != 2:
+        raise ValueError("fm_map_noise takes one [n, n] map")
+    var = torch.empty((J - 1, n, n), dtype=torch.float64, device=g1.device)
+    snr = torch.empty((J - 1, n, n), dtype=g1.dtype, device=g1.device) if with_snr else None
+    c = _cfg(_prec(g1), boundary, fuse_depth)
+    _check(_lib.fm_map_noise(_ptr(g1), _ptr(g2), _ptr(var), _ptr(snr), n, J, int(R),
+                             ctypes.c_uint64(int(seed) & (2**64 - 1)), ctypes.byref(c), _stream(stream)),
+           "fm_map_noise")
+    return var, snr
+
+
+def fm_launch_count() -> int:
+    return int(_lib.fm_launch_count())
+
+
+def fm_profile_select(kernel: str | int) -> None:
+    kid = KERNEL_IDS[kernel] if isinstance(kernel, str) else int(kernel)
+    _check(_lib.fm_profile_select(kid), "fm_profile_select")
+
+
+def fm_profile_read():
+    ms = ctypes.c_double(0)
+    cnt = ctypes.c_int64(0)
+    _check(_lib.fm_profile_read(ctypes.byref(ms), ctypes.byref(cnt)), "fm_profile_read")
+    return ms.value, cnt.value
+
+
+class Server:
+    """Continuous-batching server (fm_serve_*): submit, poll, wait."""
+
+    def __init__(self, mem_budget_bytes: int, max_slots: int = 4):
+        h = ctypes.c_void_p()
+        _check(_lib.fm_serve_create(int(mem_budget_bytes), int(max_slots), ctypes.byref(h)), "fm_serve_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, g1, g2, J, out_pyramid, R=0, seed=0, out_var=None) -> int:
+        n, batch = _maps(g1, g2)
+        if batch != 1 or g1.dim() != 2:
+            raise ValueError("one [n, n] map per request")
+        r = fm_request(n=n, J=J, R=int(R), seed=int(seed) & (2**64 - 1), precision=_prec(g1),
+                       g1=g1.data_ptr(), g2=g2.data_ptr(), out_pyramid=out_pyramid.data_ptr(),
+                       out_var=out_var.data_ptr() if out_var is not None else None)
+        t = ctypes.c_uint64()
+        _check(_lib.fm_serve_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "fm_serve_submit")
+        self._keep[t.value] = (g1, g2, out_pyramid, out_var)  # keep buffers alive until done
+        return t.value
+
+    def poll(self, ticket: int):
+        res = fm_result()
+        st = _lib.fm_serve_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(res))
+        if st == FM_PENDING:
+            return None
+        _check(st, "fm_serve_poll")
+        self._keep.pop(ticket, None)
+        return res
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        res = fm_result()
+        st = _lib.fm_serve_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(res), float(timeout_s))
+        _check(st, "fm_serve_wait")
+        self._keep.pop(ticket, None)
+        return res
+
+    @staticmethod
+    def scratch_bytes(n, J, R=0, precision=FM_F32, with_var=False) -> int:
+        r = fm_request(n=n, J=J, R=R, seed=0, precision=precision, g1=None, g2=None, out_pyramid=None,
+                       out_var=1 if with_var else None)
+        return int(_lib.fm_request_scratch_bytes(ctypes.byref(r)))
+
+    def close(self):
+        if self._h:
+            _check(_lib.fm_serve_destroy(self._h), "fm_serve_destroy")
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

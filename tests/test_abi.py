@@ -1,0 +1,73 @@
+"""CPU-side checks of the C ABI: the library builds and loads, exports every
+function include/fastmap.h declares, and rejects invalid arguments before it
+touches a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fastmap.h")
+
+
+@pytest.fixture(scope="module")
+def fm():
+    from paper_1204_4293_gb300 import build
+    build.build()
+    from paper_1204_4293_gb300 import fastmap
+    return fastmap
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(fm_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("fm_ks_invert", "fm_starlet_forward", "fm_map_direct", "fm_map_noise", "fm_serve_create",
+                     "fm_serve_submit", "fm_serve_poll", "fm_serve_destroy", "fm_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(fm):
+    lib = ctypes.CDLL(fm.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(fm):
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7):
+        assert fm.lib.fm_status_string(code)
+    assert fm.lib.fm_status_string(-99) == b"unknown status"
+
+
+def test_validation_before_any_device_work(fm):
+    c = fm._cfg(0)
+    cfg = ctypes.byref(c)
+    lib = fm.lib
+    assert lib.fm_ks_invert(None, None, None, None, 48, 1, cfg, None) == fm.FM_EINVAL
+    assert lib.fm_ks_invert(None, None, None, None, 16384, 1, cfg, None) == fm.FM_EINVAL
+    assert lib.fm_ks_forward(None, None, None, 64, 0, cfg, None) == fm.FM_EINVAL
+    assert lib.fm_starlet_forward(None, None, 16, 5, 1, cfg, None) == fm.FM_EINVAL
+    assert lib.fm_starlet_forward(None, None, 64, 1, 1, cfg, None) == fm.FM_EINVAL
+    assert lib.fm_map_starlet(None, None, None, 64, 3, 1, cfg, None) == fm.FM_EINVAL  # null pointers
+    assert lib.fm_map_direct(None, None, None, 64, 7, 2.0, 3, 0.0, cfg, None) == fm.FM_EINVAL
+    assert lib.fm_map_direct(None, None, None, 64, 0, -1.0, 3, 0.0, cfg, None) == fm.FM_EINVAL
+    assert lib.fm_map_noise(None, None, None, None, 64, 4, 1, 0, cfg, None) == fm.FM_EINVAL
+    bad = fm._cfg(2)
+    assert lib.fm_starlet_forward(None, None, 64, 3, 1, ctypes.byref(bad), None) == fm.FM_EINVAL
+    assert b"precision" in lib.fm_last_error()
+    h = ctypes.c_void_p()
+    assert lib.fm_serve_create(0, 2, ctypes.byref(h)) == fm.FM_EINVAL
+    assert lib.fm_serve_poll(None, 1, None) == fm.FM_EINVAL
+
+
+def test_request_scratch_bytes_is_monotone(fm):
+    small = fm.Server.scratch_bytes(256, 6)
+    big = fm.Server.scratch_bytes(1024, 8)
+    noisy = fm.Server.scratch_bytes(1024, 8, R=100, with_var=True)
+    assert 0 < small < big <= noisy

@@ -1,0 +1,90 @@
+"""C-ABI behaviour on the GPU: errors come back as status codes, launches are
+counted, the profiling hook times a selected kernel, and serving gives each
+request the same result alone and in a concurrent mix."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import shear
+
+pytestmark = pytest.mark.gpu
+
+
+def _fm():
+    from paper_1204_4293_gb300 import fastmap
+    return fastmap
+
+
+def test_invalid_arguments_return_einval():
+    fm = _fm()
+    x = torch.zeros(2, 48, 48, device="cuda")
+    with pytest.raises(fm.FastmapError) as e:
+        fm.fm_ks_invert(x, x)  # 48 is not a power of two
+    assert e.value.status == fm.FM_EINVAL
+    with pytest.raises(fm.FastmapError):
+        fm.fm_starlet_forward(torch.zeros(16, 16, device="cuda"), 5)  # n < 2^J
+    c = fm._cfg(0)
+    assert fm.lib.fm_map_direct(None, None, None, 16, 9, 2.0, 3, 0.0, ctypes.byref(c), None) == fm.FM_EINVAL
+    # the context is still healthy
+    y = fm.fm_starlet_forward(torch.ones(32, 32, device="cuda"), 3)
+    torch.cuda.synchronize()
+    assert torch.isfinite(y).all()
+
+
+def test_launch_count_and_profile_hook():
+    fm = _fm()
+    g1 = torch.randn(4, 256, 256, device="cuda")
+    g2 = torch.randn(4, 256, 256, device="cuda")
+    fm.fm_map_starlet(g1, g2, 6)
+    c0 = fm.fm_launch_count()
+    fm.fm_profile_select("fft_cols_ks")
+    for _ in range(3):
+        fm.fm_map_starlet(g1, g2, 6)
+    ms, cnt = fm.fm_profile_read()
+    fm.fm_profile_select(0)
+    assert cnt == 3 and ms > 0
+    assert fm.fm_launch_count() - c0 >= 3 * 5
+
+
+def test_serving_mix_equals_alone():
+    fm = _fm()
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(10):
+        n = int(rng.choice([64, 128, 256]))
+        J = int(np.log2(n)) - 2
+        R = int(rng.choice([0, 0, 4]))
+        g1, g2 = shear(n, seed=30 + i, dtype=np.float32)
+        reqs.append((torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda(), J, R))
+    alone = []
+    for g1, g2, J, R in reqs:
+        pyr = fm.fm_map_starlet(g1, g2, J)
+        var = fm.fm_map_noise(g1, g2, J, R, seed=77, with_snr=False)[0] if R else None
+        alone.append((pyr, var))
+    torch.cuda.synchronize()
+    with fm.Server(mem_budget_bytes=64 << 20, max_slots=4) as sv:
+        outs, tickets = [], []
+        for g1, g2, J, R in reqs:
+            n = g1.shape[-1]
+            pyr = torch.empty(J, n, n, device="cuda")
+            var = torch.empty(J - 1, n, n, dtype=torch.float64, device="cuda") if R else None
+            tickets.append(sv.submit(g1, g2, J, pyr, R=R, seed=77, out_var=var))
+            outs.append((pyr, var))
+        res = [sv.wait(t, 60.0) for t in tickets]
+    assert all(r.status == fm.FM_OK for r in res)
+    assert all(r.t_submit_ns <= r.t_admit_ns <= r.t_done_ns for r in res)
+    for (pa, va), (pb, vb) in zip(alone, outs):
+        assert torch.equal(pa, pb)
+        if va is not None:
+            assert torch.allclose(va, vb, rtol=1e-12, atol=0)
+
+
+def test_serving_rejects_over_budget():
+    fm = _fm()
+    g1 = torch.zeros(512, 512, device="cuda")
+    pyr = torch.empty(7, 512, 512, device="cuda")
+    with fm.Server(mem_budget_bytes=1 << 20, max_slots=2) as sv:
+        res = sv.wait(sv.submit(g1, g1, 7, pyr), 30.0)
+    assert res.status == fm.FM_EBUDGET

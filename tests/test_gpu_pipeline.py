@@ -1,0 +1,60 @@
+"""GPU shear -> KS -> starlet (the fast aperture-mass maps) against the oracle,
+at the small configuration (256^2, J = 5), at the paper's 1024^2 J = 7 in the
+benchmark's batched launch, and through the host-buffer entry point."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import TOL, band_errs, shear
+
+pytestmark = pytest.mark.gpu
+
+
+def _fm():
+    from paper_1204_4293_gb300 import fastmap
+    return fastmap
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("n,J,batch", [(16, 3, 2), (64, 5, 1), (256, 5, 2)])
+def test_map_starlet_matches_oracle(n, J, batch, dtype):
+    fm = _fm()
+    maps = [shear(n, seed=20 + b, dtype=dtype) for b in range(batch)]
+    g1 = torch.from_numpy(np.stack([m[0] for m in maps])).cuda()
+    g2 = torch.from_numpy(np.stack([m[1] for m in maps])).cuda()
+    pyr = fm.fm_map_starlet(g1, g2, J).cpu().numpy()
+    for b in range(batch):
+        ref = oracle.map_starlet(maps[b][0].astype(np.float64), maps[b][1].astype(np.float64), J)
+        assert max(band_errs(pyr[b], ref)) <= TOL[dtype]
+
+
+def test_map_starlet_paper_size_batched():
+    # the benchmark's workload: a batch of 1024^2 fp32 shear maps, J = 7;
+    # the oracle checks the first and the last map of the batch in full.
+    fm = _fm()
+    n, J, batch = 1024, 7, 8
+    maps = [shear(n, seed=2 + b, dtype=np.float32) for b in (0, batch - 1)]
+    g1 = torch.empty((batch, n, n), dtype=torch.float32, device="cuda")
+    g2 = torch.empty_like(g1)
+    g1.normal_(0, 0.1)
+    g2.normal_(0, 0.1)
+    g1[0], g2[0] = torch.from_numpy(maps[0][0]), torch.from_numpy(maps[0][1])
+    g1[-1], g2[-1] = torch.from_numpy(maps[1][0]), torch.from_numpy(maps[1][1])
+    pyr = fm.fm_map_starlet(g1, g2, J)
+    for idx, m in ((0, maps[0]), (batch - 1, maps[1])):
+        ref = oracle.map_starlet(m[0].astype(np.float64), m[1].astype(np.float64), J)
+        errs = band_errs(pyr[idx].cpu().numpy(), ref)
+        assert max(errs) <= 1e-5, errs
+
+
+def test_map_starlet_host_equals_device():
+    fm = _fm()
+    n, J, batch = 128, 6, 3
+    g1 = torch.randn(batch, n, n, dtype=torch.float32).mul_(0.1).pin_memory()
+    g2 = torch.randn(batch, n, n, dtype=torch.float32).mul_(0.1).pin_memory()
+    out = torch.empty(batch, J, n, n, dtype=torch.float32).pin_memory()
+    fm.fm_map_starlet_host(g1, g2, J, out)
+    torch.cuda.synchronize()
+    dev = fm.fm_map_starlet(g1.cuda(), g2.cuda(), J).cpu()
+    assert torch.equal(out, dev)

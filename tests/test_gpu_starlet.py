@@ -1,0 +1,74 @@
+"""GPU starlet transform (Sec. 3, Sec. 4.2) against the FP64 oracle.
+
+Sizes span several 64-pixel tiles with ragged tails (n not a multiple of the
+tile, n not a power of two), the smallest legal maps (n = 2^J), both
+boundaries, every fusion depth, batches, and the degenerate constant map.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import TOL, band_errs
+from paper_1204_4293_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _fm():
+    from paper_1204_4293_gb300 import fastmap
+    return fastmap
+
+
+CASES = [(4, 2), (8, 3), (16, 4), (37, 5), (64, 6), (100, 6), (200, 7), (256, 5), (130, 7)]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("boundary", [0, 1])
+@pytest.mark.parametrize("n,J", CASES)
+def test_starlet_matches_oracle(n, J, boundary, dtype):
+    fm = _fm()
+    kappa = synth.grf_kappa(n, seed=n + J) + synth.white((n, n), seed=J, scale=0.05)
+    kappa = kappa.astype(dtype)
+    ref = oracle.starlet(kappa.astype(np.float64), J, boundary)
+    for fuse in sorted({-1, 1, 2, 3, J - 1}):
+        if fuse > J - 1:
+            continue
+        pyr = fm.fm_starlet_forward(torch.from_numpy(kappa).cuda(), J, boundary=boundary, fuse_depth=fuse)
+        errs = band_errs(pyr.cpu().numpy(), ref)
+        assert max(errs) <= TOL[dtype], (fuse, errs)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_starlet_batch_and_reconstruction(dtype):
+    fm = _fm()
+    n, J, batch = 96, 6, 3
+    maps = np.stack([synth.grf_kappa(n, seed=s) for s in range(batch)]).astype(dtype)
+    pyr = fm.fm_starlet_forward(torch.from_numpy(maps).cuda(), J).cpu().numpy()
+    assert pyr.shape == (batch, J, n, n)
+    for b in range(batch):
+        ref = oracle.starlet(maps[b].astype(np.float64), J)
+        assert max(band_errs(pyr[b], ref)) <= TOL[dtype]
+        # kappa = c_J + sum_j w_j (Sec. 3)
+        rec = pyr[b].astype(np.float64).sum(axis=0)
+        assert np.abs(rec - maps[b]).max() <= 1e-5 * np.abs(maps[b]).max()
+
+
+def test_constant_map_gives_zero_bands():
+    fm = _fm()
+    kappa = torch.full((64, 64), 0.75, dtype=torch.float32, device="cuda")
+    pyr = fm.fm_starlet_forward(kappa, 5).cpu().numpy()
+    assert np.abs(pyr[:-1]).max() < 1e-6
+    assert np.abs(pyr[-1] - 0.75).max() < 1e-6
+
+
+def test_starlet_full_size_paper_config():
+    # 1024 x 1024, J = 7 (theta = 2..64 px), a batch of maps as the benchmark runs it
+    fm = _fm()
+    n, J, batch = 1024, 7, 4
+    maps = np.stack([synth.grf_kappa(n, seed=100 + b) for b in range(batch)]).astype(np.float32)
+    pyr = fm.fm_starlet_forward(torch.from_numpy(maps).cuda(), J).cpu().numpy()
+    for b in (0, batch - 1):
+        ref = oracle.starlet(maps[b].astype(np.float64), J)
+        errs = band_errs(pyr[b], ref)
+        assert max(errs) <= 1e-5, errs
