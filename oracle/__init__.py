@@ -97,6 +97,13 @@ def _n_of(a):
     return a.shape[0]
 
 
+def _pow2_n(a):
+    n = _n_of(a)
+    if n < 1 or n & (n - 1):
+        raise ValueError("the radix-2 FFT needs n a power of two")
+    return n
+
+
 MIRROR, PERIODIC = 0, 1
 STARLET_Q, S98, JBJ04, VW98 = 0, 1, 2, 3
 
@@ -148,7 +155,7 @@ def default_cut(filt):
 def fft2(a, inverse=False):
     """2-D FFT (forward unnormalised, inverse / n^2) of a complex n x n array."""
     a = np.ascontiguousarray(a, dtype=np.complex128).copy()
-    n = _n_of(a)
+    n = _pow2_n(a)
     _load().oracle_fft2(a.view(np.float64).ctypes.data_as(_D), n, 1 if inverse else 0)
     return a
 
@@ -156,7 +163,7 @@ def fft2(a, inverse=False):
 def ks_forward(kappa):
     """gamma1, gamma2 = KS forward of kappa (Sec. 4.4)."""
     k = _in(kappa)
-    n = _n_of(k)
+    n = _pow2_n(k)
     g1, g2 = np.empty_like(k), np.empty_like(k)
     _load().oracle_ks_forward(_p(k), _p(g1), _p(g2), n)
     return g1, g2
@@ -165,7 +172,7 @@ def ks_forward(kappa):
 def ks_invert(g1, g2):
     """(kappa_E, kappa_B) = KS inverse of the shear (Sec. 4.4)."""
     a = _in(g1)
-    n = _n_of(a)
+    n = _pow2_n(a)
     b = _in(g2, n)
     kE, kB = np.empty_like(a), np.empty_like(a)
     _load().oracle_ks_invert(_p(a), _p(b), _p(kE), _p(kB), n)
@@ -184,7 +191,7 @@ def starlet(kappa, J, boundary=MIRROR):
 def map_starlet(g1, g2, J, boundary=MIRROR):
     """KS inversion then the starlet of kappa_E."""
     a = _in(g1)
-    n = _n_of(a)
+    n = _pow2_n(a)
     b = _in(g2, n)
     pyr = np.empty((J, n, n))
     _load().oracle_map_starlet(_p(a), _p(b), _p(pyr), n, int(J), int(boundary))
@@ -223,7 +230,7 @@ def noise_u(seed, r, y, x, n):
 
 def rotate_shear(g1, g2, r, seed):
     a = _in(g1)
-    n = _n_of(a)
+    n = _pow2_n(a)
     b = _in(g2, n)
     o1, o2 = np.empty_like(a), np.empty_like(a)
     _load().oracle_rotate_shear(_p(a), _p(b), _p(o1), _p(o2), n, int(r), int(seed) & (2**64 - 1))
@@ -233,7 +240,7 @@ def rotate_shear(g1, g2, r, seed):
 def map_noise(g1, g2, J, R, seed, boundary=MIRROR, with_snr=True):
     """(var, snr): per-band variance over R rotated realisations and S/N."""
     a = _in(g1)
-    n = _n_of(a)
+    n = _pow2_n(a)
     b = _in(g2, n)
     var = np.empty((J - 1, n, n))
     snr = np.empty((J - 1, n, n)) if with_snr else None

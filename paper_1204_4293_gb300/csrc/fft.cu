@@ -11,63 +11,10 @@
 // done in place in shared memory with a barrier between the loads and the
 // stores of a pass; twiddles come from an FP64-computed table.
 #include "common.cuh"
+#include "dft.cuh"
+#include "rng.cuh"
 
 namespace fm {
-
-// ---------------------------------------------------------------------------
-// radix-R DFT in registers; forward kernel exp(-2 pi i m k / R), inverse +.
-template <bool INV, typename V> __device__ __forceinline__ V mul_minus_i(V a)
-{
-    // forward: a * (-i); inverse: a * (+i)
-    return INV ? cmake<V>(-a.y, a.x) : cmake<V>(a.y, -a.x);
-}
-
-template <int R, bool INV, typename V> struct Dft;
-
-template <bool INV, typename V> struct Dft<2, INV, V> {
-    __device__ __forceinline__ static void run(V *v)
-    {
-        V a = cadd(v[0], v[1]);
-        V b = csub(v[0], v[1]);
-        v[0] = a;
-        v[1] = b;
-    }
-};
-
-template <bool INV, typename V> struct Dft<4, INV, V> {
-    __device__ __forceinline__ static void run(V *v)
-    {
-        V t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        V t2 = cadd(v[1], v[3]), t3 = mul_minus_i<INV>(csub(v[1], v[3]));
-        v[0] = cadd(t0, t2);
-        v[2] = csub(t0, t2);
-        v[1] = cadd(t1, t3);
-        v[3] = csub(t1, t3);
-    }
-};
-
-template <bool INV, typename V> struct Dft<8, INV, V> {
-    __device__ __forceinline__ static void run(V *v)
-    {
-        using T = decltype(V::x);
-        const T h = (T)0.70710678118654752440;  // sqrt(1/2)
-        V e[4] = {v[0], v[2], v[4], v[6]};
-        V o[4] = {v[1], v[3], v[5], v[7]};
-        Dft<4, INV, V>::run(e);
-        Dft<4, INV, V>::run(o);
-        // o_k *= W8^k, W8 = exp(-+ i pi / 4)
-        o[1] = INV ? cmake<V>(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
-                   : cmake<V>(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
-        o[2] = mul_minus_i<INV>(o[2]);
-        o[3] = INV ? cmake<V>(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
-                   : cmake<V>(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            v[k] = cadd(e[k], o[k]);
-            v[k + 4] = csub(e[k], o[k]);
-        }
-    }
-};
 
 // element address inside one smem vector: padded (one slot per 8) for the
 // row layout to spread the stride-R stores over the banks.
@@ -153,19 +100,6 @@ __device__ void smem_fft(V *buf, int n, int logn, int lognvec, int vstride, int 
 }
 
 // ---------------------------------------------------------------------------
-// SplitMix64 at a counter (Steele, Lea & Flood 2014): state `seed` advanced
-// (index + 1) times by the golden gamma, then the 64-bit finaliser.
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t index)
-{
-    uint64_t z = seed + (index + 1ull) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ void rot_sincos(float two_u, float *s, float *c) { sincospif(two_u, s, c); }
-__device__ __forceinline__ void rot_sincos(double two_u, double *s, double *c) { sincospi(two_u, s, c); }
-
 // rows_fwd: one CTA holds `1 << lognvec` rows.  in2 may be null (real input).
 template <typename T, int E>
 __global__ void __launch_bounds__(1024) k_rows_fwd(const T *__restrict__ in1, const T *__restrict__ in2,
@@ -189,16 +123,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T *__restrict__ in1, co
             const long off = b * in_bstride + (long)y * n + x;
             T a = in1[off];
             T c = in2 ? in2[off] : (T)0;
-            if (rotate) {
-                const uint64_t ctr = ((uint64_t)(r0 + b) * (uint64_t)n + (uint64_t)y) * (uint64_t)n + (uint64_t)x;
-                const T u = (T)(splitmix64_at(seed, ctr) >> 40) * (T)(1.0 / 16777216.0);
-                T sn, cs;
-                rot_sincos((T)2 * u, &sn, &cs);
-                const T ra = a * cs - c * sn;
-                const T rc = a * sn + c * cs;
-                a = ra;
-                c = rc;
-            }
+            if (rotate) rotate_shear(a, c, seed, r0 + b, y, x, n);
             val = cmake<V>(a, c);
         }
         buf[rr * vstride + x + (x >> 3)] = val;
@@ -340,6 +265,13 @@ int launch_ks(const void *in1, const void *in2, long in_bstride, void *out1, voi
     if (precision == FM_F64)
         return ks_impl<double>((const double *)in1, (const double *)in2, in_bstride, (double *)out1, (double *)out2,
                                (double2 *)work, n, batch, forward, rot_seed, rot_r0, rotate, s);
+    if (n >= 32) {  // register-resident radix-32 path (fft32.cu)
+        int st = FM_OK;
+        const float2 *tw = static_cast<const float2 *>(twiddles(n, FM_F32, s, &st));
+        if (!tw) return st;
+        return launch_ks32((const float *)in1, (const float *)in2, in_bstride, (float *)out1, (float *)out2,
+                           (float2 *)work, n, batch, forward, rot_seed, rot_r0, rotate, tw, s);
+    }
     return ks_impl<float>((const float *)in1, (const float *)in2, in_bstride, (float *)out1, (float *)out2,
                           (float2 *)work, n, batch, forward, rot_seed, rot_r0, rotate, s);
 }

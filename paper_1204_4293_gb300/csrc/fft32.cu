@@ -1,0 +1,258 @@
+// fft32.cu -- fp32 Kaiser-Squires FFT (Sec. 4.4) with register-resident
+// radix-32 sub-transforms, for n = 32 .. 8192.
+//
+// A length-n transform (n = 2^LOGN) is split into Stockham passes: radix 32,
+// then radix 32 again while needed, then one last radix RL = n / 32^k.  Each
+// thread owns 32 elements.  The first pass reads its inputs straight from
+// global memory (x[j + r n/32], coalesced over j), the last pass writes its
+// outputs straight back (X[b + r n/RL], coalesced over b), and the passes in
+// between exchange through shared memory (one slot of padding per 32
+// elements keeps the stride-32 stores conflict free).  Small DFTs run in
+// registers with constant twiddles; inter-pass twiddles come from the FP64
+// table.
+//
+//   rows_fwd32 : (gamma1 + i gamma2) [rotated for noise maps] -> row FFT
+//   cols_ks32  : column FFT -> x conj(D) (or D) -> column inverse FFT, on a
+//                strip of W columns; for n = 1024 the forward output is
+//                already in the inverse's input order, so it stays in registers
+//   rows_inv32 : row inverse FFT -> (Re, Im) * 1/n^2
+#include "common.cuh"
+#include "dft.cuh"
+#include "rng.cuh"
+
+namespace fm {
+
+__device__ __forceinline__ int pad32(int a) { return a + (a >> 5); }
+
+template <int LOGN> struct Plan32 {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int TV = N / 32;                     // threads per vector
+    static constexpr int NPASS = (LOGN + 4) / 5;          // passes (all radix 32 but the last)
+    static constexpr int LOGRL = LOGN - 5 * (NPASS - 1);  // log2 of the last radix
+    static constexpr int RL = 1 << LOGRL;
+    static constexpr int ML = 32 / RL;                    // butterflies per thread in the last pass
+    static constexpr int NSL = N / RL;                    // stride of the last pass outputs
+    // column strip width: 64 B row segments at n = 1024, >= 16 B above
+    static constexpr int W = N <= 512 ? 16 : (N >= 4096 ? 2 : 8192 / N);
+};
+
+template <bool INV> __device__ __forceinline__ float2 twid(const float2 *__restrict__ tw, int t)
+{
+    float2 w = __ldg(tw + t);
+    if (INV) w.y = -w.y;
+    return w;
+}
+
+// In: v[r] = x[j + r TV].  Out: v[m RL + r] = X[j + m TV + r NSL].
+// Element i of the vector lives at sm[pad32(i W + c)] between passes.
+// Every thread of the CTA must call this (it holds barriers).
+template <int LOGN, int W, bool INV>
+__device__ __forceinline__ void fft_vec(float2 (&v)[32], float2 *sm, int c, int j, const float2 *__restrict__ tw)
+{
+    using P = Plan32<LOGN>;
+    Dft<32, INV, float2>::run(v);  // pass 1: Ns = 1, no twiddles; outputs at 32 j + r
+    if constexpr (P::NPASS > 1) {
+        __syncthreads();  // the buffer may still be read by an earlier pass
+#pragma unroll
+        for (int r = 0; r < 32; ++r) sm[pad32((j * 32 + r) * W + c)] = v[r];
+        __syncthreads();
+        if constexpr (P::NPASS > 2) {
+            // pass 2: radix 32, Ns = 32
+            constexpr int NS = 32;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) v[r] = sm[pad32((j + r * P::TV) * W + c)];
+            const int k = j & (NS - 1);
+            const int step = k * (P::N / (NS * 32));
+#pragma unroll
+            for (int r = 1; r < 32; ++r) v[r] = cmul(v[r], twid<INV>(tw, r * step));
+            Dft<32, INV, float2>::run(v);
+            __syncthreads();
+            const int o = (j - k) * 32 + k;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) sm[pad32((o + r * NS) * W + c)] = v[r];
+            __syncthreads();
+        }
+        // last pass: radix RL, Ns = NSL, butterfly b = j + m TV (< NSL), twiddle W_n^(r b)
+#pragma unroll
+        for (int m = 0; m < P::ML; ++m) {
+            const int b = j + m * P::TV;
+#pragma unroll
+            for (int r = 0; r < P::RL; ++r) {
+                float2 x = sm[pad32((b + r * P::NSL) * W + c)];
+                if (r > 0) x = cmul(x, twid<INV>(tw, r * b));
+                v[m * P::RL + r] = x;
+            }
+            Dft<P::RL, INV, float2>::run(v + m * P::RL);
+        }
+    }
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__ in1, const float *__restrict__ in2,
+                                                       long in_bs, float2 *__restrict__ work, long total_rows,
+                                                       const float2 *__restrict__ tw, uint64_t seed, int r0,
+                                                       int rotate)
+{
+    using P = Plan32<LOGN>;
+    constexpr int RPC = P::TV >= 256 ? 1 : 256 / P::TV;
+    extern __shared__ __align__(16) float2 sm32[];
+    const int vr = threadIdx.x / P::TV, j = threadIdx.x % P::TV;
+    const long row = (long)blockIdx.x * RPC + vr;
+    float2 *sm = sm32 + vr * (P::N + P::N / 32);
+    const bool live = row < total_rows;
+    float2 v[32];
+    if (live) {
+        const long b = row >> LOGN;
+        const int y = (int)(row & (P::N - 1));
+        const float *p1 = in1 + b * in_bs + (long)y * P::N;
+        const float *p2 = in2 ? in2 + b * in_bs + (long)y * P::N : nullptr;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const int x = j + r * P::TV;
+            float a = p1[x];
+            float cc = p2 ? p2[x] : 0.f;
+            if (rotate) rotate_shear(a, cc, seed, r0 + b, y, x, P::N);
+            v[r] = make_float2(a, cc);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
+    }
+    fft_vec<LOGN, 1, false>(v, sm, 0, j, tw);
+    if (live) {
+        float2 *dst = work + row * P::N;
+#pragma unroll
+        for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+            for (int r = 0; r < P::RL; ++r) dst[j + m * P::TV + r * P::NSL] = v[m * P::RL + r];
+    }
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(256, 2) k_rows_inv32(const float2 *__restrict__ work, float *__restrict__ out1,
+                                                       float *__restrict__ out2, long total_rows,
+                                                       const float2 *__restrict__ tw, float scale)
+{
+    using P = Plan32<LOGN>;
+    constexpr int RPC = P::TV >= 256 ? 1 : 256 / P::TV;
+    extern __shared__ __align__(16) float2 sm32[];
+    const int vr = threadIdx.x / P::TV, j = threadIdx.x % P::TV;
+    const long row = (long)blockIdx.x * RPC + vr;
+    float2 *sm = sm32 + vr * (P::N + P::N / 32);
+    const bool live = row < total_rows;
+    float2 v[32];
+    const float2 *src = work + row * P::N;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = live ? src[j + r * P::TV] : make_float2(0.f, 0.f);
+    fft_vec<LOGN, 1, true>(v, sm, 0, j, tw);
+    if (live) {
+#pragma unroll
+        for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+            for (int r = 0; r < P::RL; ++r) {
+                const long pos = row * P::N + j + m * P::TV + r * P::NSL;
+                const float2 x = v[m * P::RL + r];
+                out1[pos] = x.x * scale;
+                if (out2) out2[pos] = x.y * scale;
+            }
+    }
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, const float2 *__restrict__ tw,
+                                                   int forward)
+{
+    using P = Plan32<LOGN>;
+    constexpr int W = P::W, N = P::N;
+    constexpr int STRIPS = N / W;
+    extern __shared__ __align__(16) float2 sm32[];
+    const long b = blockIdx.x / STRIPS;
+    const int x0 = (blockIdx.x % STRIPS) * W;
+    const int c = threadIdx.x % W, j = threadIdx.x / W;
+    float2 *base = work + b * (long)N * N + x0 + c;
+    float2 v[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = base[(long)(j + r * P::TV) * N];
+    fft_vec<LOGN, W, false>(v, sm32, c, j, tw);
+    // kappa_hat = conj(D) gamma_hat (inverse KS) or D kappa_hat (forward KS),
+    // D = (k1^2 - k2^2 + 2 i k1 k2) / (k1^2 + k2^2), D(0) = 0
+    const int xi = x0 + c;
+    const int k1 = xi < N / 2 ? xi : xi - N;
+#pragma unroll
+    for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+        for (int r = 0; r < P::RL; ++r) {
+            const int yi = j + m * P::TV + r * P::NSL;
+            const int k2 = yi < N / 2 ? yi : yi - N;
+            const int den = k1 * k1 + k2 * k2;
+            float2 d = make_float2(0.f, 0.f);
+            if (den != 0) {
+                const float inv = 1.f / (float)den;
+                const float im = (float)(2 * k1 * k2) * inv;
+                d = make_float2((float)(k1 * k1 - k2 * k2) * inv, forward ? im : -im);
+            }
+            v[m * P::RL + r] = cmul(v[m * P::RL + r], d);
+        }
+    if constexpr (!(P::RL == 32 || P::NPASS == 1)) {
+        // bring the spectrum back to the inverse's input order x[j + r TV]
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+            for (int r = 0; r < P::RL; ++r) sm32[pad32((j + m * P::TV + r * P::NSL) * W + c)] = v[m * P::RL + r];
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = sm32[pad32((j + r * P::TV) * W + c)];
+    }
+    fft_vec<LOGN, W, true>(v, sm32, c, j, tw);
+#pragma unroll
+    for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+        for (int r = 0; r < P::RL; ++r) base[(long)(j + m * P::TV + r * P::NSL) * N] = v[m * P::RL + r];
+}
+
+// ---------------------------------------------------------------------------
+template <int LOGN>
+static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int batch,
+                     bool forward, uint64_t seed, int r0, bool rotate, const float2 *tw, cudaStream_t s)
+{
+    using P = Plan32<LOGN>;
+    constexpr int RPC = P::TV >= 256 ? 1 : 256 / P::TV;
+    const long total_rows = (long)batch * P::N;
+    const unsigned row_grid = (unsigned)((total_rows + RPC - 1) / RPC);
+    const size_t row_smem = P::NPASS > 1 ? (size_t)RPC * (P::N + P::N / 32) * sizeof(float2) : 0;
+    const int col_threads = P::W * P::TV;
+    const size_t col_smem = P::NPASS > 1 ? (size_t)(P::N * P::W + P::N * P::W / 32 + 1) * sizeof(float2) : 0;
+    const unsigned col_grid = (unsigned)((long)batch * (P::N / P::W));
+    FM_CUDA_TRY(cudaFuncSetAttribute(k_rows_fwd32<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));
+    FM_CUDA_TRY(cudaFuncSetAttribute(k_rows_inv32<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));
+    FM_CUDA_TRY(cudaFuncSetAttribute(k_cols_ks32<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem));
+    FM_LAUNCH(FM_K_FFT_ROWS_FWD, k_rows_fwd32<LOGN>, row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs, work,
+              total_rows, tw, seed, r0, rotate ? 1 : 0);
+    FM_LAUNCH(FM_K_FFT_COLS_KS, k_cols_ks32<LOGN>, col_grid, col_threads, col_smem, s, work, tw, forward ? 1 : 0);
+    const float scale = 1.f / ((float)P::N * (float)P::N);
+    FM_LAUNCH(FM_K_FFT_ROWS_INV, k_rows_inv32<LOGN>, row_grid, RPC * P::TV, row_smem, s, work, out1, out2,
+              total_rows, tw, scale);
+    return FM_OK;
+}
+
+// n = 32 .. 8192 (power of two); other sizes return FM_EINVAL to the caller,
+// which then uses the generic shared-memory Stockham kernels.
+int launch_ks32(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int n,
+                int batch, bool forward, uint64_t seed, int r0, bool rotate, const float2 *tw, cudaStream_t s)
+{
+    switch (n) {
+    case 32: return ks32_impl<5>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
+    case 64: return ks32_impl<6>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
+    case 128: return ks32_impl<7>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
+    case 256: return ks32_impl<8>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
+    case 512: return ks32_impl<9>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
+    case 1024: return ks32_impl<10>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
+    case 2048: return ks32_impl<11>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
+    case 4096: return ks32_impl<12>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
+    case 8192: return ks32_impl<13>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
+    }
+    return FM_EINVAL;
+}
+
+}  // namespace fm

@@ -120,6 +120,12 @@ __global__ void __launch_bounds__(NW * 32) k_map_direct(const T *__restrict__ g1
             }
         }
         if (dxm >= 0) {
+            // two-level sum: this input row's taps first, then into the total
+            T part[RY][CX];
+#pragma unroll
+            for (int k = 0; k < RY; ++k)
+#pragma unroll
+                for (int o = 0; o < CX; ++o) part[k][o] = (T)0;
             for (int dx0 = -dxm; dx0 <= dxm; dx0 += 8) {
                 T w1[CX + 7], w2[CX + 7];
                 const int base = lc + dx0 + Ri;
@@ -137,12 +143,16 @@ __global__ void __launch_bounds__(NW * 32) k_map_direct(const T *__restrict__ g1
                         const V ab = __ldg(trow + t);
 #pragma unroll
                         for (int o = 0; o < CX; ++o) {
-                            acc[k][o] = fma(ab.x, w1[o + t], acc[k][o]);
-                            acc[k][o] = fma(ab.y, w2[o + t], acc[k][o]);
+                            part[k][o] = fma(ab.x, w1[o + t], part[k][o]);
+                            part[k][o] = fma(ab.y, w2[o + t], part[k][o]);
                         }
                     }
                 }
             }
+#pragma unroll
+            for (int k = 0; k < RY; ++k)
+#pragma unroll
+                for (int o = 0; o < CX; ++o) acc[k][o] += part[k][o];
         }
     }
 #pragma unroll

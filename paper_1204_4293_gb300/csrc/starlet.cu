@@ -39,125 +39,261 @@ __device__ __forceinline__ void acc_band(double *s1, double *s2, long i, double 
     }
 }
 
-// ---------------------------------------------------------------------------
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long in_bs, T *__restrict__ w_out, long w_bs,
-                                                 long w_ss, T *__restrict__ c_out, long c_bs, int n, int j0, int j1,
-                                                 int boundary, int tiles_x, int tiles_per_map, double *__restrict__ acc1,
-                                                 double *__restrict__ acc2, int acc_atomic)
+// 16-byte vectors: 4 floats or 2 doubles
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+    static constexpr int W = 4;
+    using V = float4;
+};
+template <> struct Vec16<double> {
+    static constexpr int W = 2;
+    using V = double2;
+};
+
+template <typename T> __device__ __forceinline__ void ld16(T (&d)[16 / sizeof(T)], const T *p)
 {
+    using V = typename Vec16<T>::V;
+    *reinterpret_cast<V *>(d) = *reinterpret_cast<const V *>(p);
+}
+template <typename T> __device__ __forceinline__ void st16(T *p, const T (&d)[16 / sizeof(T)])
+{
+    using V = typename Vec16<T>::V;
+    *reinterpret_cast<V *>(p) = *reinterpret_cast<const V *>(d);
+}
+
+// Store (or, in noise mode, accumulate) VW consecutive band values at
+// global pixel (gy, gx..gx+VW-1) of band `band` (1-based).
+template <typename T>
+__device__ __forceinline__ void emit_band(const T (&w)[16 / sizeof(T)], T *dst, long px, int gy, int gx, int n,
+                                          bool vec_ok, double *acc1, double *acc2, long acc_off, bool atomic)
+{
+    constexpr int VW = 16 / sizeof(T);
+    if (gy >= n) return;
+    if (acc1) {
+#pragma unroll
+        for (int t = 0; t < VW; ++t)
+            if (gx + t < n) acc_band(acc1, acc2, acc_off + px + t, (double)w[t], atomic);
+        return;
+    }
+    if (vec_ok && gx + VW <= n) {
+        st16(dst + px, w);
+    } else {
+#pragma unroll
+        for (int t = 0; t < VW; ++t)
+            if (gx + t < n) dst[px + t] = w[t];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Scales 1..F fused on a TS x TS output tile.  Shared memory holds the tile
+// with a halo of HP >= sum_{j<=F} 2^j pixels (rounded up to 4) per side,
+// twice: A = c_{j-1} (then c_j), B = rows-filtered c_{j-1}.  Each thread
+// works on VW adjacent pixels with 16-byte shared-memory accesses.
+template <typename T, int F, int TS>
+__global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long in_bs, T *__restrict__ w_out, long w_bs,
+                                                 long w_ss, T *__restrict__ c_out, long c_bs, int n, int boundary,
+                                                 int tiles_x, int tiles_per_map, double *__restrict__ acc1,
+                                                 double *__restrict__ acc2, int acc_atomic, int vec_ok)
+{
+    constexpr int VW = 16 / sizeof(T);
+    constexpr int H = (1 << (F + 1)) - 2;
+    constexpr int HP = ((H + 3) / 4) * 4;
+    constexpr int P = TS + 2 * HP;
+    constexpr int NQ = P / VW;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *A = reinterpret_cast<T *>(smem_raw);
-    const int H = (1 << (j1 + 1)) - (1 << j0);  // sum_{j=j0..j1} 2^j
-    const int P = TX + 2 * H;
-    const int rows = TY + 2 * H;
-    T *Bf = A + rows * P;
+    T *Bf = A + P * P;
     const long b = blockIdx.x / tiles_per_map;
-    const int t = blockIdx.x % tiles_per_map;
-    const int ty0 = (t / tiles_x) * TY;
-    const int tx0 = (t % tiles_x) * TX;
+    const int t = blockIdx.x - (int)(b * tiles_per_map);
+    const int ty0 = (t / tiles_x) * TS;
+    const int tx0 = (t % tiles_x) * TS;
     const T *src = in + b * in_bs;
     const long nn = (long)n * n;
+    const bool vok = vec_ok != 0;
 
-    for (int idx = threadIdx.x; idx < rows * P; idx += blockDim.x) {
-        const int i = idx / P, k = idx - (idx / P) * P;
-        const int gy = fold_index(ty0 - H + i, n, boundary);
-        const int gx = fold_index(tx0 - H + k, n, boundary);
-        A[idx] = src[(long)gy * n + gx];
+    for (int e = threadIdx.x; e < P * NQ; e += blockDim.x) {
+        const int i = e / NQ, q = e % NQ;
+        const int gy = fold_index(ty0 - HP + i, n, boundary);
+        const int gx0 = tx0 - HP + q * VW;
+        const T *rowp = src + (long)gy * n;
+        T v[VW];
+        if (vok && gx0 >= 0 && gx0 + VW <= n) {
+            ld16(v, rowp + gx0);
+        } else {
+#pragma unroll
+            for (int u = 0; u < VW; ++u) v[u] = rowp[fold_index(gx0 + u, n, boundary)];
+        }
+        st16(A + i * P + q * VW, v);
     }
     __syncthreads();
 
-    int halo = H;
-    for (int j = j0; j <= j1; ++j) {
+#pragma unroll
+    for (int j = 1; j <= F; ++j) {
         const int s = 1 << (j - 1);
-        const int halo2 = halo - 2 * s;
-        // rows pass on every still-valid row, narrowing the columns by 2s
+        const int hb = (1 << (F + 1)) - (1 << j);        // halo still valid before scale j
+        const int ha = (1 << (F + 1)) - (1 << (j + 1));  // after
+        const int ncq = (TS + 2 * ha) / VW;
+        // rows pass
         {
-            const int r_lo = H - halo, nr = TY + 2 * halo;
-            const int c_lo = H - halo2, nc = TX + 2 * halo2;
-            for (int idx = threadIdx.x; idx < nr * nc; idx += blockDim.x) {
-                const int i = r_lo + idx / nc, k = c_lo + idx % nc;
-                const T *a = A + i * P + k;
-                Bf[i * P + k] = B3<T>::apply(a[-2 * s], a[-s], a[0], a[s], a[2 * s]);
-            }
-        }
-        __syncthreads();
-        // columns pass, band output, and c_j written back over c_{j-1}
-        {
-            const int lo = H - halo2, nr = TY + 2 * halo2, nc = TX + 2 * halo2;
-            const int sp = s * P;
-            for (int idx = threadIdx.x; idx < nr * nc; idx += blockDim.x) {
-                const int i = lo + idx / nc, k = lo + idx % nc;
-                const T *bp = Bf + i * P + k;
-                const T c = B3<T>::apply(bp[-2 * sp], bp[-sp], bp[0], bp[sp], bp[2 * sp]);
-                const int oi = i - H, ok = k - H;
-                if (oi >= 0 && oi < TY && ok >= 0 && ok < TX) {
-                    const int gy = ty0 + oi, gx = tx0 + ok;
-                    if (gy < n && gx < n) {
-                        const T w = A[i * P + k] - c;
-                        const long px = (long)gy * n + gx;
-                        if (acc1)
-                            acc_band(acc1, acc2, (long)(j - 1) * nn + px, (double)w, acc_atomic != 0);
-                        else
-                            w_out[b * w_bs + (long)(j - j0) * w_ss + px] = w;
-                    }
+            const int nr = TS + 2 * hb;
+            for (int e = threadIdx.x; e < nr * ncq; e += blockDim.x) {
+                const int i = HP - hb + e / ncq;
+                const int x = HP - ha + (e % ncq) * VW;
+                const T *row = A + i * P;
+                T o[VW];
+                if (2 * s <= VW) {
+                    T win[3 * VW];
+                    T *wp = win;
+                    ld16(*reinterpret_cast<T(*)[VW]>(wp), row + x - VW);
+                    ld16(*reinterpret_cast<T(*)[VW]>(wp + VW), row + x);
+                    ld16(*reinterpret_cast<T(*)[VW]>(wp + 2 * VW), row + x + VW);
+#pragma unroll
+                    for (int u = 0; u < VW; ++u)
+                        o[u] = B3<T>::apply(win[VW + u - 2 * s], win[VW + u - s], win[VW + u], win[VW + u + s],
+                                            win[VW + u + 2 * s]);
+                } else {
+                    T m2[VW], m1[VW], c0[VW], p1[VW], p2[VW];
+                    ld16(m2, row + x - 2 * s);
+                    ld16(m1, row + x - s);
+                    ld16(c0, row + x);
+                    ld16(p1, row + x + s);
+                    ld16(p2, row + x + 2 * s);
+#pragma unroll
+                    for (int u = 0; u < VW; ++u) o[u] = B3<T>::apply(m2[u], m1[u], c0[u], p1[u], p2[u]);
                 }
-                A[i * P + k] = c;
+                st16(Bf + i * P + x, o);
             }
         }
         __syncthreads();
-        halo = halo2;
-    }
-    if (c_out) {
-        for (int idx = threadIdx.x; idx < TX * TY; idx += blockDim.x) {
-            const int oi = idx / TX, ok = idx % TX;
-            const int gy = ty0 + oi, gx = tx0 + ok;
-            if (gy < n && gx < n) c_out[b * c_bs + (long)gy * n + gx] = A[(H + oi) * P + H + ok];
+        // columns pass, band output, c_j over c_{j-1}
+        {
+            const int nr = TS + 2 * ha;
+            for (int e = threadIdx.x; e < nr * ncq; e += blockDim.x) {
+                const int i = HP - ha + e / ncq;
+                const int x = HP - ha + (e % ncq) * VW;
+                const T *bp = Bf + i * P + x;
+                T m2[VW], m1[VW], c0[VW], p1[VW], p2[VW], cj[VW], prev[VW], w[VW];
+                ld16(m2, bp - 2 * s * P);
+                ld16(m1, bp - s * P);
+                ld16(c0, bp);
+                ld16(p1, bp + s * P);
+                ld16(p2, bp + 2 * s * P);
+                ld16(prev, A + i * P + x);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) {
+                    cj[u] = B3<T>::apply(m2[u], m1[u], c0[u], p1[u], p2[u]);
+                    w[u] = prev[u] - cj[u];
+                }
+                const int oi = i - HP, ox = x - HP;
+                if (oi >= 0 && oi < TS && ox >= 0 && ox < TS) {
+                    const int gy = ty0 + oi, gx = tx0 + ox;
+                    const long px = (long)gy * n + gx;
+                    emit_band<T>(w, w_out + b * w_bs + (long)(j - 1) * w_ss, px, gy, gx, n, vok, acc1, acc2,
+                                 (long)(j - 1) * nn, acc_atomic != 0);
+                    if (j == F && c_out) emit_band<T>(cj, c_out + b * c_bs, px, gy, gx, n, vok, nullptr, nullptr, 0, false);
+                }
+                if (j < F) st16(A + i * P + x, cj);
+            }
         }
+        if (j < F) __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
+// One large scale, rows: r = rows-filtered c (taps +-s, +-2s), VW pixels per
+// thread.  grid = (ceil(n / (128 VW)), n, batch).
 template <typename T>
-__global__ void __launch_bounds__(256) k_st_row(const T *__restrict__ c, long c_bs, T *__restrict__ r, int n, int s,
-                                                int boundary, long total)
+__global__ void __launch_bounds__(128) k_st_row(const T *__restrict__ c, long c_bs, T *__restrict__ r, int n, int s,
+                                                int boundary, int vec_ok)
 {
-    const long nn = (long)n * n;
-    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
-        const long b = g / nn;
-        const long p = g - b * nn;
-        const int y = (int)(p / n), x = (int)(p - (long)y * n);
-        const T *row = c + b * c_bs + (long)y * n;
-        const T v = B3<T>::apply(__ldg(row + fold_index(x - 2 * s, n, boundary)),
-                                 __ldg(row + fold_index(x - s, n, boundary)), __ldg(row + x),
-                                 __ldg(row + fold_index(x + s, n, boundary)),
-                                 __ldg(row + fold_index(x + 2 * s, n, boundary)));
-        r[g] = v;
+    constexpr int VW = 16 / sizeof(T);
+    const int x = (blockIdx.x * blockDim.x + threadIdx.x) * VW;
+    if (x >= n) return;
+    const int y = blockIdx.y;
+    const long b = blockIdx.z;
+    const T *row = c + b * c_bs + (long)y * n;
+    T *dst = r + (b * n + y) * (long)n;
+    T o[VW];
+    if (vec_ok && s % VW == 0 && x - 2 * s >= 0 && x + VW + 2 * s <= n) {
+        T m2[VW], m1[VW], c0[VW], p1[VW], p2[VW];
+        ld16(m2, row + x - 2 * s);
+        ld16(m1, row + x - s);
+        ld16(c0, row + x);
+        ld16(p1, row + x + s);
+        ld16(p2, row + x + 2 * s);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) o[u] = B3<T>::apply(m2[u], m1[u], c0[u], p1[u], p2[u]);
+    } else {
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+            const int xx = x + u < n ? x + u : n - 1;
+            o[u] = B3<T>::apply(row[fold_index(xx - 2 * s, n, boundary)], row[fold_index(xx - s, n, boundary)],
+                                row[xx], row[fold_index(xx + s, n, boundary)],
+                                row[fold_index(xx + 2 * s, n, boundary)]);
+        }
+    }
+    if (vec_ok && x + VW <= n) {
+        st16(dst + x, o);
+    } else {
+#pragma unroll
+        for (int u = 0; u < VW; ++u)
+            if (x + u < n) dst[x + u] = o[u];
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_st_col(const T *__restrict__ r, const T *c_prev, long prev_bs, T *c_next,
+// One large scale, columns: thread owns VW adjacent columns and KR rows at
+// stride s (rows r0 + s (m KR + k)), so its five taps slide down a register
+// window: KR + 4 row loads for KR outputs.  c_j = column-filtered r,
+// w_j = c_{j-1} - c_j, c_j written over c_{j-1} when they alias.
+// grid = (ceil(n / (128 VW)), s * ceil(n / (s KR)), batch).
+template <typename T, int KR>
+__global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T *c_prev, long prev_bs, T *c_next,
                                                 long next_bs, T *__restrict__ w_out, long w_bs, int n, int s,
-                                                int boundary, long total, int band, double *__restrict__ acc1,
-                                                double *__restrict__ acc2, int acc_atomic)
+                                                int boundary, int band, double *__restrict__ acc1,
+                                                double *__restrict__ acc2, int acc_atomic, int vec_ok)
 {
+    constexpr int VW = 16 / sizeof(T);
+    const int x = (blockIdx.x * blockDim.x + threadIdx.x) * VW;
+    if (x >= n) return;
+    const int r0 = blockIdx.y % s, m = blockIdx.y / s;
+    const long b = blockIdx.z;
     const long nn = (long)n * n;
-    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < total; g += (long)gridDim.x * blockDim.x) {
-        const long b = g / nn;
-        const long p = g - b * nn;
-        const int y = (int)(p / n), x = (int)(p - (long)y * n);
-        const T *col = r + b * nn + x;
-        const T c = B3<T>::apply(__ldg(col + (long)fold_index(y - 2 * s, n, boundary) * n),
-                                 __ldg(col + (long)fold_index(y - s, n, boundary) * n), __ldg(col + (long)y * n),
-                                 __ldg(col + (long)fold_index(y + s, n, boundary) * n),
-                                 __ldg(col + (long)fold_index(y + 2 * s, n, boundary) * n));
-        const T w = c_prev[b * prev_bs + p] - c;
-        if (acc1)
-            acc_band(acc1, acc2, (long)(band - 1) * nn + p, (double)w, acc_atomic != 0);
-        else
-            w_out[b * w_bs + p] = w;
-        if (c_next) c_next[b * next_bs + p] = c;
+    const bool vok = vec_ok && x + VW <= n;
+    const T *rb = r + b * nn;
+    auto load_row = [&](int yy, T (&d)[VW]) {
+        const T *p = rb + (long)fold_index(yy, n, boundary) * n;
+        if (vok) {
+            ld16(d, p + x);
+        } else {
+#pragma unroll
+            for (int u = 0; u < VW; ++u) d[u] = p[x + u < n ? x + u : n - 1];
+        }
+    };
+    T win[5][VW];
+    const int ybase = r0 + s * (m * KR);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) load_row(ybase + (u - 2) * s, win[u]);
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+        const int y = ybase + k * s;
+        if (y >= n) break;
+        load_row(y + 2 * s, win[(k + 4) % 5]);
+        T cj[VW], prev[VW], w[VW];
+        const long px = (long)y * n + x;
+        if (vok) {
+            ld16(prev, c_prev + b * prev_bs + px);
+        } else {
+#pragma unroll
+            for (int u = 0; u < VW; ++u) prev[u] = x + u < n ? c_prev[b * prev_bs + px + u] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+            cj[u] = B3<T>::apply(win[k % 5][u], win[(k + 1) % 5][u], win[(k + 2) % 5][u], win[(k + 3) % 5][u],
+                                 win[(k + 4) % 5][u]);
+            w[u] = prev[u] - cj[u];
+        }
+        emit_band<T>(w, w_out + b * w_bs, px, y, x, n, vok, acc1, acc2, (long)(band - 1) * nn, acc_atomic != 0);
+        if (c_next) emit_band<T>(cj, c_next + b * next_bs, px, y, x, n, vok, nullptr, nullptr, 0, false);
     }
 }
 
@@ -168,13 +304,9 @@ static int auto_fuse(int J, const fm_config &cfg)
 {
     if (cfg.fuse_depth < 0) return 0;
     int f = cfg.fuse_depth == 0 ? 3 : cfg.fuse_depth;
+    const int fmax = cfg.precision == FM_F64 ? 3 : 4;  // tile + halo must fit shared memory
+    if (f > fmax) f = fmax;
     if (f > J - 1) f = J - 1;
-    const size_t es = cfg.precision == FM_F64 ? 8 : 4;
-    while (f > 1) {
-        const size_t side = 32 + 2 * ((1u << (f + 1)) - 2);
-        if (2 * side * side * es <= 200 * 1024) break;
-        --f;
-    }
     return f;
 }
 
@@ -185,32 +317,46 @@ size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg)
     return 2ull * (size_t)batch * n * n;
 }
 
-template <typename T, int TS>
-static int tile_launch(const T *in, long in_bs, T *w_out, long w_bs, long w_ss, T *c_out, long c_bs, int n, int j0,
-                       int j1, int boundary, int batch, double *acc1, double *acc2, cudaStream_t s)
+template <typename T, int F, int TS>
+static int tile_launch(const T *in, T *w_out, long w_bs, long w_ss, T *c_out, long c_bs, int n, int boundary,
+                       int batch, double *acc1, double *acc2, bool vec_ok, cudaStream_t s)
 {
-    const int H = (1 << (j1 + 1)) - (1 << j0);
-    const size_t smem = 2ull * (TS + 2 * H) * (TS + 2 * H) * sizeof(T);
+    constexpr int H = (1 << (F + 1)) - 2;
+    constexpr int HP = ((H + 3) / 4) * 4;
+    constexpr int P = TS + 2 * HP;
+    const size_t smem = 2ull * P * P * sizeof(T);
     const int tiles_x = (n + TS - 1) / TS;
     const int tiles_per_map = tiles_x * tiles_x;
-    auto k = k_st_tile<T, TS, TS>;
+    auto k = k_st_tile<T, F, TS>;
     FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    FM_LAUNCH(FM_K_STARLET_TILE, k, (unsigned)(tiles_per_map * (long)batch), 256, smem, s, in, in_bs, w_out, w_bs,
-              w_ss, c_out, c_bs, n, j0, j1, boundary, tiles_x, tiles_per_map, acc1, acc2, batch > 1 ? 1 : 0);
+    FM_LAUNCH(FM_K_STARLET_TILE, k, (unsigned)(tiles_per_map * (long)batch), 256, smem, s, in, (long)n * n, w_out,
+              w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, acc1, acc2, batch > 1 ? 1 : 0,
+              vec_ok ? 1 : 0);
     return FM_OK;
 }
 
-static unsigned grid_for(long total)
+template <typename T>
+static int tile_dispatch(int f, const T *in, T *w_out, long w_bs, long w_ss, T *c_out, long c_bs, int n,
+                         int boundary, int batch, double *acc1, double *acc2, bool vec_ok, cudaStream_t s)
 {
-    long g = (total + 255) / 256;
-    const long cap = 152L * 16;
-    return (unsigned)(g < cap ? g : cap);
+    constexpr int TS = sizeof(T) == 4 ? 64 : 32;
+    switch (f) {
+    case 1: return tile_launch<T, 1, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
+    case 2: return tile_launch<T, 2, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
+    case 3: return tile_launch<T, 3, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
+    case 4: return tile_launch<T, 4, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
+    }
+    return FM_EINVAL;
 }
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 template <typename T>
 static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int batch, const fm_config &cfg,
                         T *scratch, double *acc1, double *acc2, cudaStream_t s)
 {
+    constexpr int VW = 16 / sizeof(T);
+    constexpr int KR = 8;
     const long nn = (long)n * n;
     const int f = auto_fuse(J, cfg);
     const int bnd = cfg.boundary;
@@ -218,26 +364,25 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
     T *Bb = scratch ? scratch + (long)batch * nn : nullptr;
     const bool noise = acc1 != nullptr;
     T *last = noise ? nullptr : pyr + (long)(J - 1) * nn;  // slot of the smooth array
+    const bool vec_ok = n % VW == 0 && aligned16(kappa) && (noise || aligned16(pyr)) && (!scratch || aligned16(scratch));
     if (f >= 1) {
         T *c_out = f == J - 1 ? last : A;
         const long c_bs = f == J - 1 ? pyr_bs : nn;
-        const int H = (1 << (f + 1)) - 2;
-        const size_t smem64 = 2ull * (64 + 2 * H) * (64 + 2 * H) * sizeof(T);
-        int st = smem64 <= 200 * 1024
-                     ? tile_launch<T, 64>(kappa, nn, pyr, pyr_bs, nn, c_out, c_bs, n, 1, f, bnd, batch, acc1, acc2, s)
-                     : tile_launch<T, 32>(kappa, nn, pyr, pyr_bs, nn, c_out, c_bs, n, 1, f, bnd, batch, acc1, acc2, s);
+        int st = tile_dispatch<T>(f, kappa, pyr, pyr_bs, nn, c_out, c_bs, n, bnd, batch, acc1, acc2, vec_ok, s);
         if (st != FM_OK) return st;
     }
-    const long total = (long)batch * nn;
+    const unsigned gx = (unsigned)((n + 128 * VW - 1) / (128 * VW));
     for (int j = f + 1; j <= J - 1; ++j) {
         const int sp = 1 << (j - 1);
         const T *c_prev = j == 1 ? kappa : A;
         T *c_next = j == J - 1 ? last : A;
         const long next_bs = j == J - 1 ? pyr_bs : nn;
-        FM_LAUNCH(FM_K_STARLET_ROW, k_st_row<T>, grid_for(total), 256, 0, s, c_prev, nn, Bb, n, sp, bnd, total);
-        FM_LAUNCH(FM_K_STARLET_COL, k_st_col<T>, grid_for(total), 256, 0, s, Bb, c_prev, nn, c_next, next_bs,
-                  noise ? nullptr : pyr + (long)(j - 1) * nn, pyr_bs, n, sp, bnd, total, j, acc1, acc2,
-                  batch > 1 ? 1 : 0);
+        FM_LAUNCH(FM_K_STARLET_ROW, k_st_row<T>, dim3(gx, n, batch), 128, 0, s, c_prev, nn, Bb, n, sp, bnd,
+                  vec_ok ? 1 : 0);
+        const unsigned gy = (unsigned)(sp * ((((n + sp - 1) / sp) + KR - 1) / KR));
+        FM_LAUNCH(FM_K_STARLET_COL, (k_st_col<T, KR>), dim3(gx, gy, batch), 128, 0, s, Bb, c_prev, nn, c_next,
+                  next_bs, noise ? nullptr : pyr + (long)(j - 1) * nn, pyr_bs, n, sp, bnd, j, acc1, acc2,
+                  batch > 1 ? 1 : 0, vec_ok ? 1 : 0);
     }
     return FM_OK;
 }

@@ -21,7 +21,8 @@ def _fm():
                                           (1, 16.0, 96), (2, 2.0, 50), (3, 3.0, 33), (0, 1.0, 5)])
 def test_map_direct_matches_oracle(filt, theta, n, dtype):
     fm = _fm()
-    g1, g2 = shear(max(n, 8), seed=int(theta) + n, dtype=dtype)
+    side = 1 << max(3, (n - 1).bit_length())  # shear is made on a power-of-two grid, then cropped
+    g1, g2 = shear(side, seed=int(theta) + n, dtype=dtype)
     g1, g2 = np.ascontiguousarray(g1[:n, :n]), np.ascontiguousarray(g2[:n, :n])
     m = fm.fm_map_direct(torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda(), filt, theta).cpu().numpy()
     ref = oracle.map_direct(g1.astype(np.float64), g2.astype(np.float64), filt, theta)
@@ -30,7 +31,8 @@ def test_map_direct_matches_oracle(filt, theta, n, dtype):
 
 def test_map_direct_cut_override_and_ell():
     fm = _fm()
-    g1, g2 = shear(48, seed=3, dtype=np.float32)
+    g1, g2 = shear(64, seed=3, dtype=np.float32)
+    g1, g2 = np.ascontiguousarray(g1[:48, :48]), np.ascontiguousarray(g2[:48, :48])
     m = fm.fm_map_direct(torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda(), 1, 6.0, ell=1,
                          cut_over_theta=0.5).cpu().numpy()
     ref = oracle.map_direct(g1.astype(np.float64), g2.astype(np.float64), 1, 6.0, ell=1, cut_over_theta=0.5)
