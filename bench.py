@@ -35,20 +35,25 @@ METRIC = "starlet Map Mpix*scales/s, batched FP32 vs plain FP64 (<=1e-5 err); %H
 UNIT = "Mpix*scales/s"
 L2_BYTES = 129 * 2 ** 20
 
-# Algorithmic HBM bytes per pixel of one launch, fp32 (x2 for fp64):
-# FFT passes read and write complex maps; the KS row passes read / write the
-# real maps; the fused starlet tile reads kappa once and writes f bands + c_f.
-ALGO_BYTES_PER_PX = {
-    "fft_rows_fwd": 8 + 8,
-    "fft_cols_ks": 8 + 8,
-    "fft_rows_inv": 8 + 4,
-    "starlet_row": 4 + 4,
-    "starlet_col": 4 + 4 + 4 + 4,
-}
+FUSE = 3  # starlet scales done by the fused tile kernel (library default)
 
 
-def starlet_tile_bytes_per_px(fuse):
-    return 4 + 4 * fuse + 4
+def algo_bytes_per_px(kernel, J, fuse=FUSE):
+    """Algorithmic bytes per pixel of one launch (fp32): what the kernel must
+    read and write once.  FFT passes move complex maps; the KS row passes the
+    real shear / convergence; the tile kernel reads kappa and writes f bands +
+    c_f; the large-scale row kernel reads c_f and writes one row-filtered map
+    per large scale (K = J-1-f); the column-strip kernel reads c_f and those K
+    maps and writes K bands + the smooth array."""
+    K = J - 1 - fuse
+    return {
+        "fft_rows_fwd": 8 + 8,
+        "fft_cols_ks": 8 + 8,
+        "fft_rows_inv": 8 + 4,
+        "starlet_tile": 4 + 4 * fuse + 4,
+        "starlet_row": 4 + 4 * K,
+        "starlet_col": 4 + 4 * K + 4 * K + 4,
+    }[kernel]
 
 
 # ---------------------------------------------------------------------------
@@ -354,7 +359,7 @@ def main():
     if rank == 0:
         peak, peak_src = load_peaks()
         px_per_launch = n * n * B
-        bpp = starlet_tile_bytes_per_px(3) if dom == "starlet_tile" else ALGO_BYTES_PER_PX[dom]
+        bpp = algo_bytes_per_px(dom, J)
         dom_avg_ms = dom_ms / max(dom_cnt, 1)
         achieved = bpp * px_per_launch / (dom_avg_ms * 1e-3) / 1e9
         trf = ncu_traffic(dom)

@@ -298,6 +298,151 @@ __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T
 }
 
 // ---------------------------------------------------------------------------
+// Large scales a+1..b in two passes.  The row filters X_j and the column
+// filters Y_j act on different axes and commute, so
+//   c_{a+k} = Y_{a+k} ... Y_{a+1} u_{a+k},  u_{a+k} = X_{a+k} ... X_{a+1} c_a.
+// k_st_rows_multi makes every u_{a+k} from full rows of c_a held in shared
+// memory (no halo: the row edge folds inside the row); k_st_cols_multi then
+// holds full-height strips of W columns, applies the column filters, and
+// writes w_{a+k} = c_{a+k-1} - c_{a+k} and the smooth array.
+
+// one CTA per row; u_out[k] = X_{a+k} ... X_{a+1} c_a (rows), k = 1..K
+template <typename T>
+__global__ void __launch_bounds__(256) k_st_rows_multi(const T *__restrict__ c, long c_bs, T *__restrict__ u_out,
+                                                       long u_ks, int n, int a, int K, int boundary)
+{
+    constexpr int VW = 16 / sizeof(T);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf0 = reinterpret_cast<T *>(smem_raw);
+    T *buf1 = buf0 + n;
+    const long b = blockIdx.y;
+    const int y = blockIdx.x;
+    const T *src = c + b * c_bs + (long)y * n;
+    const long roff = (b * n + y) * (long)n;
+    for (int x = threadIdx.x * VW; x < n; x += blockDim.x * VW) {
+        T v[VW];
+        ld16(v, src + x);
+        st16(buf0 + x, v);
+    }
+    __syncthreads();
+    T *in = buf0, *out = buf1;
+    for (int k = 1; k <= K; ++k) {
+        const int s = 1 << (a + k - 1);
+        T *dst = u_out + (long)(k - 1) * u_ks + roff;
+        for (int x = threadIdx.x * VW; x < n; x += blockDim.x * VW) {
+            T o[VW];
+            if (x - 2 * s >= 0 && x + VW + 2 * s <= n) {
+                T m2[VW], m1[VW], c0[VW], p1[VW], p2[VW];
+                ld16(m2, in + x - 2 * s);
+                ld16(m1, in + x - s);
+                ld16(c0, in + x);
+                ld16(p1, in + x + s);
+                ld16(p2, in + x + 2 * s);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) o[u] = B3<T>::apply(m2[u], m1[u], c0[u], p1[u], p2[u]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < VW; ++u) {
+                    const int xx = x + u;
+                    o[u] = B3<T>::apply(in[fold_index(xx - 2 * s, n, boundary)], in[fold_index(xx - s, n, boundary)],
+                                        in[xx], in[fold_index(xx + s, n, boundary)],
+                                        in[fold_index(xx + 2 * s, n, boundary)]);
+                }
+            }
+            st16(out + x, o);
+            st16(dst + x, o);
+        }
+        __syncthreads();
+        T *t = in;
+        in = out;
+        out = t;
+    }
+}
+
+// one CTA per strip of W columns x n rows, n * (W / VW) / NR threads; a thread
+// owns VW adjacent columns of the NR rows y = ty + m n / NR.
+template <typename T, int W, int NR>
+__global__ void __launch_bounds__(512) k_st_cols_multi(const T *__restrict__ c_a, long ca_bs,
+                                                       const T *__restrict__ u_in, long u_ks, T *__restrict__ w_out,
+                                                       long w_bs, long w_ss, T *__restrict__ c_out, long c_bs, int n,
+                                                       int a, int K, int boundary, double *__restrict__ acc1,
+                                                       double *__restrict__ acc2, int acc_atomic)
+{
+    constexpr int VW = 16 / sizeof(T);
+    constexpr int QW = W / VW;  // vectors per row of the strip
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *bufA = reinterpret_cast<T *>(smem_raw);
+    T *bufB = bufA + (long)n * W;
+    const int strips = n / W;
+    const long b = blockIdx.x / strips;
+    const int x0 = (blockIdx.x % strips) * W;
+    const int q = threadIdx.x % QW;
+    const int ty = threadIdx.x / QW;
+    const int rstep = n / NR;
+    const long nn = (long)n * n;
+    const int xs = x0 + q * VW;
+
+    T prev[NR][VW];  // c_{a+k-1} at the thread's pixels
+#pragma unroll
+    for (int m = 0; m < NR; ++m) ld16(prev[m], c_a + b * ca_bs + (long)(ty + m * rstep) * n + xs);
+
+    for (int k = 1; k <= K; ++k) {
+        const T *u = u_in + (long)(k - 1) * u_ks + b * nn;
+        for (int e = threadIdx.x; e < n * QW; e += blockDim.x) {
+            const int yy = e / QW, qq = e % QW;
+            T v[VW];
+            ld16(v, u + (long)yy * n + x0 + qq * VW);
+            st16(bufA + yy * W + qq * VW, v);
+        }
+        __syncthreads();
+        T *in = bufA, *out = bufB;
+        for (int p = 1; p <= k; ++p) {
+            const int s = 1 << (a + p - 1);
+            for (int e = threadIdx.x; e < n * QW; e += blockDim.x) {
+                const int yy = e / QW, qq = e % QW;
+                T m2[VW], m1[VW], c0[VW], p1[VW], p2[VW], o[VW];
+                ld16(m2, in + fold_index(yy - 2 * s, n, boundary) * W + qq * VW);
+                ld16(m1, in + fold_index(yy - s, n, boundary) * W + qq * VW);
+                ld16(c0, in + yy * W + qq * VW);
+                ld16(p1, in + fold_index(yy + s, n, boundary) * W + qq * VW);
+                ld16(p2, in + fold_index(yy + 2 * s, n, boundary) * W + qq * VW);
+#pragma unroll
+                for (int uu = 0; uu < VW; ++uu) o[uu] = B3<T>::apply(m2[uu], m1[uu], c0[uu], p1[uu], p2[uu]);
+                st16(out + yy * W + qq * VW, o);
+            }
+            __syncthreads();
+            T *t = in;
+            in = out;
+            out = t;
+        }
+        // in = c_{a+k} on the strip
+        const int band = a + k;
+#pragma unroll
+        for (int m = 0; m < NR; ++m) {
+            const int yy = ty + m * rstep;
+            T cj[VW], w[VW];
+            ld16(cj, in + yy * W + q * VW);
+#pragma unroll
+            for (int uu = 0; uu < VW; ++uu) {
+                w[uu] = prev[m][uu] - cj[uu];
+                prev[m][uu] = cj[uu];
+            }
+            const long px = (long)yy * n + xs;
+            emit_band<T>(w, w_out + b * w_bs + (long)(band - 1) * w_ss, px, yy, xs, n, true, acc1, acc2,
+                         (long)(band - 1) * nn, acc_atomic != 0);
+        }
+        __syncthreads();  // bufA is reloaded next
+    }
+    if (c_out) {
+#pragma unroll
+        for (int m = 0; m < NR; ++m) {
+            const int yy = ty + m * rstep;
+            st16(c_out + b * c_bs + (long)yy * n + xs, prev[m]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Scales handled by the fused tile kernel: 3 by default; never more than
 // fit a 32 x 32 tile with its halo (two buffers) in 200 KB of shared memory.
 static int auto_fuse(int J, const fm_config &cfg)
@@ -310,11 +455,26 @@ static int auto_fuse(int J, const fm_config &cfg)
     return f;
 }
 
+// Strip width of the column-strip kernel: 2 n W elements must fit 128 KB.
+// 0 = use the one-scale-per-pass kernels instead.
+static int cols_multi_width(int n, size_t es)
+{
+    const int vw = (int)(16 / es);
+    if (n < 64 || n % 8) return 0;
+    int w = (int)((64 * 1024 / es) / n);
+    if (w > 16) w = 16;
+    if (w < vw || n % w) return 0;
+    return w;
+}
+
 size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg)
 {
     const int f = auto_fuse(J, cfg);
     if (f >= J - 1) return 0;
-    return 2ull * (size_t)batch * n * n;
+    const size_t es = cfg.precision == FM_F64 ? 8 : 4;
+    const size_t per = (size_t)batch * n * n;
+    if (f >= 1 && cols_multi_width(n, es)) return (size_t)(J - f) * per;  // c_f + one u per large scale
+    return 2 * per;
 }
 
 template <typename T, int F, int TS>
@@ -370,6 +530,37 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
         const long c_bs = f == J - 1 ? pyr_bs : nn;
         int st = tile_dispatch<T>(f, kappa, pyr, pyr_bs, nn, c_out, c_bs, n, bnd, batch, acc1, acc2, vec_ok, s);
         if (st != FM_OK) return st;
+    }
+    const int K = J - 1 - f;  // large scales left after the tile kernel
+    const int Wc = cols_multi_width(n, sizeof(T));
+    if (K >= 1 && f >= 1 && Wc && vec_ok) {
+        T *U = A + (long)batch * nn;  // u_{f+1} .. u_{f+K}, each batch * nn
+        const size_t rsm = 2ull * n * sizeof(T);
+        FM_CUDA_TRY(cudaFuncSetAttribute(k_st_rows_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+        FM_LAUNCH(FM_K_STARLET_ROW, k_st_rows_multi<T>, dim3(n, batch), 256, rsm, s, A, nn, U, (long)batch * nn, n,
+                  f, K, bnd);
+        constexpr int NR = 8;
+        const size_t csm = 2ull * n * Wc * sizeof(T);
+        const unsigned cgrid = (unsigned)((long)batch * (n / Wc));
+        const int cthreads = n * (Wc / VW) / NR;
+        T *w_base = noise ? nullptr : pyr;
+#define FM_COLS_MULTI(WW)                                                                                          \
+    do {                                                                                                            \
+        auto kc = k_st_cols_multi<T, WW, NR>;                                                                       \
+        FM_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));               \
+        FM_LAUNCH(FM_K_STARLET_COL, kc, cgrid, cthreads, csm, s, A, nn, U, (long)batch * nn, w_base, pyr_bs, nn,     \
+                  last, pyr_bs, n, f, K, bnd, acc1, acc2, batch > 1 ? 1 : 0);                                      \
+    } while (0)
+        switch (Wc) {
+        case 16: FM_COLS_MULTI(16); break;
+        case 8: FM_COLS_MULTI(8); break;
+        case 4: FM_COLS_MULTI(4); break;
+        case 2:
+            if constexpr (VW <= 2) FM_COLS_MULTI(2);
+            break;
+        }
+#undef FM_COLS_MULTI
+        return FM_OK;
     }
     const unsigned gx = (unsigned)((n + 128 * VW - 1) / (128 * VW));
     for (int j = f + 1; j <= J - 1; ++j) {
