@@ -252,6 +252,12 @@ def side_legs(fm, torch, n, J, g1, g2):
                      "map_s98_cut_theta_ms": t_s98, "map_starletQ_cut_2theta_ms": t_stq,
                      "speedup_vs_s98": t_s98 / t_st, "speedup_ks_starlet_vs_s98": t_s98 / t_ks})
     out["direct_map"] = rows
+    # the other large-scale kernel path (all large scales in two kernels)
+    pyr_b = torch.empty(g1.shape[0], J, n, n, dtype=torch.float32, device="cuda")
+    alt = lambda: fm.fm_map_starlet(g1, g2, J, out=pyr_b, large_path=2)  # noqa: E731
+    alt()
+    ms_alt = cuda_time(torch, alt, 10)
+    out["large_path_2"] = {"ms_per_step": ms_alt, "value": n * n * J * g1.shape[0] / (ms_alt * 1e-3) / 1e6}
     # batched noise maps: R realisations of KS + starlet with FP64 accumulation
     R = 1000
     fm.fm_map_noise(s1, s2, J, 8, seed=3)

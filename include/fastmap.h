@@ -76,7 +76,9 @@ typedef struct {
     int fuse_depth; /* starlet scales done by the fused 2-D tile kernel:
                        0 = automatic, k > 0 = scales 1..k, -1 = none (the
                        plain one-scale-per-pass form) */
-    int tile;       /* 0 = automatic; reserved for tuning */
+    int large_path; /* scales after the fused ones: 0 = automatic, 1 = one row
+                       pass + one column pass per scale, 2 = all large scales
+                       in one row kernel + one column-strip kernel */
 } fm_config;
 
 /* ---- Kaiser-Squires (Sec. 4.4) ---------------------------------------------

@@ -68,18 +68,21 @@ template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s)
 // Mirror: whole-sample symmetric extension (period 2(n-1)); periodic: mod n.
 __host__ __device__ __forceinline__ int fold_mirror(int i, int n)
 {
-    if (i >= 0 && i < n) return i;
     if (n == 1) return 0;
-    const int p = 2 * (n - 1);
-    i %= p;
-    if (i < 0) i += p;
-    return i >= n ? p - i : i;
+    // reflect about 0 and n-1 until inside; one reflection covers offsets up
+    // to n - 1, which every caller's halo (<= n / 2 + tile halo) meets except
+    // on the smallest maps
+    while (i < 0 || i >= n) {
+        if (i < 0) i = -i;
+        if (i >= n) i = 2 * (n - 1) - i;
+    }
+    return i;
 }
 __host__ __device__ __forceinline__ int fold_periodic(int i, int n)
 {
-    if (i >= 0 && i < n) return i;
-    i %= n;
-    return i < 0 ? i + n : i;
+    while (i < 0) i += n;
+    while (i >= n) i -= n;
+    return i;
 }
 __host__ __device__ __forceinline__ int fold_index(int i, int n, int boundary)
 {

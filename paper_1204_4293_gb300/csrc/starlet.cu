@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long 
         const int gy = fold_index(ty0 - HP + i, n, boundary);
         const int gx0 = tx0 - HP + q * VW;
         const T *rowp = src + (long)gy * n;
-        T v[VW];
+        alignas(16) T v[VW];
         if (vok && gx0 >= 0 && gx0 + VW <= n) {
             ld16(v, rowp + gx0);
         } else {
@@ -140,9 +140,9 @@ __global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long 
                 const int i = HP - hb + e / ncq;
                 const int x = HP - ha + (e % ncq) * VW;
                 const T *row = A + i * P;
-                T o[VW];
+                alignas(16) T o[VW];
                 if (2 * s <= VW) {
-                    T win[3 * VW];
+                    alignas(16) T win[3 * VW];
                     T *wp = win;
                     ld16(*reinterpret_cast<T(*)[VW]>(wp), row + x - VW);
                     ld16(*reinterpret_cast<T(*)[VW]>(wp + VW), row + x);
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long 
                         o[u] = B3<T>::apply(win[VW + u - 2 * s], win[VW + u - s], win[VW + u], win[VW + u + s],
                                             win[VW + u + 2 * s]);
                 } else {
-                    T m2[VW], m1[VW], c0[VW], p1[VW], p2[VW];
+                    alignas(16) T m2[VW]; alignas(16) T m1[VW]; alignas(16) T c0[VW]; alignas(16) T p1[VW]; alignas(16) T p2[VW];
                     ld16(m2, row + x - 2 * s);
                     ld16(m1, row + x - s);
                     ld16(c0, row + x);
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long 
                 const int i = HP - ha + e / ncq;
                 const int x = HP - ha + (e % ncq) * VW;
                 const T *bp = Bf + i * P + x;
-                T m2[VW], m1[VW], c0[VW], p1[VW], p2[VW], cj[VW], prev[VW], w[VW];
+                alignas(16) T m2[VW]; alignas(16) T m1[VW]; alignas(16) T c0[VW]; alignas(16) T p1[VW]; alignas(16) T p2[VW]; alignas(16) T cj[VW]; alignas(16) T prev[VW]; alignas(16) T w[VW];
                 ld16(m2, bp - 2 * s * P);
                 ld16(m1, bp - s * P);
                 ld16(c0, bp);
@@ -213,9 +213,9 @@ __global__ void __launch_bounds__(128) k_st_row(const T *__restrict__ c, long c_
     const long b = blockIdx.z;
     const T *row = c + b * c_bs + (long)y * n;
     T *dst = r + (b * n + y) * (long)n;
-    T o[VW];
+    alignas(16) T o[VW];
     if (vec_ok && s % VW == 0 && x - 2 * s >= 0 && x + VW + 2 * s <= n) {
-        T m2[VW], m1[VW], c0[VW], p1[VW], p2[VW];
+        alignas(16) T m2[VW]; alignas(16) T m1[VW]; alignas(16) T c0[VW]; alignas(16) T p1[VW]; alignas(16) T p2[VW];
         ld16(m2, row + x - 2 * s);
         ld16(m1, row + x - s);
         ld16(c0, row + x);
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T
             for (int u = 0; u < VW; ++u) d[u] = p[x + u < n ? x + u : n - 1];
         }
     };
-    T win[5][VW];
+    alignas(16) T win[5][VW];
     const int ybase = r0 + s * (m * KR);
 #pragma unroll
     for (int u = 0; u < 4; ++u) load_row(ybase + (u - 2) * s, win[u]);
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T
         const int y = ybase + k * s;
         if (y >= n) break;
         load_row(y + 2 * s, win[(k + 4) % 5]);
-        T cj[VW], prev[VW], w[VW];
+        alignas(16) T cj[VW]; alignas(16) T prev[VW]; alignas(16) T w[VW];
         const long px = (long)y * n + x;
         if (vok) {
             ld16(prev, c_prev + b * prev_bs + px);
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(256) k_st_rows_multi(const T *__restrict__ c, 
     const T *src = c + b * c_bs + (long)y * n;
     const long roff = (b * n + y) * (long)n;
     for (int x = threadIdx.x * VW; x < n; x += blockDim.x * VW) {
-        T v[VW];
+        alignas(16) T v[VW];
         ld16(v, src + x);
         st16(buf0 + x, v);
     }
@@ -330,9 +330,9 @@ __global__ void __launch_bounds__(256) k_st_rows_multi(const T *__restrict__ c, 
         const int s = 1 << (a + k - 1);
         T *dst = u_out + (long)(k - 1) * u_ks + roff;
         for (int x = threadIdx.x * VW; x < n; x += blockDim.x * VW) {
-            T o[VW];
-            if (x - 2 * s >= 0 && x + VW + 2 * s <= n) {
-                T m2[VW], m1[VW], c0[VW], p1[VW], p2[VW];
+            alignas(16) T o[VW];
+            if (s % VW == 0 && x - 2 * s >= 0 && x + VW + 2 * s <= n) {  // 16-byte aligned taps only
+                alignas(16) T m2[VW]; alignas(16) T m1[VW]; alignas(16) T c0[VW]; alignas(16) T p1[VW]; alignas(16) T p2[VW];
                 ld16(m2, in + x - 2 * s);
                 ld16(m1, in + x - s);
                 ld16(c0, in + x);
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(512) k_st_cols_multi(const T *__restrict__ c_a
     const long nn = (long)n * n;
     const int xs = x0 + q * VW;
 
-    T prev[NR][VW];  // c_{a+k-1} at the thread's pixels
+    alignas(16) T prev[NR][VW];  // c_{a+k-1} at the thread's pixels
 #pragma unroll
     for (int m = 0; m < NR; ++m) ld16(prev[m], c_a + b * ca_bs + (long)(ty + m * rstep) * n + xs);
 
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(512) k_st_cols_multi(const T *__restrict__ c_a
         const T *u = u_in + (long)(k - 1) * u_ks + b * nn;
         for (int e = threadIdx.x; e < n * QW; e += blockDim.x) {
             const int yy = e / QW, qq = e % QW;
-            T v[VW];
+            alignas(16) T v[VW];
             ld16(v, u + (long)yy * n + x0 + qq * VW);
             st16(bufA + yy * W + qq * VW, v);
         }
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(512) k_st_cols_multi(const T *__restrict__ c_a
             const int s = 1 << (a + p - 1);
             for (int e = threadIdx.x; e < n * QW; e += blockDim.x) {
                 const int yy = e / QW, qq = e % QW;
-                T m2[VW], m1[VW], c0[VW], p1[VW], p2[VW], o[VW];
+                alignas(16) T m2[VW]; alignas(16) T m1[VW]; alignas(16) T c0[VW]; alignas(16) T p1[VW]; alignas(16) T p2[VW]; alignas(16) T o[VW];
                 ld16(m2, in + fold_index(yy - 2 * s, n, boundary) * W + qq * VW);
                 ld16(m1, in + fold_index(yy - s, n, boundary) * W + qq * VW);
                 ld16(c0, in + yy * W + qq * VW);
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(512) k_st_cols_multi(const T *__restrict__ c_a
 #pragma unroll
         for (int m = 0; m < NR; ++m) {
             const int yy = ty + m * rstep;
-            T cj[VW], w[VW];
+            alignas(16) T cj[VW]; alignas(16) T w[VW];
             ld16(cj, in + yy * W + q * VW);
 #pragma unroll
             for (int uu = 0; uu < VW; ++uu) {
@@ -473,7 +473,7 @@ size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg)
     if (f >= J - 1) return 0;
     const size_t es = cfg.precision == FM_F64 ? 8 : 4;
     const size_t per = (size_t)batch * n * n;
-    if (f >= 1 && cols_multi_width(n, es)) return (size_t)(J - f) * per;  // c_f + one u per large scale
+    if (f >= 1 && cfg.large_path == 2 && cols_multi_width(n, es)) return (size_t)(J - f) * per;  // c_f + u's
     return 2 * per;
 }
 
@@ -533,7 +533,7 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
     }
     const int K = J - 1 - f;  // large scales left after the tile kernel
     const int Wc = cols_multi_width(n, sizeof(T));
-    if (K >= 1 && f >= 1 && Wc && vec_ok) {
+    if (K >= 1 && f >= 1 && Wc && vec_ok && cfg.large_path == 2) {
         T *U = A + (long)batch * nn;  // u_{f+1} .. u_{f+K}, each batch * nn
         const size_t rsm = 2ull * n * sizeof(T);
         FM_CUDA_TRY(cudaFuncSetAttribute(k_st_rows_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));

@@ -34,7 +34,7 @@ KERNEL_IDS = {"fft_rows_fwd": 1, "fft_cols_ks": 2, "fft_rows_inv": 3, "starlet_t
 
 class fm_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("boundary", ctypes.c_int), ("accum", ctypes.c_int),
-                ("fuse_depth", ctypes.c_int), ("tile", ctypes.c_int)]
+                ("fuse_depth", ctypes.c_int), ("large_path", ctypes.c_int)]
 
 
 class fm_request(ctypes.Structure):
@@ -104,9 +104,9 @@ def _prec(t: torch.Tensor) -> int:
     raise TypeError(f"maps must be float32 or float64, got {t.dtype}")
 
 
-def _cfg(precision, boundary=FM_MIRROR, fuse_depth=0):
+def _cfg(precision, boundary=FM_MIRROR, fuse_depth=0, large_path=0):
     c = fm_config()
-    c.precision, c.boundary, c.accum, c.fuse_depth, c.tile = precision, boundary, 0, fuse_depth, 0
+    c.precision, c.boundary, c.accum, c.fuse_depth, c.large_path = precision, boundary, 0, fuse_depth, large_path
     return c
 
 
@@ -162,21 +162,21 @@ def _pyr_out(ref, J, out):
     return out
 
 
-def fm_starlet_forward(kappa, J, boundary=FM_MIRROR, fuse_depth=0, out=None, stream=None):
+def fm_starlet_forward(kappa, J, boundary=FM_MIRROR, fuse_depth=0, out=None, stream=None, large_path=0):
     """Starlet pyramid [.., J, n, n]: w_1..w_{J-1}, smooth (Sec. 3)."""
     n, batch = _maps(kappa)
     pyr = _pyr_out(kappa, J, out)
-    c = _cfg(_prec(kappa), boundary, fuse_depth)
+    c = _cfg(_prec(kappa), boundary, fuse_depth, large_path)
     _check(_lib.fm_starlet_forward(_ptr(kappa), _ptr(pyr), n, J, batch, ctypes.byref(c), _stream(stream)),
            "fm_starlet_forward")
     return pyr
 
 
-def fm_map_starlet(g1, g2, J, boundary=FM_MIRROR, fuse_depth=0, out=None, stream=None):
+def fm_map_starlet(g1, g2, J, boundary=FM_MIRROR, fuse_depth=0, out=None, stream=None, large_path=0):
     """KS inversion then starlet: all aperture-mass bands from shear."""
     n, batch = _maps(g1, g2)
     pyr = _pyr_out(g1, J, out)
-    c = _cfg(_prec(g1), boundary, fuse_depth)
+    c = _cfg(_prec(g1), boundary, fuse_depth, large_path)
     _check(_lib.fm_map_starlet(_ptr(g1), _ptr(g2), _ptr(pyr), n, J, batch, ctypes.byref(c), _stream(stream)),
            "fm_map_starlet")
     return pyr

@@ -20,7 +20,7 @@ def _fm():
     return fastmap
 
 
-CASES = [(4, 2), (8, 3), (16, 4), (37, 5), (64, 6), (100, 6), (200, 7), (256, 5), (130, 7)]
+CASES = [(4, 2), (8, 3), (16, 4), (37, 5), (64, 6), (100, 6), (200, 7), (256, 5), (130, 7), (128, 7), (512, 8)]
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
@@ -34,9 +34,11 @@ def test_starlet_matches_oracle(n, J, boundary, dtype):
     for fuse in sorted({-1, 1, 2, 3, J - 1}):
         if fuse > J - 1:
             continue
-        pyr = fm.fm_starlet_forward(torch.from_numpy(kappa).cuda(), J, boundary=boundary, fuse_depth=fuse)
-        errs = band_errs(pyr.cpu().numpy(), ref)
-        assert max(errs) <= TOL[dtype], (fuse, errs)
+        for large_path in ((1, 2) if 0 < fuse < J - 1 else (0,)):
+            pyr = fm.fm_starlet_forward(torch.from_numpy(kappa).cuda(), J, boundary=boundary, fuse_depth=fuse,
+                                        large_path=large_path)
+            errs = band_errs(pyr.cpu().numpy(), ref)
+            assert max(errs) <= TOL[dtype], (fuse, large_path, errs)
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
