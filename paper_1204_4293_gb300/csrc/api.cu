@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -122,6 +123,26 @@ const void *twiddles(int n, int precision, cudaStream_t s, int *status)
     (void)s;
     g_tw[key] = d;
     return d;
+}
+
+// ---- kernel attributes -------------------------------------------------------------
+namespace {
+std::mutex g_attr_mu;
+std::unordered_map<uint64_t, size_t> g_attr;  // (device, kernel) -> smem bytes set
+}  // namespace
+
+cudaError_t smem_attr(const void *kernel, size_t bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t key = ((uint64_t)(uintptr_t)kernel) ^ ((uint64_t)dev << 56);
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto it = g_attr.find(key);
+    if (it != g_attr.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) g_attr[key] = bytes;
+    return e;
 }
 
 // ---- scratch -------------------------------------------------------------------
@@ -259,29 +280,208 @@ int fm_starlet_forward(const void *kappa, void *pyramid, int n, int J, int batch
     return launch_starlet(kappa, pyramid, (long)J * n * n, n, J, batch, cfg, sc.p, nullptr, nullptr, s);
 }
 
-// KS then starlet of kappa_E; kappa_E and the FFT work buffer are scratch.
-static int map_starlet_dev(const void *g1, const void *g2, void *pyramid, int n, int J, int batch,
-                           const fm_config &cfg, cudaStream_t s)
-{
-    const long nn = (long)n * n;
-    const size_t es = esize(cfg);
-    Scratch wsc, ksc, ssc;
-    int st;
-    if ((st = scratch_alloc(wsc, (size_t)batch * nn * 2 * es, s))) return st;
-    if ((st = scratch_alloc(ksc, (size_t)batch * nn * es, s))) return st;
-    if ((st = scratch_alloc(ssc, starlet_scratch_elems(n, J, batch, cfg) * es, s))) return st;
-    if ((st = launch_ks(g1, g2, nn, ksc.p, nullptr, wsc.p, n, batch, cfg.precision, false, 0, 0, false, s))) return st;
-    return launch_starlet(ksc.p, pyramid, (long)J * nn, n, J, batch, cfg, ssc.p, nullptr, nullptr, s);
-}
-
 }  // extern "C"
 
 namespace fm {
+
+// ---- KS + starlet over a batch, in L2-sized chunks ---------------------------------
+// A chunk of C maps runs KS then the starlet before the next chunk starts, so
+// its intermediates (FFT work buffer, kappa, starlet scratch: ~20 B/px fp32)
+// stay in L2 and only the shear and the pyramid cross HBM.  Chunks alternate
+// between two internal streams (one scratch slot each) so one chunk's
+// kernels overlap the next one's.  Batches of more than one chunk are
+// recorded once into a CUDA graph per (pointers, sizes, config) and replayed.
+namespace {
+
+struct DevStreams {
+    cudaStream_t cap = nullptr;        // origin stream for graph capture
+    cudaStream_t s[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+};
+std::mutex g_ds_mu;  // guards g_ds and serialises multi-stream submission
+std::unordered_map<int, DevStreams> g_ds;
+
+int dev_streams(DevStreams **out)
+{
+    int dev = 0;
+    FM_CUDA_TRY(cudaGetDevice(&dev));
+    DevStreams &d = g_ds[dev];
+    if (!d.cap) {
+        FM_CUDA_TRY(cudaStreamCreateWithFlags(&d.cap, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) {
+            FM_CUDA_TRY(cudaStreamCreateWithFlags(&d.s[k], cudaStreamNonBlocking));
+            FM_CUDA_TRY(cudaEventCreateWithFlags(&d.join[k], cudaEventDisableTiming));
+        }
+        FM_CUDA_TRY(cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming));
+    }
+    *out = &d;
+    return FM_OK;
+}
+
+struct ChunkPlan {
+    int C = 1, slots = 1;
+    size_t work_b = 0, kap_b = 0, st_b = 0, slot_b = 0;
+};
+
+// intermediates of one slot kept near 40 MB (two slots in flight)
+ChunkPlan plan_chunks(int n, int J, int batch, const fm_config &cfg)
+{
+    const size_t es = cfg.precision == FM_F64 ? 8 : 4;
+    const size_t nn = (size_t)n * n;
+    const size_t per_map = nn * 3 * es + starlet_scratch_elems(n, J, 1, cfg) * es;
+    ChunkPlan p;
+    p.C = (int)((40u << 20) / per_map);
+    if (p.C < 1) p.C = 1;
+    if (p.C > batch) p.C = batch;
+    p.slots = batch > p.C ? 2 : 1;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    p.work_b = up((size_t)p.C * nn * 2 * es);
+    p.kap_b = up((size_t)p.C * nn * es);
+    p.st_b = up(starlet_scratch_elems(n, J, p.C, cfg) * es);
+    p.slot_b = p.work_b + p.kap_b + p.st_b;
+    return p;
+}
+
+int run_chunk(const char *g1, const char *g2, char *pyr, int n, int J, int b0, int bc, const fm_config &cfg,
+              const ChunkPlan &p, char *slot, cudaStream_t s)
+{
+    const size_t es = cfg.precision == FM_F64 ? 8 : 4;
+    const size_t nn = (size_t)n * n;
+    char *work = slot, *kap = slot + p.work_b, *st = kap + p.kap_b;
+    int r = launch_ks(g1 + b0 * nn * es, g2 + b0 * nn * es, (long)nn, kap, nullptr, work, n, bc, cfg.precision, false,
+                      0, 0, false, s);
+    if (r != FM_OK) return r;
+    return launch_starlet(kap, pyr + (size_t)b0 * J * nn * es, (long)J * nn, n, J, bc, cfg, st, nullptr, nullptr, s);
+}
+
+// All chunks, forked from `origin` onto the two internal streams and joined
+// back.  Caller holds g_ds_mu.
+int run_chunks(const void *g1, const void *g2, void *pyr, int n, int J, int batch, const fm_config &cfg,
+               const ChunkPlan &p, char *scratch, cudaStream_t origin, DevStreams &ds)
+{
+    FM_CUDA_TRY(cudaEventRecord(ds.fork, origin));
+    for (int k = 0; k < p.slots; ++k) FM_CUDA_TRY(cudaStreamWaitEvent(ds.s[k], ds.fork, 0));
+    int i = 0;
+    for (int b0 = 0; b0 < batch; b0 += p.C, ++i) {
+        const int k = i % p.slots;
+        const int bc = batch - b0 < p.C ? batch - b0 : p.C;
+        int r = run_chunk((const char *)g1, (const char *)g2, (char *)pyr, n, J, b0, bc, cfg, p,
+                          scratch + (size_t)k * p.slot_b, ds.s[k]);
+        if (r != FM_OK) return r;
+    }
+    for (int k = 0; k < p.slots; ++k) {
+        FM_CUDA_TRY(cudaEventRecord(ds.join[k], ds.s[k]));
+        FM_CUDA_TRY(cudaStreamWaitEvent(origin, ds.join[k], 0));
+    }
+    return FM_OK;
+}
+
+struct GraphKey {
+    const void *g1, *g2, *pyr;
+    int n, J, batch, dev;
+    fm_config cfg;
+    bool operator==(const GraphKey &o) const
+    {
+        return g1 == o.g1 && g2 == o.g2 && pyr == o.pyr && n == o.n && J == o.J && batch == o.batch &&
+               dev == o.dev && memcmp(&cfg, &o.cfg, sizeof(cfg)) == 0;
+    }
+};
+struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+    void *scratch = nullptr;
+    uint64_t used = 0;
+    int64_t kernels = 0;  // kernel nodes per replay (counted into g_launches)
+};
+std::vector<GraphEntry> g_graphs;  // guarded by g_ds_mu
+uint64_t g_graph_clock = 0;
+constexpr size_t kMaxGraphs = 4;
+
+void drop_graph(GraphEntry &e)
+{
+    cudaDeviceSynchronize();  // an evicted graph may still be running
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.scratch) cudaFree(e.scratch);
+    e.exec = nullptr;
+    e.scratch = nullptr;
+}
+
+}  // namespace
+
+static int map_starlet_dev(const void *g1, const void *g2, void *pyramid, int n, int J, int batch,
+                           const fm_config &cfg, cudaStream_t s, bool allow_graph = true)
+{
+    const ChunkPlan p = plan_chunks(n, J, batch, cfg);
+    if (p.slots == 1) {  // one chunk: straight onto the caller's stream
+        Scratch sc;
+        int st = scratch_alloc(sc, p.slot_b, s);
+        if (st) return st;
+        return run_chunk((const char *)g1, (const char *)g2, (char *)pyramid, n, J, 0, batch, cfg, p, (char *)sc.p, s);
+    }
+    int st = FM_OK;
+    if (!twiddles(n, cfg.precision, s, &st)) return st;  // build tables outside any capture
+    std::lock_guard<std::mutex> lk(g_ds_mu);
+    DevStreams *ds = nullptr;
+    if ((st = dev_streams(&ds))) return st;
+    const bool profiling = g_prof_kid.load() != 0;
+    if (!allow_graph || profiling) {
+        Scratch sc;
+        if ((st = scratch_alloc(sc, p.slot_b * p.slots, s))) return st;
+        return run_chunks(g1, g2, pyramid, n, J, batch, cfg, p, (char *)sc.p, s, *ds);
+    }
+    GraphKey key{g1, g2, pyramid, n, J, batch, 0, cfg};
+    FM_CUDA_TRY(cudaGetDevice(&key.dev));
+    GraphEntry *hit = nullptr;
+    for (auto &e : g_graphs)
+        if (e.key == key) hit = &e;
+    if (!hit) {
+        if (g_graphs.size() >= kMaxGraphs) {
+            auto lru = std::min_element(g_graphs.begin(), g_graphs.end(),
+                                        [](const GraphEntry &a, const GraphEntry &b) { return a.used < b.used; });
+            drop_graph(*lru);
+            g_graphs.erase(lru);
+        }
+        GraphEntry e;
+        e.key = key;
+        cudaError_t ce = cudaMalloc(&e.scratch, p.slot_b * p.slots);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaMalloc (graph scratch)");
+        cudaGraph_t graph = nullptr;
+        ce = cudaStreamBeginCapture(ds->cap, cudaStreamCaptureModeRelaxed);
+        if (ce != cudaSuccess) {
+            cudaFree(e.scratch);
+            return cuda_fail(ce, "cudaStreamBeginCapture");
+        }
+        const int64_t before = g_launches.load();
+        st = run_chunks(g1, g2, pyramid, n, J, batch, cfg, p, (char *)e.scratch, ds->cap, *ds);
+        e.kernels = g_launches.load() - before;
+        g_launches.fetch_sub(e.kernels);  // recorded, not launched
+        ce = cudaStreamEndCapture(ds->cap, &graph);
+        if (st == FM_OK && ce != cudaSuccess) st = cuda_fail(ce, "cudaStreamEndCapture");
+        if (st == FM_OK) {
+            ce = cudaGraphInstantiate(&e.exec, graph, 0);
+            if (ce != cudaSuccess) st = cuda_fail(ce, "cudaGraphInstantiate");
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (st != FM_OK) {
+            if (e.exec) cudaGraphExecDestroy(e.exec);
+            cudaFree(e.scratch);
+            return st;
+        }
+        g_graphs.push_back(e);
+        hit = &g_graphs.back();
+    }
+    hit->used = ++g_graph_clock;
+    FM_CUDA_TRY(cudaGraphLaunch(hit->exec, s));
+    g_launches.fetch_add(hit->kernels);
+    return FM_OK;
+}
+
 int map_starlet_run(const void *g1, const void *g2, void *pyramid, int n, int J, int batch, const fm_config &cfg,
                     cudaStream_t s)
 {
     return map_starlet_dev(g1, g2, pyramid, n, J, batch, cfg, s);
 }
+
 }  // namespace fm
 
 extern "C" {
@@ -317,7 +517,7 @@ int fm_map_starlet_host(const void *g1_host, const void *g2_host, void *pyramid_
     char *d1 = static_cast<char *>(gin.p);
     FM_CUDA_TRY(cudaMemcpyAsync(d1, g1_host, map_bytes, cudaMemcpyHostToDevice, s));
     FM_CUDA_TRY(cudaMemcpyAsync(d1 + map_bytes, g2_host, map_bytes, cudaMemcpyHostToDevice, s));
-    if ((st = map_starlet_dev(d1, d1 + map_bytes, pyr.p, n, J, batch, cfg, s))) return st;
+    if ((st = map_starlet_dev(d1, d1 + map_bytes, pyr.p, n, J, batch, cfg, s, false))) return st;
     FM_CUDA_TRY(cudaMemcpyAsync(pyramid_host, pyr.p, (size_t)J * map_bytes, cudaMemcpyDeviceToHost, s));
     return FM_OK;
 }

@@ -111,6 +111,10 @@ struct Scratch {
 };
 int scratch_alloc(Scratch &sc, size_t bytes, cudaStream_t s);
 
+// Raise a kernel's dynamic shared-memory limit once per (device, kernel,
+// size); later calls with no larger size make no driver call.
+cudaError_t smem_attr(const void *kernel, size_t bytes);
+
 // ---- internal launchers (defined per .cu file) ------------------------------------
 int launch_ks(const void *in1, const void *in2, long in_bstride, void *out1, void *out2, void *work, int n, int batch,
               int precision, bool forward, uint64_t rot_seed, int rot_r0, bool rotate, cudaStream_t s);

@@ -246,9 +246,9 @@ static int ks_impl(const T *in1, const T *in2, long in_bstride, T *out1, T *out2
     auto krf = k_rows_fwd<T, ER>;
     auto kcs = k_cols_ks<T, EC>;
     auto kri = k_rows_inv<T, ER>;
-    FM_CUDA_TRY(cudaFuncSetAttribute(krf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));
-    FM_CUDA_TRY(cudaFuncSetAttribute(kri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));
-    FM_CUDA_TRY(cudaFuncSetAttribute(kcs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem));
+    FM_CUDA_TRY(fm::smem_attr((const void *)krf, row_smem));
+    FM_CUDA_TRY(fm::smem_attr((const void *)kri, row_smem));
+    FM_CUDA_TRY(fm::smem_attr((const void *)kcs, col_smem));
 
     FM_LAUNCH(FM_K_FFT_ROWS_FWD, krf, row_grid, row_threads, row_smem, s, in1, in2, in_bstride, work, n, logn,
               lognvec, total_rows, tw, seed, r0, rotate ? 1 : 0);

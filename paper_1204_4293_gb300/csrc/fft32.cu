@@ -224,9 +224,9 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
     const int col_threads = P::W * P::TV;
     const size_t col_smem = P::NPASS > 1 ? (size_t)(P::N * P::W + P::N * P::W / 32 + 1) * sizeof(float2) : 0;
     const unsigned col_grid = (unsigned)((long)batch * (P::N / P::W));
-    FM_CUDA_TRY(cudaFuncSetAttribute(k_rows_fwd32<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));
-    FM_CUDA_TRY(cudaFuncSetAttribute(k_rows_inv32<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_smem));
-    FM_CUDA_TRY(cudaFuncSetAttribute(k_cols_ks32<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem));
+    FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_fwd32<LOGN>, row_smem));
+    FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_inv32<LOGN>, row_smem));
+    FM_CUDA_TRY(fm::smem_attr((const void *)k_cols_ks32<LOGN>, col_smem));
     FM_LAUNCH(FM_K_FFT_ROWS_FWD, k_rows_fwd32<LOGN>, row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs, work,
               total_rows, tw, seed, r0, rotate ? 1 : 0);
     FM_LAUNCH(FM_K_FFT_COLS_KS, k_cols_ks32<LOGN>, col_grid, col_threads, col_smem, s, work, tw, forward ? 1 : 0);

@@ -209,7 +209,7 @@ static int map_direct_impl(const T *g1, const T *g2, T *map, int n, int filter, 
     const int pw = width + (width >> 3) + 1;
     const size_t smem = 2ull * 2 * pw * sizeof(T);
     auto k = k_map_direct<T, CX, RY, NW>;
-    FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FM_CUDA_TRY(fm::smem_attr((const void *)k, smem));
     dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY);
     FM_LAUNCH(FM_K_MAP_DIRECT, k, grid, NW * 32, smem, s, g1, g2, dtaps, tw, ddx, map, n, Ri);
     return FM_OK;

@@ -488,7 +488,7 @@ static int tile_launch(const T *in, T *w_out, long w_bs, long w_ss, T *c_out, lo
     const int tiles_x = (n + TS - 1) / TS;
     const int tiles_per_map = tiles_x * tiles_x;
     auto k = k_st_tile<T, F, TS>;
-    FM_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FM_CUDA_TRY(fm::smem_attr((const void *)k, smem));
     FM_LAUNCH(FM_K_STARLET_TILE, k, (unsigned)(tiles_per_map * (long)batch), 256, smem, s, in, (long)n * n, w_out,
               w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, acc1, acc2, batch > 1 ? 1 : 0,
               vec_ok ? 1 : 0);
@@ -536,7 +536,7 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
     if (K >= 1 && f >= 1 && Wc && vec_ok && cfg.large_path == 2) {
         T *U = A + (long)batch * nn;  // u_{f+1} .. u_{f+K}, each batch * nn
         const size_t rsm = 2ull * n * sizeof(T);
-        FM_CUDA_TRY(cudaFuncSetAttribute(k_st_rows_multi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+        FM_CUDA_TRY(fm::smem_attr((const void *)k_st_rows_multi<T>, rsm));
         FM_LAUNCH(FM_K_STARLET_ROW, k_st_rows_multi<T>, dim3(n, batch), 256, rsm, s, A, nn, U, (long)batch * nn, n,
                   f, K, bnd);
         constexpr int NR = 8;
@@ -547,7 +547,7 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
 #define FM_COLS_MULTI(WW)                                                                                          \
     do {                                                                                                            \
         auto kc = k_st_cols_multi<T, WW, NR>;                                                                       \
-        FM_CUDA_TRY(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));               \
+        FM_CUDA_TRY(fm::smem_attr((const void *)kc, csm));               \
         FM_LAUNCH(FM_K_STARLET_COL, kc, cgrid, cthreads, csm, s, A, nn, U, (long)batch * nn, w_base, pyr_bs, nn,     \
                   last, pyr_bs, n, f, K, bnd, acc1, acc2, batch > 1 ? 1 : 0);                                      \
     } while (0)
