@@ -200,6 +200,153 @@ __global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long 
 }
 
 // ---------------------------------------------------------------------------
+// fp32 variant of the fused tile with register reuse of the filter taps:
+// the rows pass gives each thread 8 adjacent pixels (taps shared between its
+// two float4s), the columns pass 4 pixels of one float4 column at rows
+// i, i+s, i+2s, i+3s (8 row loads for 4 outputs).  Filter sums are kept
+// unnormalised (taps 1,4,6,4,1) and scaled by 1/256 once per scale, which is
+// exact (a power of two).
+__device__ __forceinline__ float4 f4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void sf4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float tap5(float a, float b, float c, float d, float e)
+{
+    // (a + e) + 4 (b + d) + 6 c
+    return fmaf(6.f, c, fmaf(4.f, b + d, a + e));
+}
+__device__ __forceinline__ float4 tap5(float4 a, float4 b, float4 c, float4 d, float4 e)
+{
+    return make_float4(tap5(a.x, b.x, c.x, d.x, e.x), tap5(a.y, b.y, c.y, d.y, e.y), tap5(a.z, b.z, c.z, d.z, e.z),
+                       tap5(a.w, b.w, c.w, d.w, e.w));
+}
+__device__ __forceinline__ float get(const float4 &v, int u) { return u == 0 ? v.x : u == 1 ? v.y : u == 2 ? v.z : v.w; }
+
+template <int F>
+__global__ void __launch_bounds__(256) k_st_tile32(const float *__restrict__ in, long in_bs, float *__restrict__ w_out,
+                                                   long w_bs, long w_ss, float *__restrict__ c_out, long c_bs, int n,
+                                                   int boundary, int tiles_x, int tiles_per_map,
+                                                   double *__restrict__ acc1, double *__restrict__ acc2,
+                                                   int acc_atomic, int vec_ok)
+{
+    constexpr int TS = 64;
+    constexpr int H = (1 << (F + 1)) - 2;
+    constexpr int HP = ((H + 3) / 4) * 4;
+    constexpr int P = TS + 2 * HP;
+    constexpr int NQ = P / 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *A = reinterpret_cast<float *>(smem_raw);  // c_{j-1} (true scale)
+    float *Bf = A + P * P;                            // 16 x rows-filtered c_{j-1}
+    const long b = blockIdx.x / tiles_per_map;
+    const int t = blockIdx.x - (int)(b * tiles_per_map);
+    const int ty0 = (t / tiles_x) * TS;
+    const int tx0 = (t % tiles_x) * TS;
+    const float *src = in + b * in_bs;
+    const long nn = (long)n * n;
+    const bool vok = vec_ok != 0;
+
+    for (int e = threadIdx.x; e < P * NQ; e += blockDim.x) {
+        const int i = e / NQ, q = e % NQ;
+        const int gy = fold_index(ty0 - HP + i, n, boundary);
+        const int gx0 = tx0 - HP + q * 4;
+        const float *rowp = src + (long)gy * n;
+        float4 v;
+        if (vok && gx0 >= 0 && gx0 + 4 <= n) {
+            v = f4(rowp + gx0);
+        } else {
+            v.x = rowp[fold_index(gx0, n, boundary)];
+            v.y = rowp[fold_index(gx0 + 1, n, boundary)];
+            v.z = rowp[fold_index(gx0 + 2, n, boundary)];
+            v.w = rowp[fold_index(gx0 + 3, n, boundary)];
+        }
+        sf4(A + i * P + q * 4, v);
+    }
+    __syncthreads();
+
+#pragma unroll
+    for (int j = 1; j <= F; ++j) {
+        const int s = 1 << (j - 1);
+        const int hb = (1 << (F + 1)) - (1 << j);
+        const int ha = (1 << (F + 1)) - (1 << (j + 1));
+        const int ncq = (TS + 2 * ha) / 4;  // float4 columns of the region (even)
+        const int c_lo = HP - ha;
+        // rows pass: 8 pixels (two float4) per task
+        {
+            const int nr = TS + 2 * hb, npair = ncq / 2;
+            for (int e = threadIdx.x; e < nr * npair; e += blockDim.x) {
+                const int i = HP - hb + e / npair;
+                const int x = c_lo + (e % npair) * 8;
+                const float *row = A + i * P + x;
+                float4 o0, o1;
+                if (s <= 2) {
+                    const float4 a = f4(row - 4), bq = f4(row), c = f4(row + 4), d = f4(row + 8);
+                    const float w[16] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w,
+                                         c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
+                    float o[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        o[u] = tap5(w[4 + u - 2 * s], w[4 + u - s], w[4 + u], w[4 + u + s], w[4 + u + 2 * s]);
+                    o0 = make_float4(o[0], o[1], o[2], o[3]);
+                    o1 = make_float4(o[4], o[5], o[6], o[7]);
+                } else if (s == 4) {
+                    const float4 m8 = f4(row - 8), m4 = f4(row - 4), z = f4(row), p4 = f4(row + 4),
+                                 p8 = f4(row + 8), p12 = f4(row + 12);
+                    o0 = tap5(m8, m4, z, p4, p8);
+                    o1 = tap5(m4, z, p4, p8, p12);
+                } else {
+                    o0 = tap5(f4(row - 2 * s), f4(row - s), f4(row), f4(row + s), f4(row + 2 * s));
+                    o1 = tap5(f4(row + 4 - 2 * s), f4(row + 4 - s), f4(row + 4), f4(row + 4 + s),
+                              f4(row + 4 + 2 * s));
+                }
+                sf4(Bf + i * P + x, o0);
+                sf4(Bf + i * P + x + 4, o1);
+            }
+        }
+        __syncthreads();
+        // columns pass: rows lo + r + s (4m + k), k = 0..3, one float4 column
+        {
+            const int nr = TS + 2 * ha;  // divisible by 4 s
+            const int groups = nr / (4 * s);
+            const int ntask = s * groups * ncq;
+            for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
+                const int qq = e % ncq;
+                const int rg = e / ncq;  // residue + s * group
+                const int r = rg % s, m = rg / s;
+                const int x = c_lo + qq * 4;
+                const int i0 = HP - ha + r + s * 4 * m;
+                const float *bp = Bf + i0 * P + x;
+                float4 win[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) win[u] = f4(bp + (u - 2) * s * P);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int i = i0 + k * s;
+                    float4 c = tap5(win[k], win[k + 1], win[k + 2], win[k + 3], win[k + 4]);
+                    c.x *= (1.f / 256.f);
+                    c.y *= (1.f / 256.f);
+                    c.z *= (1.f / 256.f);
+                    c.w *= (1.f / 256.f);
+                    float *ap = A + i * P + x;
+                    const float4 prev = f4(ap);
+                    const int oi = i - HP, ox = x - HP;
+                    if (oi >= 0 && oi < TS && ox >= 0 && ox < TS) {
+                        const int gy = ty0 + oi, gx = tx0 + ox;
+                        alignas(16) float w[4] = {prev.x - c.x, prev.y - c.y, prev.z - c.z, prev.w - c.w};
+                        const long px = (long)gy * n + gx;
+                        emit_band<float>(w, w_out + b * w_bs + (long)(j - 1) * w_ss, px, gy, gx, n, vok, acc1, acc2,
+                                         (long)(j - 1) * nn, acc_atomic != 0);
+                        if (j == F && c_out) {
+                            alignas(16) float cc[4] = {c.x, c.y, c.z, c.w};
+                            emit_band<float>(cc, c_out + b * c_bs, px, gy, gx, n, vok, nullptr, nullptr, 0, false);
+                        }
+                    }
+                    if (j < F) sf4(ap, c);
+                }
+            }
+        }
+        if (j < F) __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // One large scale, rows: r = rows-filtered c (taps +-s, +-2s), VW pixels per
 // thread.  grid = (ceil(n / (128 VW)), n, batch).
 template <typename T>
@@ -495,11 +642,40 @@ static int tile_launch(const T *in, T *w_out, long w_bs, long w_ss, T *c_out, lo
     return FM_OK;
 }
 
+template <int F>
+static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, float *c_out, long c_bs, int n,
+                         int boundary, int batch, double *acc1, double *acc2, bool vec_ok, cudaStream_t s)
+{
+    constexpr int TS = 64;
+    constexpr int H = (1 << (F + 1)) - 2;
+    constexpr int HP = ((H + 3) / 4) * 4;
+    constexpr int P = TS + 2 * HP;
+    const size_t smem = 2ull * P * P * sizeof(float);
+    const int tiles_x = (n + TS - 1) / TS;
+    const int tiles_per_map = tiles_x * tiles_x;
+    FM_CUDA_TRY(fm::smem_attr((const void *)k_st_tile32<F>, smem));
+    FM_LAUNCH(FM_K_STARLET_TILE, k_st_tile32<F>, (unsigned)(tiles_per_map * (long)batch), 256, smem, s, in,
+              (long)n * n, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, acc1, acc2,
+              batch > 1 ? 1 : 0, vec_ok ? 1 : 0);
+    return FM_OK;
+}
+
 template <typename T>
 static int tile_dispatch(int f, const T *in, T *w_out, long w_bs, long w_ss, T *c_out, long c_bs, int n,
                          int boundary, int batch, double *acc1, double *acc2, bool vec_ok, cudaStream_t s)
 {
     constexpr int TS = sizeof(T) == 4 ? 64 : 32;
+    if constexpr (sizeof(T) == 4) {
+        const float *fi = (const float *)in;
+        float *fw = (float *)w_out, *fc = (float *)c_out;
+        switch (f) {
+        case 1: return tile32_launch<1>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
+        case 2: return tile32_launch<2>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
+        case 3: return tile32_launch<3>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
+        case 4: return tile32_launch<4>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
+        }
+        return FM_EINVAL;
+    }
     switch (f) {
     case 1: return tile_launch<T, 1, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
     case 2: return tile_launch<T, 2, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
