@@ -323,14 +323,19 @@ struct ChunkPlan {
     size_t work_b = 0, kap_b = 0, st_b = 0, slot_b = 0;
 };
 
-// intermediates of one slot kept near 40 MB (two slots in flight)
+constexpr int64_t kDefaultChunkBytes = 0;  // measured: chunking did not beat one pass
+std::atomic<int64_t> g_chunk_bytes{kDefaultChunkBytes};
+std::atomic<int> g_use_graphs{1};
+
+// intermediates of one slot kept near the chunk budget (two slots in flight)
 ChunkPlan plan_chunks(int n, int J, int batch, const fm_config &cfg)
 {
     const size_t es = cfg.precision == FM_F64 ? 8 : 4;
     const size_t nn = (size_t)n * n;
     const size_t per_map = nn * 3 * es + starlet_scratch_elems(n, J, 1, cfg) * es;
     ChunkPlan p;
-    p.C = (int)((40u << 20) / per_map);
+    const int64_t budget = g_chunk_bytes.load();
+    p.C = budget <= 0 ? batch : (int)(budget / (int64_t)per_map);
     if (p.C < 1) p.C = 1;
     if (p.C > batch) p.C = batch;
     p.slots = batch > p.C ? 2 : 1;
@@ -424,7 +429,7 @@ static int map_starlet_dev(const void *g1, const void *g2, void *pyramid, int n,
     DevStreams *ds = nullptr;
     if ((st = dev_streams(&ds))) return st;
     const bool profiling = g_prof_kid.load() != 0;
-    if (!allow_graph || profiling) {
+    if (!allow_graph || profiling || !g_use_graphs.load()) {
         Scratch sc;
         if ((st = scratch_alloc(sc, p.slot_b * p.slots, s))) return st;
         return run_chunks(g1, g2, pyramid, n, J, batch, cfg, p, (char *)sc.p, s, *ds);
@@ -600,6 +605,15 @@ const char *fm_status_string(int status)
 }
 
 const char *fm_last_error(void) { return t_last_error.c_str(); }
+
+int fm_tune(int knob, int64_t value)
+{
+    switch (knob) {
+    case FM_TUNE_CHUNK_BYTES: g_chunk_bytes.store(value < 0 ? kDefaultChunkBytes : value); return FM_OK;
+    case FM_TUNE_GRAPHS: g_use_graphs.store(value < 0 ? 1 : (value != 0)); return FM_OK;
+    }
+    return einval("unknown tuning knob");
+}
 
 int64_t fm_launch_count(void) { return g_launches.load(); }
 
