@@ -165,6 +165,15 @@ const char *fm_status_string(int status);
 const char *fm_last_error(void);   /* message of the calling thread's last error */
 int64_t fm_launch_count(void);     /* kernels launched by this library so far */
 
+/* Tuning knobs (process-wide; value < 0 restores the default):
+ *   FM_TUNE_CHUNK_BYTES  L2 budget of one chunk's intermediates in batched
+ *                        KS + starlet calls; 0 = no chunking (the default)
+ *   FM_TUNE_GRAPHS       1 = replay batched calls from cached CUDA graphs
+ *                        (default), 0 = launch every kernel each call */
+#define FM_TUNE_CHUNK_BYTES 1
+#define FM_TUNE_GRAPHS 2
+int fm_tune(int knob, int64_t value);
+
 /* Kernel ids for fm_profile_select. */
 #define FM_K_FFT_ROWS_FWD 1
 #define FM_K_FFT_COLS_KS 2

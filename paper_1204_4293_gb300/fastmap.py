@@ -68,6 +68,7 @@ _SIGS = {
     "fm_last_error": (ctypes.c_char_p, []),
     "fm_launch_count": (ctypes.c_int64, []),
     "fm_profile_select": (_I, [_I]),
+    "fm_tune": (_I, [_I, ctypes.c_int64]),
     "fm_profile_read": (_I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -218,6 +219,14 @@ def fm_map_noise(g1, g2, J, R, seed, boundary=FM_MIRROR, with_snr=True, fuse_dep
                              ctypes.c_uint64(int(seed) & (2**64 - 1)), ctypes.byref(c), _stream(stream)),
            "fm_map_noise")
     return var, snr
+
+
+FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS = 1, 2
+
+
+def fm_tune(knob: int, value: int) -> None:
+    """Process-wide tuning knob (FM_TUNE_*); value < 0 restores the default."""
+    _check(_lib.fm_tune(int(knob), int(value)), "fm_tune")
 
 
 def fm_launch_count() -> int:
