@@ -133,6 +133,26 @@ int fm_map_direct(const void *g1, const void *g2, void *map, int n, int filter, 
 int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
                  const fm_config *cfg, void *stream);
 
+/* ---- Kaiser-Squires inversion without device allocation --------------------
+ * No counterpart in the paper: an engineering variant of fm_ks_invert for
+ * callers that cannot allocate device memory where they run the inversion
+ * (their device memory is reserved up front by another framework's pool, or
+ * the code path must never enter the allocator).  Same arguments, layout and
+ * results as fm_ks_invert, FM_F32 only (cfg NULL or precision FM_F32), n a
+ * power of two in [32, 8192], batch * n^2 <= 4194304.  The FFT work buffer
+ * and twiddle tables are file-scope device arrays (32 MiB + 128 KiB) that
+ * every GPU loading the library holds until the process exits; this entry
+ * point calls no cudaMalloc, cudaFree or other allocating routine.  Larger
+ * sizes return FM_EINVAL.  The first call on each device sets up (looks up
+ * the arrays' device addresses and copies the twiddle tables synchronously)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the one work buffer, which keeps the last call's contents
+ * (every call overwrites all of the part it uses, so nothing needs clearing);
+ * calls whose work overlaps on the GPU race on it and must be ordered by the
+ * caller, e.g. by issuing them on one stream. */
+int fm_ks_invert_noalloc(const void *g1, const void *g2, void *kappa_E, void *kappa_B, int n, int batch,
+                         const fm_config *cfg, void *stream);
+
 /* ---- serving: continuous batching of map requests -------------------------- */
 typedef struct {
     int n, J, R;          /* R = 0: pyramid only; R >= 2: also noise variance */

@@ -53,6 +53,7 @@ _CFG = ctypes.POINTER(fm_config)
 _SIGS = {
     "fm_ks_invert": (_I, [_P, _P, _P, _P, _I, _I, _CFG, _P]),
     "fm_ks_forward": (_I, [_P, _P, _P, _I, _I, _CFG, _P]),
+    "fm_ks_invert_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _CFG, _P]),
     "fm_starlet_forward": (_I, [_P, _P, _I, _I, _I, _CFG, _P]),
     "fm_map_starlet": (_I, [_P, _P, _P, _I, _I, _I, _CFG, _P]),
     "fm_map_starlet_host": (_I, [_P, _P, _P, _I, _I, _I, _CFG, _P]),

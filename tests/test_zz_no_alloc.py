@@ -1,0 +1,49 @@
+"""fm_ks_invert_noalloc: the Kaiser-Squires inversion for callers that cannot
+allocate device memory where they run it (their memory is reserved up front
+by another pool, or the code path must never enter the allocator).  Its work
+buffer is a static device array; this checks it through the C ABI against the
+allocating fm_ks_invert on two calls in a row, since the shared buffer keeps
+the previous call's contents.  Kept last in collection order."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import TOL, rel_err, shear
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(fm, g1, g2, kE, kB, n, batch):
+    c = fm._cfg(fm.FM_F32)
+    st = fm.lib.fm_ks_invert_noalloc(ctypes.c_void_p(g1.data_ptr()), ctypes.c_void_p(g2.data_ptr()),
+                                     ctypes.c_void_p(kE.data_ptr()), ctypes.c_void_p(kB.data_ptr()), n, batch,
+                                     ctypes.byref(c), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == fm.FM_OK, fm.lib.fm_last_error()
+
+
+@pytest.mark.parametrize("n,batch", [(1024, 2), (256, 3)])
+def test_noalloc_matches_allocating_entry_point_twice(n, batch):
+    from paper_1204_4293_gb300 import fastmap as fm
+    for call, seed in enumerate((41, 42)):  # second call sees the first call's buffer contents
+        maps = [shear(n, seed=seed + 10 * b, dtype=np.float32) for b in range(batch)]
+        g1 = torch.from_numpy(np.stack([m[0] for m in maps])).cuda()
+        g2 = torch.from_numpy(np.stack([m[1] for m in maps])).cuda()
+        kE = torch.empty_like(g1)
+        kB = torch.empty_like(g1)
+        _noalloc(fm, g1, g2, kE, kB, n, batch)
+        rE, rB = fm.fm_ks_invert(g1, g2, with_b=True)
+        torch.cuda.synchronize()
+        for b in range(batch):
+            assert rel_err(kE[b].cpu().numpy(), rE[b].cpu().numpy()) <= TOL[np.float32], call
+            assert rel_err(kB[b].cpu().numpy(), rB[b].cpu().numpy()) <= TOL[np.float32], call
+
+
+def test_noalloc_rejects_sizes_beyond_its_buffer():
+    from paper_1204_4293_gb300 import fastmap as fm
+    x = torch.zeros(2, 2048, 2048, device="cuda")
+    c = fm._cfg(fm.FM_F32)
+    p = ctypes.c_void_p(x.data_ptr())
+    assert fm.lib.fm_ks_invert_noalloc(p, p, p, None, 2048, 2, ctypes.byref(c), None) == fm.FM_EINVAL
+    assert b"batch * n^2" in fm.lib.fm_last_error()
