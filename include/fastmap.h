@@ -3,7 +3,7 @@
  *
  * Implements the pipeline of Leonard, Pires & Starck, "Fast Calculation of
  * the Weak Lensing Aperture Mass Statistic" (MNRAS 2012):
- *   shear (gamma1, gamma2) --Kaiser-Squires in Fourier space (Sec. 4.4)-->
+ *   shear (gamma1, gamma2) --Kaiser-Squires in Fourier space (Sec. 4.5)-->
  *   convergence kappa --starlet / a trous B3-spline transform (Sec. 3,
  *   Sec. 4.2)--> aperture-mass maps w_j = c_{j-1} - c_j at theta = 2^j px;
  *   the brute-force direct M_ap of eq. shearmap (Sec. 2.1, Sec. 5.1) as the
@@ -81,7 +81,7 @@ typedef struct {
                        in one row kernel + one column-strip kernel */
 } fm_config;
 
-/* ---- Kaiser-Squires (Sec. 4.4) ---------------------------------------------
+/* ---- Kaiser-Squires (Sec. 4.5) ---------------------------------------------
  * Forward: gamma = IFFT(D FFT kappa); inverse: kappa = IFFT(conj(D) FFT gamma),
  * D(k) = (k1 + i k2)^2 / |k|^2, D(0) = 0 (standard KS; the paper names the
  * Fourier-space inversion without printing D).

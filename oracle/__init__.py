@@ -6,7 +6,7 @@ wraps ``oracle.c`` (plain C, FP64) through ctypes and shares nothing with the
 CUDA path.
 
 Each wrapper names the paper passage its C function follows:
-  ks_forward / ks_invert   Sec. 4.4 (Kaiser-Squires in Fourier space)
+  ks_forward / ks_invert   Sec. 4.5 (Kaiser-Squires in Fourier space)
   starlet                  Sec. 3 and Sec. 4.2 (a trous B3-spline starlet)
   map_direct               eq. shearmap (Sec. 2.1), brute force as in Sec. 5.1
   map_noise                Sec. 1 and Sec. 5.1 (randomised-data noise maps)
@@ -161,7 +161,7 @@ def fft2(a, inverse=False):
 
 
 def ks_forward(kappa):
-    """gamma1, gamma2 = KS forward of kappa (Sec. 4.4)."""
+    """gamma1, gamma2 = KS forward of kappa (Sec. 4.5)."""
     k = _in(kappa)
     n = _pow2_n(k)
     g1, g2 = np.empty_like(k), np.empty_like(k)
@@ -170,7 +170,7 @@ def ks_forward(kappa):
 
 
 def ks_invert(g1, g2):
-    """(kappa_E, kappa_B) = KS inverse of the shear (Sec. 4.4)."""
+    """(kappa_E, kappa_B) = KS inverse of the shear (Sec. 4.5)."""
     a = _in(g1)
     n = _pow2_n(a)
     b = _in(g2, n)

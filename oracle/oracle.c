@@ -172,7 +172,7 @@ void oracle_fft2(double *re_im, int n, int inverse)
 static int freq_of(int i, int n) { return i < n / 2 ? i : i - n; }
 
 /* ------------------------------------------------------------------------ */
-/* Kaiser-Squires in Fourier space (Sec. 4.4).                              */
+/* Kaiser-Squires in Fourier space (Sec. 4.5).                              */
 /* The paper states only that shear and convergence are related by a 2-D    */
 /* convolution inverted in Fourier space; the multiplier used is the        */
 /* standard D(k) = (k1 + i k2)^2 / |k|^2 with D(0) = 0, forward             */
@@ -285,7 +285,7 @@ void oracle_starlet(const double *kappa, double *pyr, int n, int J, int boundary
 }
 
 /* KS inversion followed by the starlet of kappa_E: the fast aperture-mass
- * maps of Sec. 3 computed from shear (Sec. 4.4). */
+ * maps of Sec. 3 computed from shear (Sec. 4.5). */
 void oracle_map_starlet(const double *g1, const double *g2, double *pyr, int n, int J, int boundary)
 {
     size_t nn = (size_t)n * n;

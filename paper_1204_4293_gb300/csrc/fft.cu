@@ -1,5 +1,5 @@
 // fft.cu -- batched 2-D FFT staged in shared memory, with the Kaiser-Squires
-// multiplier fused between the column passes (Sec. 4.4).
+// multiplier fused between the column passes (Sec. 4.5).
 //
 // Three kernels per transform, each one HBM read and one HBM write:
 //   rows_fwd : pack (gamma1 + i gamma2) [optionally rotated by a per-pixel

@@ -1,4 +1,4 @@
-// fft32.cu -- fp32 Kaiser-Squires FFT (Sec. 4.4) with register-resident
+// fft32.cu -- fp32 Kaiser-Squires FFT (Sec. 4.5) with register-resident
 // radix-32 sub-transforms, for n = 32 .. 8192.
 //
 // A length-n transform (n = 2^LOGN) is split into Stockham passes: radix 32,

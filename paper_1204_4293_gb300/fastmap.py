@@ -135,7 +135,7 @@ def _ptr(t):
 
 # ---- entry points ----------------------------------------------------------------
 def fm_ks_invert(g1, g2, with_b=False, stream=None):
-    """(kappa_E, kappa_B or None) from shear (Kaiser-Squires, Sec. 4.4)."""
+    """(kappa_E, kappa_B or None) from shear (Kaiser-Squires, Sec. 4.5)."""
     n, batch = _maps(g1, g2)
     kE = torch.empty_like(g1)
     kB = torch.empty_like(g1) if with_b else None

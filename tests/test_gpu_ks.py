@@ -1,4 +1,4 @@
-"""GPU Kaiser-Squires (Sec. 4.4) against the FP64 oracle, element by element."""
+"""GPU Kaiser-Squires (Sec. 4.5) against the FP64 oracle, element by element."""
 import numpy as np
 import pytest
 import torch

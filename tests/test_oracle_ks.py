@@ -1,4 +1,4 @@
-"""Pins of the oracle's FFT and Kaiser-Squires inversion (Sec. 4.4).
+"""Pins of the oracle's FFT and Kaiser-Squires inversion (Sec. 4.5).
 
 The FFT is checked against a brute-force DFT and numpy.fft; the KS pair
 against the closed-form shear of a plane wave (from the lensing potential:
