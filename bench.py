@@ -259,12 +259,58 @@ def side_legs(fm, torch, n, J, g1, g2):
     alt()
     ms_alt = cuda_time(torch, alt, 10)
     out["large_path_2"] = {"ms_per_step": ms_alt, "value": n * n * J * g1.shape[0] / (ms_alt * 1e-3) / 1e6}
+    del pyr_b
+    torch.cuda.empty_cache()
+    out["serving"] = serving_leg(fm, torch)
     # batched noise maps: R realisations of KS + starlet with FP64 accumulation
     R = 1000
     fm.fm_map_noise(s1, s2, J, 8, seed=3)
     t_noise = cuda_time(torch, lambda: fm.fm_map_noise(s1, s2, J, R, seed=3), 1)
     out["noise"] = {"R": R, "ms": t_noise, "value": n * n * J * R / (t_noise * 1e-3) / 1e6, "unit": UNIT}
     return out
+
+
+def serving_leg(fm, torch, seed=5, nreq=48, lam=200.0, budget_gb=64, slots=8):
+    """Poisson stream of mixed-size requests through the continuous-batching
+    server: side in {256..4096}, J = log2(side) - 2, R in {0, 100, 1000}.
+    Reports offered vs achieved rate and p50/p99 latency (submit -> done)."""
+    rng = np.random.default_rng(seed)
+    sides = rng.choice([256, 512, 1024, 2048, 4096], nreq)
+    Rs = rng.choice([0, 100, 1000], nreq)
+    gaps = rng.exponential(1.0 / lam, nreq)
+    reqs = []
+    for side, R in zip(sides, Rs):
+        side, R = int(side), int(R)
+        J = int(np.log2(side)) - 2
+        g1 = 0.1 * torch.randn(side, side, device="cuda")
+        g2 = 0.1 * torch.randn(side, side, device="cuda")
+        pyr = torch.empty(J, side, side, device="cuda")
+        var = torch.empty(J - 1, side, side, dtype=torch.float64, device="cuda") if R else None
+        reqs.append((g1, g2, J, pyr, R, var))
+    torch.cuda.synchronize()
+    with fm.Server(mem_budget_bytes=budget_gb << 30, max_slots=slots) as sv:
+        # warm the kernels of every size once so the trace measures steady state
+        for side in sorted(set(int(x) for x in sides)):
+            g = 0.1 * torch.randn(side, side, device="cuda")
+            Jw = int(np.log2(side)) - 2
+            sv.wait(sv.submit(g, g, Jw, torch.empty(Jw, side, side, device="cuda")), 120.0)
+        tickets = []
+        t0 = time.perf_counter()
+        due = t0
+        for (g1, g2, J, pyr, R, var), gap in zip(reqs, gaps):
+            due += gap
+            while time.perf_counter() < due:
+                pass
+            tickets.append(sv.submit(g1, g2, J, pyr, R=R, seed=7, out_var=var))
+        res = [sv.wait(t, 600.0) for t in tickets]
+    ok = [r for r in res if r.status == fm.FM_OK]
+    lat = np.array([(r.t_done_ns - r.t_submit_ns) / 1e6 for r in ok])
+    span = (max(r.t_done_ns for r in ok) - min(r.t_submit_ns for r in ok)) / 1e9
+    pix_scales = sum(int(side) ** 2 * (int(np.log2(side)) - 2) * (1 + int(R)) for side, R in zip(sides, Rs))
+    return {"requests": nreq, "ok": len(ok), "offered_req_per_s": lam, "achieved_req_per_s": len(ok) / span,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mpix_scales_per_s": pix_scales / span / 1e6, "slots": slots, "budget_gb": budget_gb,
+            "trace": f"seed {seed}, Poisson {lam}/s, side U{{256..4096}}, J=log2(side)-2, R U{{0,100,1000}}"}
 
 
 def main():

@@ -200,10 +200,10 @@ __global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long 
 }
 
 // ---------------------------------------------------------------------------
-// fp32 variant of the fused tile with register reuse of the filter taps:
-// the rows pass gives each thread 8 adjacent pixels (taps shared between its
-// two float4s), the columns pass 4 pixels of one float4 column at rows
-// i, i+s, i+2s, i+3s (8 row loads for 4 outputs).  Filter sums are kept
+// fp32 variant of the fused tile with register reuse of the filter taps in
+// the columns pass: a thread computes 4 pixels of one float4 column at rows
+// i, i+s, i+2s, i+3s from 8 row loads.  Tasks of one row (or row group) start
+// on an 8-lane boundary so 128-bit shared-memory accesses do not conflict.  Filter sums are kept
 // unnormalised (taps 1,4,6,4,1) and scaled by 1/256 once per scale, which is
 // exact (a power of two).
 __device__ __forceinline__ float4 f4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
@@ -268,36 +268,30 @@ __global__ void __launch_bounds__(256) k_st_tile32(const float *__restrict__ in,
         const int ha = (1 << (F + 1)) - (1 << (j + 1));
         const int ncq = (TS + 2 * ha) / 4;  // float4 columns of the region (even)
         const int c_lo = HP - ha;
-        // rows pass: 8 pixels (two float4) per task
+        // rows pass: one float4 per task; a row's tasks start on an 8-lane
+        // boundary (ncq padded to ncqp) so a quarter warp's 128-bit loads
+        // stay within one row and hit distinct banks
+        const int ncqp = (ncq + 7) & ~7;
         {
-            const int nr = TS + 2 * hb, npair = ncq / 2;
-            for (int e = threadIdx.x; e < nr * npair; e += blockDim.x) {
-                const int i = HP - hb + e / npair;
-                const int x = c_lo + (e % npair) * 8;
+            const int nr = TS + 2 * hb;
+            for (int e = threadIdx.x; e < nr * ncqp; e += blockDim.x) {
+                const int q = e % ncqp;
+                if (q >= ncq) continue;
+                const int i = HP - hb + e / ncqp;
+                const int x = c_lo + q * 4;
                 const float *row = A + i * P + x;
-                float4 o0, o1;
+                float4 o;
                 if (s <= 2) {
-                    const float4 a = f4(row - 4), bq = f4(row), c = f4(row + 4), d = f4(row + 8);
-                    const float w[16] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w,
-                                         c.x, c.y, c.z, c.w, d.x, d.y, d.z, d.w};
-                    float o[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        o[u] = tap5(w[4 + u - 2 * s], w[4 + u - s], w[4 + u], w[4 + u + s], w[4 + u + 2 * s]);
-                    o0 = make_float4(o[0], o[1], o[2], o[3]);
-                    o1 = make_float4(o[4], o[5], o[6], o[7]);
-                } else if (s == 4) {
-                    const float4 m8 = f4(row - 8), m4 = f4(row - 4), z = f4(row), p4 = f4(row + 4),
-                                 p8 = f4(row + 8), p12 = f4(row + 12);
-                    o0 = tap5(m8, m4, z, p4, p8);
-                    o1 = tap5(m4, z, p4, p8, p12);
+                    const float4 a = f4(row - 4), bq = f4(row), c = f4(row + 4);
+                    const float w[12] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w, c.x, c.y, c.z, c.w};
+                    o = make_float4(tap5(w[4 - 2 * s], w[4 - s], w[4], w[4 + s], w[4 + 2 * s]),
+                                    tap5(w[5 - 2 * s], w[5 - s], w[5], w[5 + s], w[5 + 2 * s]),
+                                    tap5(w[6 - 2 * s], w[6 - s], w[6], w[6 + s], w[6 + 2 * s]),
+                                    tap5(w[7 - 2 * s], w[7 - s], w[7], w[7 + s], w[7 + 2 * s]));
                 } else {
-                    o0 = tap5(f4(row - 2 * s), f4(row - s), f4(row), f4(row + s), f4(row + 2 * s));
-                    o1 = tap5(f4(row + 4 - 2 * s), f4(row + 4 - s), f4(row + 4), f4(row + 4 + s),
-                              f4(row + 4 + 2 * s));
+                    o = tap5(f4(row - 2 * s), f4(row - s), f4(row), f4(row + s), f4(row + 2 * s));
                 }
-                sf4(Bf + i * P + x, o0);
-                sf4(Bf + i * P + x + 4, o1);
+                sf4(Bf + i * P + x, o);
             }
         }
         __syncthreads();
@@ -305,10 +299,11 @@ __global__ void __launch_bounds__(256) k_st_tile32(const float *__restrict__ in,
         {
             const int nr = TS + 2 * ha;  // divisible by 4 s
             const int groups = nr / (4 * s);
-            const int ntask = s * groups * ncq;
+            const int ntask = s * groups * ncqp;
             for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
-                const int qq = e % ncq;
-                const int rg = e / ncq;  // residue + s * group
+                const int qq = e % ncqp;
+                if (qq >= ncq) continue;
+                const int rg = e / ncqp;  // residue + s * group
                 const int r = rg % s, m = rg / s;
                 const int x = c_lo + qq * 4;
                 const int i0 = HP - ha + r + s * 4 * m;
