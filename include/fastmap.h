@@ -128,8 +128,11 @@ int fm_map_direct(const void *g1, const void *g2, void *map, int n, int filter, 
  * state `seed`; then KS + starlet.  var_out [(J-1)][n][n] (double) receives
  * the unbiased variance of each band over the R realisations (R >= 2);
  * snr_out (element type, same shape, or NULL) receives w_j(data)/sigma_j.
- * One map; n a power of two.  Scratch ~ (2 (J-1) * 8 + 40 * chunk) bytes per
- * pixel. */
+ * One map; n a power of two.  Realisations run in batches of up to 32
+ * through KS and the starlet; the whole call is recorded once into a CUDA
+ * graph (keyed by pointers, sizes, R, seed and config) and replayed as one
+ * launch.  Scratch: 16 (J-1) + ~20 * batch bytes per pixel (fp32), kept with
+ * the graph until fm_trim or eviction. */
 int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
                  const fm_config *cfg, void *stream);
 
@@ -193,6 +196,12 @@ int64_t fm_launch_count(void);     /* kernels launched by this library so far */
 #define FM_TUNE_CHUNK_BYTES 1
 #define FM_TUNE_GRAPHS 2
 int fm_tune(int knob, int64_t value);
+
+/* Batched fm_map_starlet calls (when chunked) and fm_map_noise calls are
+ * recorded once into CUDA graphs that keep their scratch (a few per kind,
+ * least recently used dropped first).  fm_trim waits for the device and
+ * frees all of them. */
+int fm_trim(void);
 
 /* Kernel ids for fm_profile_select. */
 #define FM_K_FFT_ROWS_FWD 1

@@ -204,11 +204,13 @@ static int check_J(int n, int J)
 
 // realisations per noise chunk: keep a chunk's working set (~20 B/px each
 // in fp32) near 64 MB so it stays in L2
+// realisations per batched pass: enough maps per launch to fill the GPU
+// (~256 MB of per-realisation working set), at most 32
 static int noise_chunk(int n, int R, size_t es)
 {
     const long nn = (long)n * n;
-    long chunk = (64L << 20) / (nn * 5 * (long)es);
-    chunk = chunk < 1 ? 1 : (chunk > 16 ? 16 : chunk);
+    long chunk = (256L << 20) / (nn * 5 * (long)es);
+    chunk = chunk < 1 ? 1 : (chunk > 32 ? 32 : chunk);
     return (int)(chunk > R ? R : chunk);
 }
 
@@ -481,6 +483,153 @@ static int map_starlet_dev(const void *g1, const void *g2, void *pyramid, int n,
     return FM_OK;
 }
 
+// ---- noise maps: R rotated realisations, batched, in one graph launch ------------
+namespace {
+
+struct NoiseLayout {
+    int chunk = 1;
+    size_t acc_b = 0, work_b = 0, kap_b = 0, st_b = 0, pyr_b = 0, total = 0;
+};
+
+NoiseLayout noise_layout(int n, int J, int R, const fm_config &cfg, bool with_snr)
+{
+    const size_t es = cfg.precision == FM_F64 ? 8 : 4;
+    const size_t nn = (size_t)n * n;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    NoiseLayout L;
+    L.chunk = noise_chunk(n, R, es);
+    L.acc_b = up(2 * (size_t)(J - 1) * nn * sizeof(double));
+    L.work_b = up((size_t)L.chunk * nn * 2 * es);
+    L.kap_b = up((size_t)L.chunk * nn * es);
+    L.st_b = up(starlet_scratch_elems(n, J, L.chunk, cfg) * es);
+    L.pyr_b = with_snr ? up((size_t)J * nn * es) : 0;
+    L.total = L.acc_b + L.work_b + L.kap_b + L.st_b + L.pyr_b;
+    return L;
+}
+
+// Everything of one fm_map_noise call, on one stream: zero the FP64 sums,
+// the unrotated pass (for S/N), every batch of rotated realisations (KS +
+// starlet accumulating S1 += w, S2 += w^2), then the finalize kernel.
+int noise_submit(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
+                 const fm_config &cfg, const NoiseLayout &L, char *scr, cudaStream_t s)
+{
+    const long nn = (long)n * n;
+    const long nb = (long)(J - 1) * nn;
+    double *s1 = reinterpret_cast<double *>(scr);
+    double *s2 = s1 + nb;
+    char *work = scr + L.acc_b, *kap = work + L.work_b, *st = kap + L.kap_b, *pyr = st + L.st_b;
+    int r;
+    FM_CUDA_TRY(cudaMemsetAsync(s1, 0, (size_t)2 * nb * sizeof(double), s));
+    if (snr_out) {
+        if ((r = launch_ks(g1, g2, nn, kap, nullptr, work, n, 1, cfg.precision, false, 0, 0, false, s))) return r;
+        if ((r = launch_starlet(kap, pyr, (long)J * nn, n, J, 1, cfg, st, nullptr, nullptr, s))) return r;
+    }
+    for (int r0 = 0; r0 < R; r0 += L.chunk) {
+        const int b = R - r0 < L.chunk ? R - r0 : L.chunk;
+        // every batch entry reads the same input map (batch stride 0) and
+        // rotates it with its own realisation index r0 + entry
+        if ((r = launch_ks(g1, g2, 0, kap, nullptr, work, n, b, cfg.precision, false, seed, r0, true, s))) return r;
+        if ((r = launch_starlet(kap, nullptr, 0, n, J, b, cfg, st, s1, s2, s))) return r;
+    }
+    return launch_noise_finalize(s1, s2, snr_out ? pyr : nullptr, var_out, snr_out, nb, R, cfg.precision, s);
+}
+
+struct NoiseKey {
+    const void *g1, *g2, *var, *snr;
+    int n, J, R, dev;
+    uint64_t seed;
+    fm_config cfg;
+    bool operator==(const NoiseKey &o) const
+    {
+        return g1 == o.g1 && g2 == o.g2 && var == o.var && snr == o.snr && n == o.n && J == o.J && R == o.R &&
+               dev == o.dev && seed == o.seed && memcmp(&cfg, &o.cfg, sizeof(cfg)) == 0;
+    }
+};
+struct NoiseGraph {
+    NoiseKey key;
+    cudaGraphExec_t exec = nullptr;
+    void *scratch = nullptr;
+    uint64_t used = 0;
+    int64_t kernels = 0;
+};
+std::vector<NoiseGraph> g_noise_graphs;  // guarded by g_ds_mu
+constexpr size_t kMaxNoiseGraphs = 2;
+
+void drop_noise_graph(NoiseGraph &e)
+{
+    cudaDeviceSynchronize();
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.scratch) cudaFree(e.scratch);
+    e.exec = nullptr;
+    e.scratch = nullptr;
+}
+
+}  // namespace
+
+// allow_graph: record the whole call once into a CUDA graph (kept with its
+// scratch, LRU of two) and replay it; otherwise launch eagerly with
+// stream-ordered scratch (the serving path, whose buffers change per call).
+int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
+                  const fm_config &cfg, cudaStream_t s, bool allow_graph)
+{
+    const NoiseLayout L = noise_layout(n, J, R, cfg, snr_out != nullptr);
+    int st = FM_OK;
+    if (!twiddles(n, cfg.precision, s, &st)) return st;  // tables before any capture
+    if (!allow_graph || g_prof_kid.load() != 0 || !g_use_graphs.load()) {
+        Scratch sc;
+        if ((st = scratch_alloc(sc, L.total, s))) return st;
+        return noise_submit(g1, g2, var_out, snr_out, n, J, R, seed, cfg, L, (char *)sc.p, s);
+    }
+    std::lock_guard<std::mutex> lk(g_ds_mu);
+    DevStreams *ds = nullptr;
+    if ((st = dev_streams(&ds))) return st;
+    NoiseKey key{g1, g2, var_out, snr_out, n, J, R, 0, seed, cfg};
+    FM_CUDA_TRY(cudaGetDevice(&key.dev));
+    NoiseGraph *hit = nullptr;
+    for (auto &e : g_noise_graphs)
+        if (e.key == key) hit = &e;
+    if (!hit) {
+        if (g_noise_graphs.size() >= kMaxNoiseGraphs) {
+            auto lru = std::min_element(g_noise_graphs.begin(), g_noise_graphs.end(),
+                                        [](const NoiseGraph &a, const NoiseGraph &b) { return a.used < b.used; });
+            drop_noise_graph(*lru);
+            g_noise_graphs.erase(lru);
+        }
+        NoiseGraph e;
+        e.key = key;
+        cudaError_t ce = cudaMalloc(&e.scratch, L.total);
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaMalloc (noise graph scratch)");
+        cudaGraph_t graph = nullptr;
+        ce = cudaStreamBeginCapture(ds->cap, cudaStreamCaptureModeRelaxed);
+        if (ce != cudaSuccess) {
+            cudaFree(e.scratch);
+            return cuda_fail(ce, "cudaStreamBeginCapture");
+        }
+        const int64_t before = g_launches.load();
+        st = noise_submit(g1, g2, var_out, snr_out, n, J, R, seed, cfg, L, (char *)e.scratch, ds->cap);
+        e.kernels = g_launches.load() - before;
+        g_launches.fetch_sub(e.kernels);
+        ce = cudaStreamEndCapture(ds->cap, &graph);
+        if (st == FM_OK && ce != cudaSuccess) st = cuda_fail(ce, "cudaStreamEndCapture");
+        if (st == FM_OK) {
+            ce = cudaGraphInstantiate(&e.exec, graph, 0);
+            if (ce != cudaSuccess) st = cuda_fail(ce, "cudaGraphInstantiate");
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (st != FM_OK) {
+            if (e.exec) cudaGraphExecDestroy(e.exec);
+            cudaFree(e.scratch);
+            return st;
+        }
+        g_noise_graphs.push_back(e);
+        hit = &g_noise_graphs.back();
+    }
+    hit->used = ++g_graph_clock;
+    FM_CUDA_TRY(cudaGraphLaunch(hit->exec, s));
+    g_launches.fetch_add(hit->kernels);
+    return FM_OK;
+}
+
 int map_starlet_run(const void *g1, const void *g2, void *pyramid, int n, int J, int batch, const fm_config &cfg,
                     cudaStream_t s)
 {
@@ -558,34 +707,17 @@ int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out,
     if ((st = check_J(n, J))) return st;
     if (R < 2) return einval("R must be >= 2");
     if (!g1 || !g2 || !var_out) return einval("null pointer");
-    cudaStream_t s = (cudaStream_t)stream;
-    const long nn = (long)n * n;
-    const size_t es = esize(cfg);
-    const long nb = (long)(J - 1) * nn;
-    const int chunk = noise_chunk(n, R, es);
-    Scratch acc, work, kap, ssc, pyr;
-    if ((st = scratch_alloc(acc, (size_t)2 * nb * sizeof(double), s))) return st;
-    double *s1 = static_cast<double *>(acc.p);
-    double *s2 = s1 + nb;
-    FM_CUDA_TRY(cudaMemsetAsync(s1, 0, (size_t)2 * nb * sizeof(double), s));
-    if ((st = scratch_alloc(work, (size_t)chunk * nn * 2 * es, s))) return st;
-    if ((st = scratch_alloc(kap, (size_t)chunk * nn * es, s))) return st;
-    if ((st = scratch_alloc(ssc, starlet_scratch_elems(n, J, chunk, cfg) * es, s))) return st;
-    if (snr_out) {
-        if ((st = scratch_alloc(pyr, (size_t)J * nn * es, s))) return st;
-        if ((st = launch_ks(g1, g2, nn, kap.p, nullptr, work.p, n, 1, cfg.precision, false, 0, 0, false, s)))
-            return st;
-        if ((st = launch_starlet(kap.p, pyr.p, (long)J * nn, n, J, 1, cfg, ssc.p, nullptr, nullptr, s))) return st;
-    }
-    for (int r0 = 0; r0 < R; r0 += chunk) {
-        const int b = R - r0 < chunk ? R - r0 : chunk;
-        // every batch entry reads the same input map (batch stride 0) and
-        // rotates it with its own realisation index r0 + b
-        if ((st = launch_ks(g1, g2, 0, kap.p, nullptr, work.p, n, b, cfg.precision, false, seed, r0, true, s)))
-            return st;
-        if ((st = launch_starlet(kap.p, nullptr, 0, n, J, b, cfg, ssc.p, s1, s2, s))) return st;
-    }
-    return launch_noise_finalize(s1, s2, pyr.p, var_out, snr_out, nb, R, cfg.precision, s);
+    return map_noise_run(g1, g2, var_out, snr_out, n, J, R, seed, cfg, (cudaStream_t)stream, true);
+}
+
+int fm_trim(void)
+{
+    std::lock_guard<std::mutex> lk(g_ds_mu);
+    for (auto &e : g_graphs) drop_graph(e);
+    g_graphs.clear();
+    for (auto &e : g_noise_graphs) drop_noise_graph(e);
+    g_noise_graphs.clear();
+    return FM_OK;
 }
 
 const char *fm_status_string(int status)

@@ -125,6 +125,8 @@ int launch_ks32(const float *in1, const float *in2, long in_bs, float *out1, flo
 size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg);
 int launch_map_direct(const void *g1, const void *g2, void *map, int n, int filter, double theta, int ell,
                       double cut, int precision, cudaStream_t s);
+int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
+                  const fm_config &cfg, cudaStream_t s, bool allow_graph);
 int launch_noise_finalize(const double *s1, const double *s2, const void *wdata, double *var, void *snr,
                           long nelem, int R, int precision, cudaStream_t s);
 

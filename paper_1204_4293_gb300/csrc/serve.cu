@@ -81,7 +81,7 @@ struct Server {
         cfg.precision = r.precision;
         int st = map_starlet_run(r.g1, r.g2, r.out_pyramid, r.n, r.J, 1, cfg, s);
         if (st == FM_OK && r.R >= 2 && r.out_var)
-            st = fm_map_noise(r.g1, r.g2, r.out_var, nullptr, r.n, r.J, r.R, r.seed, &cfg, s);
+            st = map_noise_run(r.g1, r.g2, r.out_var, nullptr, r.n, r.J, r.R, r.seed, cfg, s, false);
         return st;
     }
 

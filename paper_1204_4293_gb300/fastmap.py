@@ -70,6 +70,7 @@ _SIGS = {
     "fm_launch_count": (ctypes.c_int64, []),
     "fm_profile_select": (_I, [_I]),
     "fm_tune": (_I, [_I, ctypes.c_int64]),
+    "fm_trim": (_I, []),
     "fm_profile_read": (_I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -228,6 +229,11 @@ FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS = 1, 2
 def fm_tune(knob: int, value: int) -> None:
     """Process-wide tuning knob (FM_TUNE_*); value < 0 restores the default."""
     _check(_lib.fm_tune(int(knob), int(value)), "fm_tune")
+
+
+def fm_trim() -> None:
+    """Free the library's cached CUDA graphs and their scratch."""
+    _check(_lib.fm_trim(), "fm_trim")
 
 
 def fm_launch_count() -> int:

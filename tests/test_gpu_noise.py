@@ -44,3 +44,33 @@ def test_noise_paper_size_few_realisations():
     var = var.cpu().numpy()
     for j in range(J - 1):
         assert np.abs(var[j] - rv[j]).max() / rv[j].mean() <= 1e-4
+
+
+def test_noise_graph_replay_matches_eager_launches():
+    # fm_map_noise records the whole call into a CUDA graph and replays it;
+    # the replay, a second replay and eager launches must agree (up to the
+    # order of the FP64 atomic additions)
+    fm = _fm()
+    n, J, R = 128, 5, 40
+    g1, g2 = shear(n, seed=9, dtype=np.float32)
+    t1, t2 = torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda()
+    var = torch.empty(J - 1, n, n, dtype=torch.float64, device="cuda")
+    snr = torch.empty(J - 1, n, n, dtype=torch.float32, device="cuda")
+    c = fm._cfg(fm.FM_F32)
+    import ctypes
+    args = (ctypes.c_void_p(t1.data_ptr()), ctypes.c_void_p(t2.data_ptr()), ctypes.c_void_p(var.data_ptr()),
+            ctypes.c_void_p(snr.data_ptr()), n, J, R, ctypes.c_uint64(5), ctypes.byref(c),
+            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert fm.lib.fm_map_noise(*args) == 0
+    first = var.clone()
+    assert fm.lib.fm_map_noise(*args) == 0  # replay
+    second = var.clone()
+    fm.fm_tune(fm.FM_TUNE_GRAPHS, 0)
+    try:
+        assert fm.lib.fm_map_noise(*args) == 0  # eager
+    finally:
+        fm.fm_tune(fm.FM_TUNE_GRAPHS, -1)
+    torch.cuda.synchronize()
+    for other in (second, var):
+        assert torch.allclose(first, other, rtol=1e-12, atol=0)
+    fm.fm_trim()
