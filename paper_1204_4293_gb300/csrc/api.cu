@@ -224,10 +224,9 @@ size_t noise_scratch_bytes(int n, int J, int R, const fm_config &cfg, bool with_
 {
     const size_t es = esize(cfg), nn = (size_t)n * n;
     const int chunk = noise_chunk(n, R, es);
-    size_t b = 2 * (size_t)(J - 1) * nn * sizeof(double) + (size_t)chunk * nn * 3 * es +
-               starlet_scratch_elems(n, J, chunk, cfg) * es + 5 * 256;
-    if (with_snr) b += (size_t)J * nn * es;
-    return b;
+    (void)with_snr;
+    return 2 * (size_t)(J - 1) * nn * sizeof(double) + (size_t)chunk * nn * (3 + J) * es +
+           starlet_scratch_elems(n, J, chunk, cfg) * es + 5 * 256;
 }
 
 }  // namespace fm
@@ -502,7 +501,9 @@ NoiseLayout noise_layout(int n, int J, int R, const fm_config &cfg, bool with_sn
     L.work_b = up((size_t)L.chunk * nn * 2 * es);
     L.kap_b = up((size_t)L.chunk * nn * es);
     L.st_b = up(starlet_scratch_elems(n, J, L.chunk, cfg) * es);
-    L.pyr_b = with_snr ? up((size_t)J * nn * es) : 0;
+    // the batch's pyramids (the unrotated pass for S/N uses the first one)
+    L.pyr_b = up((size_t)L.chunk * J * nn * es);
+    (void)with_snr;
     L.total = L.acc_b + L.work_b + L.kap_b + L.st_b + L.pyr_b;
     return L;
 }
@@ -520,16 +521,20 @@ int noise_submit(const void *g1, const void *g2, double *var_out, void *snr_out,
     char *work = scr + L.acc_b, *kap = work + L.work_b, *st = kap + L.kap_b, *pyr = st + L.st_b;
     int r;
     FM_CUDA_TRY(cudaMemsetAsync(s1, 0, (size_t)2 * nb * sizeof(double), s));
-    if (snr_out) {
-        if ((r = launch_ks(g1, g2, nn, kap, nullptr, work, n, 1, cfg.precision, false, 0, 0, false, s))) return r;
-        if ((r = launch_starlet(kap, pyr, (long)J * nn, n, J, 1, cfg, st, nullptr, nullptr, s))) return r;
-    }
+    // S/N needs the unrotated bands after the batches reuse the pyramid buffer:
+    // finalize reads them from the first slot, so the data pass runs last
     for (int r0 = 0; r0 < R; r0 += L.chunk) {
         const int b = R - r0 < L.chunk ? R - r0 : L.chunk;
         // every batch entry reads the same input map (batch stride 0) and
-        // rotates it with its own realisation index r0 + entry
+        // rotates it with its own realisation index r0 + entry; the batch's
+        // bands are then summed into S1, S2 by one reduction pass
         if ((r = launch_ks(g1, g2, 0, kap, nullptr, work, n, b, cfg.precision, false, seed, r0, true, s))) return r;
-        if ((r = launch_starlet(kap, nullptr, 0, n, J, b, cfg, st, s1, s2, s))) return r;
+        if ((r = launch_starlet(kap, pyr, (long)J * nn, n, J, b, cfg, st, nullptr, nullptr, s))) return r;
+        if ((r = launch_noise_accum(pyr, b, (long)J * nn, nn, J - 1, s1, s2, cfg.precision, s))) return r;
+    }
+    if (snr_out) {
+        if ((r = launch_ks(g1, g2, nn, kap, nullptr, work, n, 1, cfg.precision, false, 0, 0, false, s))) return r;
+        if ((r = launch_starlet(kap, pyr, (long)J * nn, n, J, 1, cfg, st, nullptr, nullptr, s))) return r;
     }
     return launch_noise_finalize(s1, s2, snr_out ? pyr : nullptr, var_out, snr_out, nb, R, cfg.precision, s);
 }
