@@ -212,6 +212,7 @@ int fm_trim(void);
 #define FM_K_STARLET_COL 6
 #define FM_K_MAP_DIRECT 7
 #define FM_K_NOISE_FINAL 8
+#define FM_K_NOISE_ACCUM 9
 
 /* Bracket every later launch of kernel `kid` (0 = none) with CUDA events on
  * its launch stream; fm_profile_read synchronises those events and returns

@@ -4,30 +4,35 @@
 
 namespace fm {
 
-// S1 += sum_b w, S2 += sum_b w^2 over a batch of `nb` realisations' pyramids
-// ([nb][J][n][n], bands 0..J-2 used); one thread per 4 band pixels, FP64
-// sums in registers, one plain read-modify-write of S1 and S2 per batch.
-template <typename T>
+// S1 += sum_b w, S2 += sum_b w^2 over a batch of `nb` (<= 32) realisations'
+// pyramids ([nb][J][n][n], bands 0..J-2 used).  The batch's partial sums are
+// formed in the element type (at most 32 terms) and added once to the FP64
+// running sums: GB300's FP64 rate is a small fraction of its FP32 rate, so
+// the FP64 work is two additions per band pixel per batch.
+template <typename T, typename V>
 __global__ void __launch_bounds__(256) k_noise_accum(const T *__restrict__ pyr, int nb, long pyr_bs, long nn,
                                                      int bands, double *__restrict__ s1, double *__restrict__ s2)
 {
-    const long nq = bands * nn / 4;  // nn % 4 == 0 (n a power of two >= 4)
+    constexpr int VW = sizeof(V) / sizeof(T);
+    const long nq = bands * nn / VW;  // nn % 4 == 0 (n a power of two >= 4)
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nq; i += (long)gridDim.x * blockDim.x) {
-        const long e = i * 4;  // band-major element index: band * nn + pixel
-        double a[4] = {0, 0, 0, 0}, q[4] = {0, 0, 0, 0};
-        for (int b = 0; b < nb; ++b) {
-            const T *p = pyr + b * pyr_bs + e;
+        const long e = i * VW;  // band-major element index: band * nn + pixel
+        T a[VW], q[VW];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const double w = (double)__ldg(p + u);
-                a[u] += w;
-                q[u] += w * w;
+        for (int u = 0; u < VW; ++u) a[u] = q[u] = (T)0;
+        for (int b = 0; b < nb; ++b) {
+            const V v = __ldg(reinterpret_cast<const V *>(pyr + b * pyr_bs + e));
+            const T *w = reinterpret_cast<const T *>(&v);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) {
+                a[u] += w[u];
+                q[u] = fma(w[u], w[u], q[u]);
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            s1[e + u] += a[u];
-            s2[e + u] += q[u];
+        for (int u = 0; u < VW; ++u) {
+            s1[e + u] += (double)a[u];
+            s2[e + u] += (double)q[u];
         }
     }
 }
@@ -38,11 +43,11 @@ int launch_noise_accum(const void *pyr, int nb, long pyr_bs, long nn, int bands,
     long g = (bands * nn / 4 + 255) / 256;
     if (g > 152L * 16) g = 152L * 16;
     if (precision == FM_F64)
-        FM_LAUNCH(FM_K_NOISE_FINAL, k_noise_accum<double>, (unsigned)g, 256, 0, s, (const double *)pyr, nb, pyr_bs,
-                  nn, bands, s1, s2);
+        FM_LAUNCH(FM_K_NOISE_ACCUM, (k_noise_accum<double, double2>), (unsigned)g, 256, 0, s, (const double *)pyr,
+                  nb, pyr_bs, nn, bands, s1, s2);
     else
-        FM_LAUNCH(FM_K_NOISE_FINAL, k_noise_accum<float>, (unsigned)g, 256, 0, s, (const float *)pyr, nb, pyr_bs,
-                  nn, bands, s1, s2);
+        FM_LAUNCH(FM_K_NOISE_ACCUM, (k_noise_accum<float, float4>), (unsigned)g, 256, 0, s, (const float *)pyr, nb,
+                  pyr_bs, nn, bands, s1, s2);
     return FM_OK;
 }
 
