@@ -156,6 +156,14 @@ int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out,
 int fm_ks_invert_noalloc(const void *g1, const void *g2, void *kappa_E, void *kappa_B, int n, int batch,
                          const fm_config *cfg, void *stream);
 
+/* ---- statistics of the aperture-mass maps (Sec. 2.2) ----------------------------
+ * For every map b and pyramid array j of pyramid [batch][J][n][n] (any n),
+ * moments[(b*J + j)*4 + 0..3] = mean, variance <M_ap^2> (over the n^2
+ * pixels, divided by n^2), skewness and excess kurtosis.  Two passes; fp32
+ * partial sums of at most ~16 pixels per thread, FP64 across threads. */
+int fm_band_moments(const void *pyramid, double *moments, int n, int J, int batch, const fm_config *cfg,
+                    void *stream);
+
 /* ---- serving: continuous batching of map requests -------------------------- */
 typedef struct {
     int n, J, R;          /* R = 0: pyramid only; R >= 2: also noise variance */

@@ -715,6 +715,22 @@ int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out,
     return map_noise_run(g1, g2, var_out, snr_out, n, J, R, seed, cfg, (cudaStream_t)stream, true);
 }
 
+int fm_band_moments(const void *pyramid, double *moments, int n, int J, int batch, const fm_config *cfgp,
+                    void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if (n < 1 || n > 65536) return einval("n must be in [1, 65536]");
+    if (J < 1 || J > 20) return einval("J must be in [1, 20]");
+    if (batch < 1 || batch > 65535) return einval("batch must be in [1, 65535]");
+    if (!pyramid || !moments) return einval("null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc;
+    if ((st = scratch_alloc(sc, sizeof(double) * 4 * (size_t)batch * J, s))) return st;
+    return launch_band_moments(pyramid, moments, n, J, batch, cfg.precision, sc.p, s);
+}
+
 int fm_trim(void)
 {
     std::lock_guard<std::mutex> lk(g_ds_mu);

@@ -127,6 +127,8 @@ int launch_map_direct(const void *g1, const void *g2, void *map, int n, int filt
                       double cut, int precision, cudaStream_t s);
 int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
                   const fm_config &cfg, cudaStream_t s, bool allow_graph);
+int launch_band_moments(const void *pyr, double *moments, int n, int J, int batch, int precision, void *scratch,
+                        cudaStream_t s);
 int launch_noise_accum(const void *pyr, int nb, long pyr_bs, long nn, int bands, double *s1, double *s2,
                        int precision, cudaStream_t s);
 int launch_noise_finalize(const double *s1, const double *s2, const void *wdata, double *var, void *snr,

@@ -59,6 +59,7 @@ _SIGS = {
     "fm_map_starlet_host": (_I, [_P, _P, _P, _I, _I, _I, _CFG, _P]),
     "fm_map_direct": (_I, [_P, _P, _P, _I, _I, _D, _I, _D, _CFG, _P]),
     "fm_map_noise": (_I, [_P, _P, _P, _P, _I, _I, _I, _U64, _CFG, _P]),
+    "fm_band_moments": (_I, [_P, _P, _I, _I, _I, _CFG, _P]),
     "fm_serve_create": (_I, [_SZ, _I, ctypes.POINTER(ctypes.c_void_p)]),
     "fm_serve_submit": (_I, [_P, ctypes.POINTER(fm_request), ctypes.POINTER(ctypes.c_uint64)]),
     "fm_serve_poll": (_I, [_P, _U64, ctypes.POINTER(fm_result)]),
@@ -229,6 +230,20 @@ FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS = 1, 2
 def fm_tune(knob: int, value: int) -> None:
     """Process-wide tuning knob (FM_TUNE_*); value < 0 restores the default."""
     _check(_lib.fm_tune(int(knob), int(value)), "fm_tune")
+
+
+def fm_band_moments(pyramid, stream=None):
+    """[.., J, 4] float64: mean, variance, skewness, excess kurtosis of each
+    pyramid array over its pixels (Sec. 2.2)."""
+    if pyramid.dim() not in (3, 4) or not pyramid.is_cuda or not pyramid.is_contiguous():
+        raise ValueError("pyramid is a contiguous CUDA tensor [J, n, n] or [batch, J, n, n]")
+    batch = 1 if pyramid.dim() == 3 else pyramid.shape[0]
+    J, n = pyramid.shape[-3], pyramid.shape[-1]
+    out = torch.empty(tuple(pyramid.shape[:-2]) + (4,), dtype=torch.float64, device=pyramid.device)
+    c = _cfg(_prec(pyramid))
+    _check(_lib.fm_band_moments(_ptr(pyramid), _ptr(out), n, J, batch, ctypes.byref(c), _stream(stream)),
+           "fm_band_moments")
+    return out
 
 
 def fm_trim() -> None:

@@ -23,8 +23,10 @@ def _rng(seed: int) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(int(seed)))
 
 
-def grf_kappa(n: int, alpha: float = 2.0, rms: float = 0.02, seed: int = 1) -> np.ndarray:
-    """n x n float64 Gaussian random field with P(k) proportional to k^-alpha."""
+def grf_kappa(n: int, alpha: float = 2.0, rms: float | None = 0.02, seed: int = 1) -> np.ndarray:
+    """n x n float64 Gaussian random field with P(k) proportional to k^-alpha
+    (exactly |kappa_hat(k)|^2 = |k|^-alpha in expectation when rms is None;
+    otherwise rescaled to the given sample RMS)."""
     rng = _rng(seed)
     f = np.fft.fftfreq(n) * n
     k = np.sqrt(f[None, :] ** 2 + f[:, None] ** 2)
@@ -34,6 +36,8 @@ def grf_kappa(n: int, alpha: float = 2.0, rms: float = 0.02, seed: int = 1) -> n
     b = rng.standard_normal((n, n))
     field = np.real(np.fft.ifft2(amp * (a + 1j * b) / np.sqrt(2.0)))
     field -= field.mean()
+    if rms is None:
+        return field
     std = field.std()
     return field * (rms / std) if std > 0 else field
 
