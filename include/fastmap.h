@@ -197,12 +197,16 @@ const char *fm_last_error(void);   /* message of the calling thread's last error
 int64_t fm_launch_count(void);     /* kernels launched by this library so far */
 
 /* Tuning knobs (process-wide; value < 0 restores the default):
- *   FM_TUNE_CHUNK_BYTES  L2 budget of one chunk's intermediates in batched
- *                        KS + starlet calls; 0 = no chunking (the default)
+ *   FM_TUNE_CHUNK_BYTES  budget of one chunk's intermediates in batched
+ *                        KS + starlet calls (default 80 MiB, so two chunks in
+ *                        flight keep most of them in L2); 0 = no chunking
  *   FM_TUNE_GRAPHS       1 = replay batched calls from cached CUDA graphs
- *                        (default), 0 = launch every kernel each call */
+ *                        (default), 0 = launch every kernel each call
+ *   FM_TUNE_CHUNK_STREAMS number of streams chunks alternate on (1 or 2,
+ *                        default 2) */
 #define FM_TUNE_CHUNK_BYTES 1
 #define FM_TUNE_GRAPHS 2
+#define FM_TUNE_CHUNK_STREAMS 3
 int fm_tune(int knob, int64_t value);
 
 /* Batched fm_map_starlet calls (when chunked) and fm_map_noise calls are

@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__
 #pragma unroll
         for (int r = 0; r < 32; ++r) {
             const int x = j + r * P::TV;
-            float a = p1[x];
-            float cc = p2 ? p2[x] : 0.f;
+            float a = __ldcs(p1 + x);  // the shear is read once
+            float cc = p2 ? __ldcs(p2 + x) : 0.f;
             if (rotate) rotate_shear(a, cc, seed, r0 + b, y, x, P::N);
             v[r] = make_float2(a, cc);
         }

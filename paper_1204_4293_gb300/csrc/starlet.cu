@@ -60,12 +60,22 @@ template <typename T> __device__ __forceinline__ void st16(T *p, const T (&d)[16
     using V = typename Vec16<T>::V;
     *reinterpret_cast<V *>(p) = *reinterpret_cast<const V *>(d);
 }
+// streaming (evict-first) store for outputs nothing in the pipeline reads
+// again, so they do not push intermediates out of L2
+template <typename T> __device__ __forceinline__ void st16cs(T *p, const T (&d)[16 / sizeof(T)])
+{
+    using V = typename Vec16<T>::V;
+    __stcs(reinterpret_cast<V *>(p), *reinterpret_cast<const V *>(d));
+}
 
 // Store (or, in noise mode, accumulate) VW consecutive band values at
-// global pixel (gy, gx..gx+VW-1) of band `band` (1-based).
+// global pixel (gy, gx..gx+VW-1) of band `band` (1-based).  Band values are
+// final outputs and use streaming stores; `keep` selects plain stores (for
+// arrays a later kernel reads).
 template <typename T>
 __device__ __forceinline__ void emit_band(const T (&w)[16 / sizeof(T)], T *dst, long px, int gy, int gx, int n,
-                                          bool vec_ok, double *acc1, double *acc2, long acc_off, bool atomic)
+                                          bool vec_ok, double *acc1, double *acc2, long acc_off, bool atomic,
+                                          bool keep = false)
 {
     constexpr int VW = 16 / sizeof(T);
     if (gy >= n) return;
@@ -76,7 +86,10 @@ __device__ __forceinline__ void emit_band(const T (&w)[16 / sizeof(T)], T *dst, 
         return;
     }
     if (vec_ok && gx + VW <= n) {
-        st16(dst + px, w);
+        if (keep)
+            st16(dst + px, w);
+        else
+            st16cs(dst + px, w);
     } else {
 #pragma unroll
         for (int t = 0; t < VW; ++t)
@@ -190,7 +203,7 @@ __global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long 
                     const long px = (long)gy * n + gx;
                     emit_band<T>(w, w_out + b * w_bs + (long)(j - 1) * w_ss, px, gy, gx, n, vok, acc1, acc2,
                                  (long)(j - 1) * nn, acc_atomic != 0);
-                    if (j == F && c_out) emit_band<T>(cj, c_out + b * c_bs, px, gy, gx, n, vok, nullptr, nullptr, 0, false);
+                    if (j == F && c_out) emit_band<T>(cj, c_out + b * c_bs, px, gy, gx, n, vok, nullptr, nullptr, 0, false, true);
                 }
                 if (j < F) st16(A + i * P + x, cj);
             }
@@ -330,7 +343,7 @@ __global__ void __launch_bounds__(256) k_st_tile32(const float *__restrict__ in,
                                          (long)(j - 1) * nn, acc_atomic != 0);
                         if (j == F && c_out) {
                             alignas(16) float cc[4] = {c.x, c.y, c.z, c.w};
-                            emit_band<float>(cc, c_out + b * c_bs, px, gy, gx, n, vok, nullptr, nullptr, 0, false);
+                            emit_band<float>(cc, c_out + b * c_bs, px, gy, gx, n, vok, nullptr, nullptr, 0, false, true);
                         }
                     }
                     if (j < F) sf4(ap, c);
@@ -435,7 +448,7 @@ __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T
             w[u] = prev[u] - cj[u];
         }
         emit_band<T>(w, w_out + b * w_bs, px, y, x, n, vok, acc1, acc2, (long)(band - 1) * nn, acc_atomic != 0);
-        if (c_next) emit_band<T>(cj, c_next + b * next_bs, px, y, x, n, vok, nullptr, nullptr, 0, false);
+        if (c_next) emit_band<T>(cj, c_next + b * next_bs, px, y, x, n, vok, nullptr, nullptr, 0, false, true);
     }
 }
 
