@@ -144,12 +144,13 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def make_inputs(fm, torch, n, batch, seed, dtype):
-    """Seeded GRF shear maps (P(k) ~ k^-2, rms 0.02) + N(0, 0.1^2) shape noise,
-    built on the device: GRF on the host, forward KS through the library."""
+def make_inputs(fm, torch, n, batch, seed, dtype, distinct=None, alpha=2.0):
+    """Seeded GRF shear maps (P(k) ~ k^-alpha, rms 0.02) + N(0, 0.1^2) shape
+    noise, built on the device: GRF on the host, forward KS through the
+    library; `distinct` different fields are repeated over the batch."""
     from paper_1204_4293_gb300 import synth
-    distinct = min(batch, 8)
-    kap = np.stack([synth.grf_kappa(n, seed=seed + i) for i in range(distinct)]).astype(np.float32)
+    distinct = min(batch, 8) if distinct is None else distinct
+    kap = np.stack([synth.grf_kappa(n, alpha=alpha, seed=seed + i) for i in range(distinct)]).astype(np.float32)
     kd = torch.from_numpy(kap).cuda()
     g1, g2 = fm.fm_ks_forward(kd)
     reps = (batch + distinct - 1) // distinct
@@ -261,12 +262,31 @@ def side_legs(fm, torch, n, J, g1, g2):
     out["large_path_2"] = {"ms_per_step": ms_alt, "value": n * n * J * g1.shape[0] / (ms_alt * 1e-3) / 1e6}
     del pyr_b
     torch.cuda.empty_cache()
+    out["large_fields"] = large_fields_leg(fm, torch)
     out["serving"] = serving_leg(fm, torch)
     # batched noise maps: R realisations of KS + starlet with FP64 accumulation
     R = 1000
     fm.fm_map_noise(s1, s2, J, 8, seed=3)
     t_noise = cuda_time(torch, lambda: fm.fm_map_noise(s1, s2, J, R, seed=3), 1)
     out["noise"] = {"R": R, "ms": t_noise, "value": n * n * J * R / (t_noise * 1e-3) / 1e6, "unit": UNIT}
+    return out
+
+
+def large_fields_leg(fm, torch, J=9):
+    """Large fields, batched: 16 x 4096^2 and 1 x 8192^2 fp32 maps, P(k) ~
+    k^-2.5, starlet J = 9 (two distinct GRFs per size, repeated, plus shape
+    noise)."""
+    out = {}
+    for n, B in ((4096, 16), (8192, 1)):
+        g1, g2 = make_inputs(fm, torch, n, B, seed=40, dtype=torch.float32, distinct=min(B, 2), alpha=2.5)
+        pyr = torch.empty(B, J, n, n, dtype=torch.float32, device="cuda")
+        fn = lambda: fm.fm_map_starlet(g1, g2, J, out=pyr)  # noqa: E731
+        fn()
+        ms = cuda_time(torch, fn, 3)
+        out[f"{B}x{n}"] = {"ms": ms, "value": n * n * J * B / (ms * 1e-3) / 1e6, "unit": UNIT, "J": J,
+                           "hbm_algorithmic_gbs": (12 + 4 * (J + 1)) * n * n * B / (ms * 1e-3) / 1e9}
+        del g1, g2, pyr
+        torch.cuda.empty_cache()
     return out
 
 

@@ -58,3 +58,31 @@ def test_map_starlet_host_equals_device():
     torch.cuda.synchronize()
     dev = fm.fm_map_starlet(g1.cuda(), g2.cuda(), J).cpu()
     assert torch.equal(out, dev)
+
+
+def test_map_starlet_large_field_4096_j9():
+    # the large-field configuration: 4096^2, P(k) ~ k^-2.5, J = 9, a batch of
+    # two; the oracle checks the first map in full
+    fm = _fm()
+    n, J = 4096, 9
+    g1, g2 = shear(n, seed=40, alpha=2.5, dtype=np.float32)
+    t1 = torch.from_numpy(np.stack([g1, g1[::-1].copy()])).cuda()
+    t2 = torch.from_numpy(np.stack([g2, g2[::-1].copy()])).cuda()
+    pyr = fm.fm_map_starlet(t1, t2, J)
+    ref = oracle.map_starlet(g1.astype(np.float64), g2.astype(np.float64), J)
+    errs = band_errs(pyr[0].cpu().numpy(), ref)
+    assert max(errs) <= 1e-5, errs
+
+
+def test_map_starlet_8192_reconstruction_and_ks():
+    # the largest field: the pyramid sums back to kappa_E (exact reconstruction)
+    fm = _fm()
+    n, J = 8192, 9
+    from paper_1204_4293_gb300 import synth
+    kap = torch.from_numpy(synth.grf_kappa(n, alpha=2.5, seed=56).astype(np.float32)).cuda()
+    g1, g2 = fm.fm_ks_forward(kap)
+    pyr = fm.fm_map_starlet(g1, g2, J)
+    kE, _ = fm.fm_ks_invert(g1, g2)
+    rms = kap.double().pow(2).mean().sqrt().item()
+    assert (pyr.double().sum(0) - kE.double()).abs().max().item() / rms < 1e-5
+    assert (kE - kap).abs().max().item() / rms < 1e-5
