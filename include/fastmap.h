@@ -203,10 +203,13 @@ int64_t fm_launch_count(void);     /* kernels launched by this library so far */
  *   FM_TUNE_GRAPHS       1 = replay batched calls from cached CUDA graphs
  *                        (default), 0 = launch every kernel each call
  *   FM_TUNE_CHUNK_STREAMS number of streams chunks alternate on (1 or 2,
- *                        default 2) */
+ *                        default 2)
+ *   FM_TUNE_PDL          1 = launch kernels as programmatic dependents of
+ *                        the previous kernel in their stream (default), 0 = off */
 #define FM_TUNE_CHUNK_BYTES 1
 #define FM_TUNE_GRAPHS 2
 #define FM_TUNE_CHUNK_STREAMS 3
+#define FM_TUNE_PDL 4
 int fm_tune(int knob, int64_t value);
 
 /* Batched fm_map_starlet calls (when chunked) and fm_map_noise calls are

@@ -37,6 +37,7 @@ static int einval(const std::string &msg)
 
 // ---- launch accounting and profiling ------------------------------------------
 std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_pdl{1};
 
 namespace {
 struct Prof {
@@ -389,10 +390,12 @@ struct GraphKey {
     const void *g1, *g2, *pyr;
     int n, J, batch, dev;
     fm_config cfg;
+    int chunk, slots, pdl;  // the plan and launch mode the graph was recorded with
     bool operator==(const GraphKey &o) const
     {
         return g1 == o.g1 && g2 == o.g2 && pyr == o.pyr && n == o.n && J == o.J && batch == o.batch &&
-               dev == o.dev && memcmp(&cfg, &o.cfg, sizeof(cfg)) == 0;
+               dev == o.dev && memcmp(&cfg, &o.cfg, sizeof(cfg)) == 0 && chunk == o.chunk && slots == o.slots &&
+               pdl == o.pdl;
     }
 };
 struct GraphEntry {
@@ -438,7 +441,7 @@ static int map_starlet_dev(const void *g1, const void *g2, void *pyramid, int n,
         if ((st = scratch_alloc(sc, p.slot_b * p.slots, s))) return st;
         return run_chunks(g1, g2, pyramid, n, J, batch, cfg, p, (char *)sc.p, s, *ds);
     }
-    GraphKey key{g1, g2, pyramid, n, J, batch, 0, cfg};
+    GraphKey key{g1, g2, pyramid, n, J, batch, 0, cfg, p.C, p.slots, g_pdl.load()};
     FM_CUDA_TRY(cudaGetDevice(&key.dev));
     GraphEntry *hit = nullptr;
     for (auto &e : g_graphs)
@@ -547,10 +550,11 @@ struct NoiseKey {
     int n, J, R, dev;
     uint64_t seed;
     fm_config cfg;
+    int pdl;
     bool operator==(const NoiseKey &o) const
     {
         return g1 == o.g1 && g2 == o.g2 && var == o.var && snr == o.snr && n == o.n && J == o.J && R == o.R &&
-               dev == o.dev && seed == o.seed && memcmp(&cfg, &o.cfg, sizeof(cfg)) == 0;
+               dev == o.dev && seed == o.seed && memcmp(&cfg, &o.cfg, sizeof(cfg)) == 0 && pdl == o.pdl;
     }
 };
 struct NoiseGraph {
@@ -591,7 +595,7 @@ int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out
     std::lock_guard<std::mutex> lk(g_ds_mu);
     DevStreams *ds = nullptr;
     if ((st = dev_streams(&ds))) return st;
-    NoiseKey key{g1, g2, var_out, snr_out, n, J, R, 0, seed, cfg};
+    NoiseKey key{g1, g2, var_out, snr_out, n, J, R, 0, seed, cfg, g_pdl.load()};
     FM_CUDA_TRY(cudaGetDevice(&key.dev));
     NoiseGraph *hit = nullptr;
     for (auto &e : g_noise_graphs)
@@ -768,6 +772,7 @@ int fm_tune(int knob, int64_t value)
     case FM_TUNE_CHUNK_BYTES: g_chunk_bytes.store(value < 0 ? kDefaultChunkBytes : value); return FM_OK;
     case FM_TUNE_GRAPHS: g_use_graphs.store(value < 0 ? 1 : (value != 0)); return FM_OK;
     case FM_TUNE_CHUNK_STREAMS: g_chunk_streams.store(value < 0 ? 2 : (value >= 2 ? 2 : 1)); return FM_OK;
+    case FM_TUNE_PDL: g_pdl.store(value < 0 ? 1 : (value != 0)); return FM_OK;
     }
     return einval("unknown tuning knob");
 }

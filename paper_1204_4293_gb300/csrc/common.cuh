@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <string>
+#include <utility>
 
 #include "../../include/fastmap.h"
 
@@ -32,15 +33,44 @@ extern std::atomic<int64_t> g_launches;
 void prof_before(int kid, cudaStream_t s);
 void prof_after(int kid, cudaStream_t s);
 
+// Programmatic dependent launch: every kernel of the library starts with
+// pdl_entry(), which waits until the kernel it depends on in the stream has
+// finished (a no-op when launched without the attribute) and then lets the
+// next kernel's CTAs be scheduled into SMs this grid leaves idle in its tail.
+extern std::atomic<int> g_pdl;
+__device__ __forceinline__ void pdl_entry()
+{
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    cudaGridDependencySynchronize();
+    cudaTriggerProgrammaticLaunchCompletion();
+#endif
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = g_pdl.load(std::memory_order_relaxed) ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Launch helper: counts the launch, brackets it with profiling events when
 // that kernel id is selected, and checks the launch status.
-#define FM_LAUNCH(kid, kernel, grid, block, smem, stream, ...)           \
-    do {                                                                 \
-        fm::prof_before(kid, stream);                                    \
-        kernel<<<grid, block, smem, stream>>>(__VA_ARGS__);              \
-        fm::g_launches.fetch_add(1, std::memory_order_relaxed);          \
-        FM_CHECK_LAUNCH(#kernel);                                        \
-        fm::prof_after(kid, stream);                                     \
+#define FM_LAUNCH(kid, kernel, grid, block, smem, stream, ...)                              \
+    do {                                                                                    \
+        fm::prof_before(kid, stream);                                                       \
+        cudaError_t le_ = fm::launch_ex(kernel, dim3(grid), dim3(block), smem, stream, __VA_ARGS__); \
+        fm::g_launches.fetch_add(1, std::memory_order_relaxed);                             \
+        if (le_ != cudaSuccess) return fm::cuda_fail(le_, #kernel);                          \
+        fm::prof_after(kid, stream);                                                        \
     } while (0)
 
 // ---- complex helpers ----------------------------------------------------------

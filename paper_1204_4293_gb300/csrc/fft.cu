@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T *__restrict__ in1, co
                                                    int lognvec, long total_rows, const cplx_t<T> *__restrict__ tw,
                                                    uint64_t seed, int r0, int rotate)
 {
+    pdl_entry();
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *buf = reinterpret_cast<V *>(smem_raw);
@@ -142,6 +143,7 @@ template <typename T, int E>
 __global__ void __launch_bounds__(1024) k_cols_ks(cplx_t<T> *__restrict__ work, int n, int logn, int logw,
                                                   const cplx_t<T> *__restrict__ tw, int forward)
 {
+    pdl_entry();
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *buf = reinterpret_cast<V *>(smem_raw);
@@ -188,6 +190,7 @@ __global__ void __launch_bounds__(1024) k_rows_inv(const cplx_t<T> *__restrict__
                                                    T *__restrict__ out2, int n, int logn, int lognvec,
                                                    long total_rows, const cplx_t<T> *__restrict__ tw, T scale)
 {
+    pdl_entry();
     using V = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *buf = reinterpret_cast<V *>(smem_raw);

@@ -93,6 +93,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__
                                                        const float2 *__restrict__ tw, uint64_t seed, int r0,
                                                        int rotate)
 {
+    pdl_entry();
     using P = Plan32<LOGN>;
     constexpr int RPC = P::TV >= 256 ? 1 : 256 / P::TV;
     extern __shared__ __align__(16) float2 sm32[];
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_inv32(const float2 *__restrict_
                                                        float *__restrict__ out2, long total_rows,
                                                        const float2 *__restrict__ tw, float scale)
 {
+    pdl_entry();
     using P = Plan32<LOGN>;
     constexpr int RPC = P::TV >= 256 ? 1 : 256 / P::TV;
     extern __shared__ __align__(16) float2 sm32[];
@@ -162,6 +164,7 @@ template <int LOGN>
 __global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, const float2 *__restrict__ tw,
                                                    int forward)
 {
+    pdl_entry();
     using P = Plan32<LOGN>;
     constexpr int W = P::W, N = P::N;
     constexpr int STRIPS = N / W;

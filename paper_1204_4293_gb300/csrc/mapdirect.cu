@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(NW * 32) k_map_direct(const T *__restrict__ g1
                                                         const int *__restrict__ dxmax, T *__restrict__ out, int n,
                                                         int Ri)
 {
+    pdl_entry();
     using V = cplx_t<T>;
     constexpr int TX = 32 * CX, TY = NW * RY;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -22,6 +22,7 @@ __device__ __forceinline__ double warp_sum(double v)
 template <typename T, int PASS>
 __global__ void __launch_bounds__(256) k_moments(const T *__restrict__ pyr, long nn, int J, double *__restrict__ sums)
 {
+    pdl_entry();
     const long b = blockIdx.z;
     const int j = blockIdx.y;
     const T *x = pyr + (b * J + j) * nn;
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(256) k_moments(const T *__restrict__ pyr, long
 // moments[(b * J + j) * 4 + {0,1,2,3}] = mean, variance, skewness, excess kurtosis
 __global__ void k_moments_final(const double *__restrict__ sums, double *__restrict__ out, long nn, int count)
 {
+    pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const double *s = sums + 4 * (long)i;

@@ -13,6 +13,7 @@ template <typename T, typename V>
 __global__ void __launch_bounds__(256) k_noise_accum(const T *__restrict__ pyr, int nb, long pyr_bs, long nn,
                                                      int bands, double *__restrict__ s1, double *__restrict__ s2)
 {
+    pdl_entry();
     constexpr int VW = sizeof(V) / sizeof(T);
     const long nq = bands * nn / VW;  // nn % 4 == 0 (n a power of two >= 4)
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nq; i += (long)gridDim.x * blockDim.x) {
@@ -56,6 +57,7 @@ __global__ void k_noise_final(const double *__restrict__ s1, const double *__res
                               const T *__restrict__ wdata, double *__restrict__ var, T *__restrict__ snr, long nelem,
                               int R)
 {
+    pdl_entry();
     const double invR = 1.0 / R, invR1 = 1.0 / (R - 1);
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nelem; i += (long)gridDim.x * blockDim.x) {
         const double a = s1[i], q = s2[i];

@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long 
                                                  int tiles_x, int tiles_per_map, double *__restrict__ acc1,
                                                  double *__restrict__ acc2, int acc_atomic, int vec_ok)
 {
+    pdl_entry();
     constexpr int VW = 16 / sizeof(T);
     constexpr int H = (1 << (F + 1)) - 2;
     constexpr int HP = ((H + 3) / 4) * 4;
@@ -240,6 +241,7 @@ __global__ void __launch_bounds__(256) k_st_tile32(const float *__restrict__ in,
                                                    double *__restrict__ acc1, double *__restrict__ acc2,
                                                    int acc_atomic, int vec_ok)
 {
+    pdl_entry();
     constexpr int TS = 64;
     constexpr int H = (1 << (F + 1)) - 2;
     constexpr int HP = ((H + 3) / 4) * 4;
@@ -361,6 +363,7 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_st_row(const T *__restrict__ c, long c_bs, T *__restrict__ r, int n, int s,
                                                 int boundary, int vec_ok)
 {
+    pdl_entry();
     constexpr int VW = 16 / sizeof(T);
     const int x = (blockIdx.x * blockDim.x + threadIdx.x) * VW;
     if (x >= n) return;
@@ -407,6 +410,7 @@ __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T
                                                 int boundary, int band, double *__restrict__ acc1,
                                                 double *__restrict__ acc2, int acc_atomic, int vec_ok)
 {
+    pdl_entry();
     constexpr int VW = 16 / sizeof(T);
     const int x = (blockIdx.x * blockDim.x + threadIdx.x) * VW;
     if (x >= n) return;
@@ -466,6 +470,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_st_rows_multi(const T *__restrict__ c, long c_bs, T *__restrict__ u_out,
                                                        long u_ks, int n, int a, int K, int boundary)
 {
+    pdl_entry();
     constexpr int VW = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf0 = reinterpret_cast<T *>(smem_raw);
@@ -523,6 +528,7 @@ __global__ void __launch_bounds__(512) k_st_cols_multi(const T *__restrict__ c_a
                                                        int a, int K, int boundary, double *__restrict__ acc1,
                                                        double *__restrict__ acc2, int acc_atomic)
 {
+    pdl_entry();
     constexpr int VW = 16 / sizeof(T);
     constexpr int QW = W / VW;  // vectors per row of the strip
     extern __shared__ __align__(16) unsigned char smem_raw[];

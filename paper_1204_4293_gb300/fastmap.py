@@ -224,7 +224,7 @@ def fm_map_noise(g1, g2, J, R, seed, boundary=FM_MIRROR, with_snr=True, fuse_dep
     return var, snr
 
 
-FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS, FM_TUNE_CHUNK_STREAMS = 1, 2, 3
+FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS, FM_TUNE_CHUNK_STREAMS, FM_TUNE_PDL = 1, 2, 3, 4
 
 
 def fm_tune(knob: int, value: int) -> None:
