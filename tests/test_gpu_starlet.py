@@ -74,3 +74,33 @@ def test_starlet_full_size_paper_config():
         ref = oracle.starlet(maps[b].astype(np.float64), J)
         errs = band_errs(pyr[b], ref)
         assert max(errs) <= 1e-5, errs
+
+
+@pytest.mark.parametrize("n,J,dtype", [(2048, 8, np.float32), (4096, 6, np.float64)])
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_starlet_wide_rows(n, J, dtype, boundary):
+    # long rows at large scales (2048 fp32 and 4096 fp64 pixels per row)
+    fm = _fm()
+    kappa = (synth.grf_kappa(n, seed=n + 1) + synth.white((n, n), seed=3, scale=0.05)).astype(dtype)
+    ref = oracle.starlet(kappa.astype(np.float64), J, boundary)
+    pyr = fm.fm_starlet_forward(torch.from_numpy(kappa).cuda(), J, boundary=boundary).cpu().numpy()
+    assert max(band_errs(pyr, ref)) <= TOL[dtype]
+
+
+def test_starlet_8192_windows_match_oracle():
+    # 8192^2, J = 9: c_8 sees at most 2 (2^8 - 1) = 510 pixels away, so on a
+    # 2048^2 crop every pixel >= 510 from a cut edge (a map edge is no cut
+    # edge: the crop keeps it and its mirror) equals the full map's value.
+    fm = _fm()
+    n, J, w, h = 8192, 9, 2048, 510
+    kappa = synth.grf_kappa(n, alpha=2.5, seed=57).astype(np.float32)
+    pyr = fm.fm_starlet_forward(torch.from_numpy(kappa).cuda(), J)
+    for y0, x0 in [(0, 0), (3000, 5000), (n - w, n - w), (0, 4000)]:
+        ref = oracle.starlet(kappa[y0:y0 + w, x0:x0 + w].astype(np.float64), J)
+        ya = 0 if y0 == 0 else h
+        yb = w if y0 + w == n else w - h
+        xa = 0 if x0 == 0 else h
+        xb = w if x0 + w == n else w - h
+        got = pyr[:, y0 + ya:y0 + yb, x0 + xa:x0 + xb].cpu().numpy()
+        errs = band_errs(got, ref[:, ya:yb, xa:xb])
+        assert max(errs) <= 1e-5, ((y0, x0), errs)
