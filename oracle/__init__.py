@@ -9,6 +9,8 @@ Each wrapper names the paper passage its C function follows:
   ks_forward / ks_invert   Sec. 4.5 (Kaiser-Squires in Fourier space)
   starlet                  Sec. 3 and Sec. 4.2 (a trous B3-spline starlet)
   map_direct               eq. shearmap (Sec. 2.1), brute force as in Sec. 5.1
+  map_direct_masked        eq. shearmap with pixel weights for missing data
+                           (Sec. 4.3, Sec. 4.5)
   map_noise                Sec. 1 and Sec. 5.1 (randomised-data noise maps)
   u_/q_ filters            eq. sch, eq. mexhat, the starlet U and Q (Sec. 4)
 """
@@ -67,6 +69,8 @@ def _load():
             "oracle_map_starlet": (None, [_D, _D, _D, c_int, c_int, c_int]),
             "oracle_map_direct": (None, [_D, _D, _D, c_int, c_int, c_double, c_int, c_double]),
             "oracle_map_direct_at": (None, [_D, _D, _I, _I, c_int, _D, c_int, c_int, c_double, c_int, c_double]),
+            "oracle_map_direct_masked_at": (None, [_D, _D, _D, _I, _I, c_int, _D, _D, c_int, c_int, c_double, c_int,
+                                                    c_double]),
             "oracle_splitmix64": (c_u64, [c_u64, c_u64]),
             "oracle_noise_u": (c_double, [c_u64, c_int, c_int, c_int, c_int]),
             "oracle_rotate_shear": (None, [_D, _D, _D, _D, c_int, c_int, c_u64]),
@@ -218,6 +222,30 @@ def map_direct_at(g1, g2, ys, xs, filt, theta, ell=3, cut_over_theta=0.0):
     _load().oracle_map_direct_at(_p(a), _p(b), ys.ctypes.data_as(_I), xs.ctypes.data_as(_I), len(ys), _p(out), n,
                                  int(filt), float(theta), int(ell), float(cut_over_theta))
     return out
+
+
+def map_direct_masked_at(g1, g2, w, ys, xs, filt, theta, ell=3, cut_over_theta=0.0):
+    """Weighted direct M_ap (missing data, Sec. 4.3 and 4.5) at listed pixels:
+    returns (M, coverage) with M = N_R sum w Q gamma_t / sum w."""
+    a = _in(g1)
+    n = _n_of(a)
+    b = _in(g2, n)
+    c = _in(w, n)
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    m = np.empty(len(ys))
+    cov = np.empty(len(ys))
+    _load().oracle_map_direct_masked_at(_p(a), _p(b), _p(c), ys.ctypes.data_as(_I), xs.ctypes.data_as(_I), len(ys),
+                                        _p(m), _p(cov), n, int(filt), float(theta), int(ell), float(cut_over_theta))
+    return m, cov
+
+
+def map_direct_masked(g1, g2, w, filt, theta, ell=3, cut_over_theta=0.0):
+    """Weighted direct M_ap over the whole map: (M, coverage), each n x n."""
+    n = _n_of(_in(g1))
+    ys, xs = np.mgrid[0:n, 0:n]
+    m, cov = map_direct_masked_at(g1, g2, w, ys.ravel(), xs.ravel(), filt, theta, ell, cut_over_theta)
+    return m.reshape(n, n), cov.reshape(n, n)
 
 
 def splitmix64(seed, index):

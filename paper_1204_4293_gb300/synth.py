@@ -10,7 +10,10 @@ data set; a Gaussian random field stands in for its convergence maps):
   kappa_hat(k) = |k|^(-alpha/2) (a + i b) / sqrt(2), a, b ~ N(0, 1) iid,
   |k| in integer frequency units, kappa_hat(0) = 0;
   kappa = Re IFFT2(kappa_hat), rescaled to the requested RMS (default 0.02);
-  shape noise: N(0, sigma^2) per pixel per shear component (default 0.1).
+  shape noise: N(0, sigma^2) per pixel per shear component (default 0.1);
+  masks (missing data: bright stars, bad pixels): 0/1 weights with discs of
+  log-uniform radius at uniform centres until the masked fraction is reached,
+  plus one bad column strip.
 The shear of a field is obtained by the caller through a forward
 Kaiser-Squires transform (the oracle's in tests, the library's on the GPU).
 """
@@ -58,3 +61,22 @@ def delta_kappa(n: int, amplitude: float = 1.0) -> np.ndarray:
 def white(shape, seed: int = 1, scale: float = 1.0) -> np.ndarray:
     """iid N(0, scale^2) values (generic test input)."""
     return scale * _rng(seed).standard_normal(shape)
+
+
+def star_mask(n: int, frac: float = 0.15, r_min: float = 2.0, r_max: float | None = None, seed: int = 1) -> np.ndarray:
+    """n x n float64 weights: 1 for data, 0 inside masked discs (stars) and one
+    bad 2-pixel column strip, drawn until about `frac` of the field is masked."""
+    rng = _rng(seed + 0xA5C)
+    r_max = max(r_min, n / 32.0) if r_max is None else r_max
+    w = np.ones((n, n))
+    yy, xx = np.mgrid[0:n, 0:n]
+    if n >= 8:
+        c = int(rng.integers(0, n - 2))
+        w[:, c:c + 2] = 0.0
+    for _ in range(100000):
+        if 1.0 - w.mean() >= frac:
+            break
+        cy, cx = rng.random(2) * n
+        r = float(np.exp(rng.uniform(np.log(r_min), np.log(r_max))))
+        w[(yy - cy) ** 2 + (xx - cx) ** 2 <= r * r] = 0.0
+    return w
