@@ -122,6 +122,25 @@ int fm_map_starlet_host(const void *g1_host, const void *g2_host, void *pyramid_
 int fm_map_direct(const void *g1, const void *g2, void *map, int n, int filter, double theta_px, int ell,
                   double cut_over_theta, const fm_config *cfg, void *stream);
 
+/* ---- direct M_ap with missing data (Sec. 4.3, Sec. 4.5) -----------------------
+ * The paper notes that masks (bright stars, bad pixels) and field edges
+ * leave pixels without data and that the brute-force aperture sum suffers
+ * more the larger the aperture.  This call weights each pixel: weight[y][x]
+ * >= 0, 0 for a masked pixel (a galaxy count or inverse variance also
+ * works).  Over the lattice offsets 0 < |d| <= R inside the field,
+ *   S(x) = sum w(x+d) Q(|d|) gamma_t(x+d; x),   D(x) = sum w(x+d),
+ *   map(x) = N_R S(x) / D(x)  (0 where D(x) <= 0),
+ *   coverage(x) = D(x) / N_R  (NULL: not written),
+ * N_R = number of lattice offsets 0 < |d| <= R.  With all weights 1 and the
+ * aperture inside the field this is fm_map_direct's value.  g1, g2, map and
+ * coverage are [batch][n][n]; weight map b starts at weight + b *
+ * weight_bstride elements (0: one weight map for the whole batch).  Element
+ * type per cfg precision; R as in fm_map_direct and >= 1.  Arguments are
+ * checked on the host (FM_EINVAL); weights are not read on the host. */
+int fm_map_direct_masked(const void *g1, const void *g2, const void *weight, long weight_bstride, void *map,
+                         void *coverage, int n, int batch, int filter, double theta_px, int ell,
+                         double cut_over_theta, const fm_config *cfg, void *stream);
+
 /* ---- noise maps by randomised shear (Sec. 1, Sec. 5.1) ------------------------
  * Realisation r rotates every pixel's shear by 2 alpha, alpha = pi u with u
  * the top 24 bits (times 2^-24) of SplitMix64 at counter (r*n + y)*n + x from
@@ -205,11 +224,16 @@ int64_t fm_launch_count(void);     /* kernels launched by this library so far */
  *   FM_TUNE_CHUNK_STREAMS number of streams chunks alternate on (1 or 2,
  *                        default 2)
  *   FM_TUNE_PDL          1 = launch kernels as programmatic dependents of
- *                        the previous kernel in their stream (default), 0 = off */
+ *                        the previous kernel in their stream (default), 0 = off
+ *   FM_TUNE_TILE         fp32 kernel of the fused small starlet scales:
+ *                        0 = row-filtered shared buffer, 1 = register
+ *                        window, fewest serial rows per thread (default),
+ *                        2 = register window, least shared-memory traffic */
 #define FM_TUNE_CHUNK_BYTES 1
 #define FM_TUNE_GRAPHS 2
 #define FM_TUNE_CHUNK_STREAMS 3
 #define FM_TUNE_PDL 4
+#define FM_TUNE_TILE 5
 int fm_tune(int knob, int64_t value);
 
 /* Batched fm_map_starlet calls (when chunked) and fm_map_noise calls are

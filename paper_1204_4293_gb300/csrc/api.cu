@@ -38,6 +38,7 @@ static int einval(const std::string &msg)
 // ---- launch accounting and profiling ------------------------------------------
 std::atomic<int64_t> g_launches{0};
 std::atomic<int> g_pdl{1};
+std::atomic<int> g_tile_variant{1};
 
 namespace {
 struct Prof {
@@ -390,7 +391,7 @@ struct GraphKey {
     const void *g1, *g2, *pyr;
     int n, J, batch, dev;
     fm_config cfg;
-    int chunk, slots, pdl;  // the plan and launch mode the graph was recorded with
+    int chunk, slots, pdl;  // the plan and launch mode (PDL bit, tile variant) the graph was recorded with
     bool operator==(const GraphKey &o) const
     {
         return g1 == o.g1 && g2 == o.g2 && pyr == o.pyr && n == o.n && J == o.J && batch == o.batch &&
@@ -441,7 +442,7 @@ static int map_starlet_dev(const void *g1, const void *g2, void *pyramid, int n,
         if ((st = scratch_alloc(sc, p.slot_b * p.slots, s))) return st;
         return run_chunks(g1, g2, pyramid, n, J, batch, cfg, p, (char *)sc.p, s, *ds);
     }
-    GraphKey key{g1, g2, pyramid, n, J, batch, 0, cfg, p.C, p.slots, g_pdl.load()};
+    GraphKey key{g1, g2, pyramid, n, J, batch, 0, cfg, p.C, p.slots, g_pdl.load() | (g_tile_variant.load() << 1)};
     FM_CUDA_TRY(cudaGetDevice(&key.dev));
     GraphEntry *hit = nullptr;
     for (auto &e : g_graphs)
@@ -595,7 +596,7 @@ int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out
     std::lock_guard<std::mutex> lk(g_ds_mu);
     DevStreams *ds = nullptr;
     if ((st = dev_streams(&ds))) return st;
-    NoiseKey key{g1, g2, var_out, snr_out, n, J, R, 0, seed, cfg, g_pdl.load()};
+    NoiseKey key{g1, g2, var_out, snr_out, n, J, R, 0, seed, cfg, g_pdl.load() | (g_tile_variant.load() << 1)};
     FM_CUDA_TRY(cudaGetDevice(&key.dev));
     NoiseGraph *hit = nullptr;
     for (auto &e : g_noise_graphs)
@@ -703,7 +704,31 @@ int fm_map_direct(const void *g1, const void *g2, void *map, int n, int filter, 
                      theta_px;
     if (R > 2048) return einval("cut radius above 2048 px");
     if (!g1 || !g2 || !map) return einval("null pointer");
-    return launch_map_direct(g1, g2, map, n, filter, theta_px, ell, cut, cfg.precision, (cudaStream_t)stream);
+    return launch_map_direct(g1, g2, nullptr, 0, map, nullptr, n, 1, filter, theta_px, ell, cut, cfg.precision,
+                             (cudaStream_t)stream);
+}
+
+int fm_map_direct_masked(const void *g1, const void *g2, const void *weight, long weight_bstride, void *map,
+                         void *coverage, int n, int batch, int filter, double theta_px, int ell,
+                         double cut_over_theta, const fm_config *cfgp, void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if (n < 1 || n > 65536) return einval("n must be in [1, 65536]");
+    if (batch < 1 || batch > 65535) return einval("batch must be in [1, 65535]");
+    if (weight_bstride < 0) return einval("weight_bstride must be >= 0");
+    if (filter < FM_FILTER_STARLET || filter > FM_FILTER_VW98) return einval("unknown filter");
+    if (!(theta_px > 0) || theta_px > 4096) return einval("theta_px must be in (0, 4096]");
+    if (filter == FM_FILTER_S98 && (ell < 0 || ell > 64)) return einval("ell must be in [0, 64]");
+    const double cut = cut_over_theta > 0 ? cut_over_theta : 0.0;
+    const double R = (cut > 0 ? cut : (filter == FM_FILTER_STARLET ? 2.0 : filter == FM_FILTER_S98 ? 1.0 : 5.0)) *
+                     theta_px;
+    if (R > 2048) return einval("cut radius above 2048 px");
+    if (R < 1) return einval("cut radius below one pixel: the aperture holds no pixel");
+    if (!g1 || !g2 || !weight || !map) return einval("null pointer");
+    return launch_map_direct(g1, g2, weight, weight_bstride, map, coverage, n, batch, filter, theta_px, ell, cut,
+                             cfg.precision, (cudaStream_t)stream);
 }
 
 // Noise maps (Sec. 1): one unrotated pass for w_j(data), then R rotated
@@ -773,6 +798,10 @@ int fm_tune(int knob, int64_t value)
     case FM_TUNE_GRAPHS: g_use_graphs.store(value < 0 ? 1 : (value != 0)); return FM_OK;
     case FM_TUNE_CHUNK_STREAMS: g_chunk_streams.store(value < 0 ? 2 : (value >= 2 ? 2 : 1)); return FM_OK;
     case FM_TUNE_PDL: g_pdl.store(value < 0 ? 1 : (value != 0)); return FM_OK;
+    case FM_TUNE_TILE:
+        if (value > 2) return einval("FM_TUNE_TILE takes 0, 1 or 2");
+        g_tile_variant.store(value < 0 ? 1 : (int)value);
+        return FM_OK;
     }
     return einval("unknown tuning knob");
 }

@@ -38,6 +38,7 @@ void prof_after(int kid, cudaStream_t s);
 // finished (a no-op when launched without the attribute) and then lets the
 // next kernel's CTAs be scheduled into SMs this grid leaves idle in its tail.
 extern std::atomic<int> g_pdl;
+extern std::atomic<int> g_tile_variant;  // fp32 fused-scale tile kernel: 0 = smem row buffer, 1, 2 = register window
 __device__ __forceinline__ void pdl_entry()
 {
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
@@ -153,8 +154,8 @@ int launch_starlet(const void *kappa, void *pyr, long pyr_bstride, int n, int J,
 int launch_ks32(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int n,
                 int batch, bool forward, uint64_t seed, int r0, bool rotate, const float2 *tw, cudaStream_t s);
 size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg);
-int launch_map_direct(const void *g1, const void *g2, void *map, int n, int filter, double theta, int ell,
-                      double cut, int precision, cudaStream_t s);
+int launch_map_direct(const void *g1, const void *g2, const void *weight, long w_bs, void *map, void *coverage, int n,
+                      int batch, int filter, double theta, int ell, double cut, int precision, cudaStream_t s);
 int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
                   const fm_config &cfg, cudaStream_t s, bool allow_graph);
 int launch_band_moments(const void *pyr, double *moments, int n, int J, int batch, int precision, void *scratch,

@@ -18,6 +18,13 @@
 // is stored with one pad slot per 8 so that the lanes' 8-column windows hit
 // distinct banks.  FP32 cores (FFMA), no tensor cores: not a contraction the
 // tensor cores can take at this precision.
+//
+// Missing data (Sec. 4.3, Sec. 4.5): with pixel weights w >= 0 (0 = masked)
+// the same pass also forms D(x) = sum w(x+d) over the in-field offsets
+// 0 < |d| <= R (a third staged component and a 0/1 disc table), stages
+// w gamma1, w gamma2 instead of the shear, and writes
+// M = N_R S / D (0 where D <= 0) and optionally coverage = D / N_R, N_R the
+// aperture's pixel count.
 #include <math.h>
 
 #include <vector>
@@ -68,43 +75,64 @@ static double default_cut(int filter) { return filter == FM_FILTER_STARLET ? 2.0
 // ---- kernel -------------------------------------------------------------------
 __device__ __forceinline__ int padc(int c) { return c + (c >> 3); }
 
-template <typename T, int CX, int RY, int NW>
+template <typename T, int CX, int RY, int NW, bool MASK>
 __global__ void __launch_bounds__(NW * 32) k_map_direct(const T *__restrict__ g1, const T *__restrict__ g2,
-                                                        const cplx_t<T> *__restrict__ taps, int tw,
-                                                        const int *__restrict__ dxmax, T *__restrict__ out, int n,
-                                                        int Ri)
+                                                        const T *__restrict__ wgt, long w_bs,
+                                                        const cplx_t<T> *__restrict__ taps,
+                                                        const T *__restrict__ disc, int tw,
+                                                        const int *__restrict__ dxmax, T *__restrict__ out,
+                                                        T *__restrict__ cov, int n, int Ri, T n_r)
 {
     pdl_entry();
     using V = cplx_t<T>;
     constexpr int TX = 32 * CX, TY = NW * RY;
+    constexpr int NC = MASK ? 3 : 2;  // staged components
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int width = TX + 2 * Ri + 8;
     const int pw = padc(width) + 1;
-    T *s1 = reinterpret_cast<T *>(smem_raw);  // [2 buffers][2 comps][pw]
+    T *s1 = reinterpret_cast<T *>(smem_raw);  // [2 buffers][NC comps][pw]
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const long nn = (long)n * n;
+    const long b = blockIdx.z;
+    g1 += b * nn;
+    g2 += b * nn;
+    out += b * nn;
+    if (MASK) {
+        wgt += b * w_bs;
+        if (cov) cov += b * nn;
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int yw = y0 + warp * RY;
     const int lc = lane * CX;
 
-    T acc[RY][CX];
+    T acc[RY][CX], accw[MASK ? RY : 1][CX];
 #pragma unroll
     for (int k = 0; k < RY; ++k)
 #pragma unroll
-        for (int o = 0; o < CX; ++o) acc[k][o] = (T)0;
+        for (int o = 0; o < CX; ++o) {
+            acc[k][o] = (T)0;
+            if (MASK) accw[k][o] = (T)0;
+        }
 
     const int iy_lo = y0 - Ri, iy_hi = y0 + TY - 1 + Ri;
     for (int iy = iy_lo; iy <= iy_hi; ++iy) {
-        T *buf = s1 + ((iy - iy_lo) & 1) * 2 * pw;
+        T *buf = s1 + ((iy - iy_lo) & 1) * NC * pw;
         const bool rin = iy >= 0 && iy < n;
         for (int c = threadIdx.x; c < width; c += blockDim.x) {
             const int gx = x0 - Ri + c;
-            T a = (T)0, bb = (T)0;
+            T a = (T)0, bb = (T)0, ww = (T)0;
             if (rin && gx >= 0 && gx < n) {
                 a = g1[(long)iy * n + gx];
                 bb = g2[(long)iy * n + gx];
+                if (MASK) {
+                    ww = wgt[(long)iy * n + gx];
+                    a *= ww;
+                    bb *= ww;
+                }
             }
             buf[padc(c)] = a;
             buf[pw + padc(c)] = bb;
+            if (MASK) buf[2 * pw + padc(c)] = ww;
         }
         __syncthreads();
 
@@ -122,23 +150,28 @@ __global__ void __launch_bounds__(NW * 32) k_map_direct(const T *__restrict__ g1
         }
         if (dxm >= 0) {
             // two-level sum: this input row's taps first, then into the total
-            T part[RY][CX];
+            T part[RY][CX], partw[MASK ? RY : 1][CX];
 #pragma unroll
             for (int k = 0; k < RY; ++k)
 #pragma unroll
-                for (int o = 0; o < CX; ++o) part[k][o] = (T)0;
+                for (int o = 0; o < CX; ++o) {
+                    part[k][o] = (T)0;
+                    if (MASK) partw[k][o] = (T)0;
+                }
             for (int dx0 = -dxm; dx0 <= dxm; dx0 += 8) {
-                T w1[CX + 7], w2[CX + 7];
+                T w1[CX + 7], w2[CX + 7], w3[MASK ? CX + 7 : 1];
                 const int base = lc + dx0 + Ri;
 #pragma unroll
                 for (int q = 0; q < CX + 7; ++q) {
                     w1[q] = buf[padc(base + q)];
                     w2[q] = buf[pw + padc(base + q)];
+                    if (MASK) w3[q] = buf[2 * pw + padc(base + q)];
                 }
 #pragma unroll
                 for (int k = 0; k < RY; ++k) {
                     if (!act[k]) continue;
-                    const V *trow = taps + (long)(dy[k] + Ri) * tw + (dx0 + Ri);
+                    const long toff = (long)(dy[k] + Ri) * tw + (dx0 + Ri);
+                    const V *trow = taps + toff;
 #pragma unroll
                     for (int t = 0; t < 8; ++t) {
                         const V ab = __ldg(trow + t);
@@ -147,13 +180,21 @@ __global__ void __launch_bounds__(NW * 32) k_map_direct(const T *__restrict__ g1
                             part[k][o] = fma(ab.x, w1[o + t], part[k][o]);
                             part[k][o] = fma(ab.y, w2[o + t], part[k][o]);
                         }
+                        if (MASK) {
+                            const T in_disc = __ldg(disc + toff + t);
+#pragma unroll
+                            for (int o = 0; o < CX; ++o) partw[k][o] = fma(in_disc, w3[o + t], partw[k][o]);
+                        }
                     }
                 }
             }
 #pragma unroll
             for (int k = 0; k < RY; ++k)
 #pragma unroll
-                for (int o = 0; o < CX; ++o) acc[k][o] += part[k][o];
+                for (int o = 0; o < CX; ++o) {
+                    acc[k][o] += part[k][o];
+                    if (MASK) accw[k][o] += partw[k][o];
+                }
         }
     }
 #pragma unroll
@@ -163,21 +204,32 @@ __global__ void __launch_bounds__(NW * 32) k_map_direct(const T *__restrict__ g1
 #pragma unroll
         for (int o = 0; o < CX; ++o) {
             const int x = x0 + lc + o;
-            if (x < n) out[(long)y * n + x] = acc[k][o];
+            if (x >= n) continue;
+            if (MASK) {
+                const T d = accw[k][o];
+                out[(long)y * n + x] = d > (T)0 ? n_r * acc[k][o] / d : (T)0;
+                if (cov) cov[(long)y * n + x] = d / n_r;
+            } else {
+                out[(long)y * n + x] = acc[k][o];
+            }
         }
     }
 }
 
 template <typename T>
-static int map_direct_impl(const T *g1, const T *g2, T *map, int n, int filter, double theta, int ell, double cut,
-                           cudaStream_t s)
+static int map_direct_impl(const T *g1, const T *g2, const T *wgt, long w_bs, T *map, T *cov, int n, int batch,
+                           int filter, double theta, int ell, double cut, cudaStream_t s)
 {
     using V = cplx_t<T>;
+    const bool mask = wgt != nullptr;
     const double R = (cut > 0 ? cut : default_cut(filter)) * theta;
     const int Ri = (int)floor(R);
     const int tw = 2 * Ri + 8;  // weight row: dx = -Ri .. Ri + 7 (zeros beyond R)
-    std::vector<V> htaps((size_t)(2 * Ri + 1) * tw);
+    const size_t ntap = (size_t)(2 * Ri + 1) * tw;
+    std::vector<V> htaps(ntap);
+    std::vector<T> hdisc(mask ? ntap : 0);
     std::vector<int> hdx(2 * Ri + 1);
+    long n_r = 0;  // lattice offsets 0 < |d| <= R
     for (int dy = -Ri; dy <= Ri; ++dy) {
         const double m2 = R * R - (double)dy * dy;
         hdx[dy + Ri] = m2 >= 0 ? (int)floor(sqrt(m2)) : -1;
@@ -186,43 +238,63 @@ static int map_direct_impl(const T *g1, const T *g2, T *map, int n, int filter, 
             const double r2 = (double)dx * dx + (double)dy * dy;
             V ab;
             ab.x = ab.y = 0;
-            if (r2 > 0 && r2 <= R * R) {
+            const bool in = r2 > 0 && r2 <= R * R;
+            if (in) {
                 const double q = q_of(filter, sqrt(r2), theta, ell);
                 ab.x = (decltype(ab.x))(-q * ((double)dx * dx - (double)dy * dy) / r2);
                 ab.y = (decltype(ab.y))(-q * 2.0 * dx * dy / r2);
+                ++n_r;
             }
             htaps[(size_t)(dy + Ri) * tw + c] = ab;
+            if (mask) hdisc[(size_t)(dy + Ri) * tw + c] = in ? (T)1 : (T)0;
         }
     }
     Scratch sc;
+    auto up = [](size_t b) { return ((b + 255) / 256) * 256; };
     const size_t tap_bytes = htaps.size() * sizeof(V);
+    const size_t disc_bytes = hdisc.size() * sizeof(T);
     const size_t dx_bytes = hdx.size() * sizeof(int);
-    int st = scratch_alloc(sc, tap_bytes + dx_bytes + 256, s);
+    int st = scratch_alloc(sc, up(tap_bytes) + up(disc_bytes) + dx_bytes, s);
     if (st != FM_OK) return st;
-    V *dtaps = static_cast<V *>(sc.p);
-    int *ddx = reinterpret_cast<int *>(static_cast<char *>(sc.p) + ((tap_bytes + 255) / 256) * 256);
+    char *base = static_cast<char *>(sc.p);
+    V *dtaps = reinterpret_cast<V *>(base);
+    T *ddisc = mask ? reinterpret_cast<T *>(base + up(tap_bytes)) : nullptr;
+    int *ddx = reinterpret_cast<int *>(base + up(tap_bytes) + up(disc_bytes));
     FM_CUDA_TRY(cudaMemcpyAsync(dtaps, htaps.data(), tap_bytes, cudaMemcpyHostToDevice, s));
+    if (mask) FM_CUDA_TRY(cudaMemcpyAsync(ddisc, hdisc.data(), disc_bytes, cudaMemcpyHostToDevice, s));
     FM_CUDA_TRY(cudaMemcpyAsync(ddx, hdx.data(), dx_bytes, cudaMemcpyHostToDevice, s));
 
-    constexpr int CX = 8, RY = 4, NW = 4;
-    constexpr int TX = 32 * CX, TY = NW * RY;
-    const int width = TX + 2 * Ri + 8;
+    constexpr int CX = 8, NW = 4;
+    const int width = 32 * CX + 2 * Ri + 8;
     const int pw = width + (width >> 3) + 1;
-    const size_t smem = 2ull * 2 * pw * sizeof(T);
-    auto k = k_map_direct<T, CX, RY, NW>;
-    FM_CUDA_TRY(fm::smem_attr((const void *)k, smem));
-    dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY);
-    FM_LAUNCH(FM_K_MAP_DIRECT, k, grid, NW * 32, smem, s, g1, g2, dtaps, tw, ddx, map, n, Ri);
+    if (!mask) {
+        constexpr int RY = 4, TX = 32 * CX, TY = NW * RY;
+        const size_t smem = 2ull * 2 * pw * sizeof(T);
+        auto k = k_map_direct<T, CX, RY, NW, false>;
+        FM_CUDA_TRY(fm::smem_attr((const void *)k, smem));
+        dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, batch);
+        FM_LAUNCH(FM_K_MAP_DIRECT, k, grid, NW * 32, smem, s, g1, g2, (const T *)nullptr, 0l, dtaps,
+                  (const T *)nullptr, tw, ddx, map, (T *)nullptr, n, Ri, (T)n_r);
+    } else {
+        constexpr int RY = 2, TX = 32 * CX, TY = NW * RY;
+        const size_t smem = 2ull * 3 * pw * sizeof(T);
+        auto k = k_map_direct<T, CX, RY, NW, true>;
+        FM_CUDA_TRY(fm::smem_attr((const void *)k, smem));
+        dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, batch);
+        FM_LAUNCH(FM_K_MAP_DIRECT, k, grid, NW * 32, smem, s, g1, g2, wgt, w_bs, dtaps, ddisc, tw, ddx, map, cov,
+                  n, Ri, (T)n_r);
+    }
     return FM_OK;
 }
 
-int launch_map_direct(const void *g1, const void *g2, void *map, int n, int filter, double theta, int ell,
-                      double cut, int precision, cudaStream_t s)
+int launch_map_direct(const void *g1, const void *g2, const void *weight, long w_bs, void *map, void *coverage, int n,
+                      int batch, int filter, double theta, int ell, double cut, int precision, cudaStream_t s)
 {
     if (precision == FM_F64)
-        return map_direct_impl<double>((const double *)g1, (const double *)g2, (double *)map, n, filter, theta, ell,
-                                       cut, s);
-    return map_direct_impl<float>((const float *)g1, (const float *)g2, (float *)map, n, filter, theta, ell, cut, s);
+        return map_direct_impl<double>((const double *)g1, (const double *)g2, (const double *)weight, w_bs,
+                                       (double *)map, (double *)coverage, n, batch, filter, theta, ell, cut, s);
+    return map_direct_impl<float>((const float *)g1, (const float *)g2, (const float *)weight, w_bs, (float *)map,
+                                  (float *)coverage, n, batch, filter, theta, ell, cut, s);
 }
 
 }  // namespace fm

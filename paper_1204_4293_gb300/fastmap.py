@@ -58,6 +58,7 @@ _SIGS = {
     "fm_map_starlet": (_I, [_P, _P, _P, _I, _I, _I, _CFG, _P]),
     "fm_map_starlet_host": (_I, [_P, _P, _P, _I, _I, _I, _CFG, _P]),
     "fm_map_direct": (_I, [_P, _P, _P, _I, _I, _D, _I, _D, _CFG, _P]),
+    "fm_map_direct_masked": (_I, [_P, _P, _P, ctypes.c_long, _P, _P, _I, _I, _I, _D, _I, _D, _CFG, _P]),
     "fm_map_noise": (_I, [_P, _P, _P, _P, _I, _I, _I, _U64, _CFG, _P]),
     "fm_band_moments": (_I, [_P, _P, _I, _I, _I, _CFG, _P]),
     "fm_serve_create": (_I, [_SZ, _I, ctypes.POINTER(ctypes.c_void_p)]),
@@ -210,6 +211,29 @@ def fm_map_direct(g1, g2, filt, theta, ell=3, cut_over_theta=0.0, out=None, stre
     return m
 
 
+def fm_map_direct_masked(g1, g2, weight, filt, theta, ell=3, cut_over_theta=0.0, coverage=False, out=None,
+                         stream=None):
+    """Weighted direct M_ap for fields with missing data: (map, coverage or
+    None).  g1, g2 are [n, n] or [batch, n, n]; weight is [n, n] (one mask
+    for the batch) or the maps' shape; weights >= 0, 0 = masked."""
+    n, batch = _maps(g1, g2)
+    if weight.dtype != g1.dtype or not weight.is_cuda or not weight.is_contiguous():
+        raise ValueError("weight must be a contiguous CUDA tensor of the maps' dtype")
+    if weight.shape == g1.shape:
+        wbs = n * n if g1.dim() == 3 else 0
+    elif weight.shape == (n, n):
+        wbs = 0
+    else:
+        raise ValueError("weight is [n, n] or the maps' shape")
+    m = torch.empty_like(g1) if out is None else out
+    cov = torch.empty_like(g1) if coverage else None
+    c = _cfg(_prec(g1))
+    _check(_lib.fm_map_direct_masked(_ptr(g1), _ptr(g2), _ptr(weight), wbs, _ptr(m), _ptr(cov), n, batch, int(filt),
+                                     float(theta), int(ell), float(cut_over_theta), ctypes.byref(c),
+                                     _stream(stream)), "fm_map_direct_masked")
+    return m, cov
+
+
 def fm_map_noise(g1, g2, J, R, seed, boundary=FM_MIRROR, with_snr=True, fuse_depth=0, stream=None):
     """(variance [J-1, n, n] float64, S/N or None) over R rotated realisations."""
     n, batch = _maps(g1, g2)
@@ -224,7 +248,7 @@ def fm_map_noise(g1, g2, J, R, seed, boundary=FM_MIRROR, with_snr=True, fuse_dep
     return var, snr
 
 
-FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS, FM_TUNE_CHUNK_STREAMS, FM_TUNE_PDL = 1, 2, 3, 4
+FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS, FM_TUNE_CHUNK_STREAMS, FM_TUNE_PDL, FM_TUNE_TILE = 1, 2, 3, 4, 5
 
 
 def fm_tune(knob: int, value: int) -> None:

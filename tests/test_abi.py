@@ -58,6 +58,10 @@ def test_validation_before_any_device_work(fm):
     assert lib.fm_map_direct(None, None, None, 64, 7, 2.0, 3, 0.0, cfg, None) == fm.FM_EINVAL
     assert lib.fm_map_direct(None, None, None, 64, 0, -1.0, 3, 0.0, cfg, None) == fm.FM_EINVAL
     assert lib.fm_map_noise(None, None, None, None, 64, 4, 1, 0, cfg, None) == fm.FM_EINVAL
+    assert lib.fm_map_direct_masked(None, None, None, 0, None, None, 64, 1, 1, 4.0, 3, 0.0, cfg, None) == fm.FM_EINVAL
+    assert lib.fm_map_direct_masked(1, 1, 1, -1, 1, None, 64, 1, 1, 4.0, 3, 0.0, cfg, None) == fm.FM_EINVAL
+    assert lib.fm_map_direct_masked(1, 1, 1, 0, 1, None, 64, 0, 1, 4.0, 3, 0.0, cfg, None) == fm.FM_EINVAL
+    assert lib.fm_map_direct_masked(1, 1, 1, 0, 1, None, 64, 1, 1, 0.5, 3, 0.0, cfg, None) == fm.FM_EINVAL
     bad = fm._cfg(2)
     assert lib.fm_starlet_forward(None, None, 64, 3, 1, ctypes.byref(bad), None) == fm.FM_EINVAL
     assert b"precision" in lib.fm_last_error()
