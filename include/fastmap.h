@@ -227,8 +227,7 @@ int64_t fm_launch_count(void);     /* kernels launched by this library so far */
  *                        the previous kernel in their stream (default), 0 = off
  *   FM_TUNE_TILE         fp32 kernel of the fused small starlet scales:
  *                        0 = row-filtered shared buffer, 1 = register
- *                        window, fewest serial rows per thread (default),
- *                        2 = register window, least shared-memory traffic */
+ *                        window (default) */
 #define FM_TUNE_CHUNK_BYTES 1
 #define FM_TUNE_GRAPHS 2
 #define FM_TUNE_CHUNK_STREAMS 3

@@ -799,7 +799,7 @@ int fm_tune(int knob, int64_t value)
     case FM_TUNE_CHUNK_STREAMS: g_chunk_streams.store(value < 0 ? 2 : (value >= 2 ? 2 : 1)); return FM_OK;
     case FM_TUNE_PDL: g_pdl.store(value < 0 ? 1 : (value != 0)); return FM_OK;
     case FM_TUNE_TILE:
-        if (value > 2) return einval("FM_TUNE_TILE takes 0, 1 or 2");
+        if (value > 1) return einval("FM_TUNE_TILE takes 0 or 1");
         g_tile_variant.store(value < 0 ? 1 : (int)value);
         return FM_OK;
     }

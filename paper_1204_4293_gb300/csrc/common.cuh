@@ -38,7 +38,7 @@ void prof_after(int kid, cudaStream_t s);
 // finished (a no-op when launched without the attribute) and then lets the
 // next kernel's CTAs be scheduled into SMs this grid leaves idle in its tail.
 extern std::atomic<int> g_pdl;
-extern std::atomic<int> g_tile_variant;  // fp32 fused-scale tile kernel: 0 = smem row buffer, 1, 2 = register window
+extern std::atomic<int> g_tile_variant;  // fp32 fused-scale tile kernel: 0 = smem row buffer, 1 = register window
 __device__ __forceinline__ void pdl_entry()
 {
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900

@@ -357,6 +357,173 @@ __global__ void __launch_bounds__(256) k_st_tile32(const float *__restrict__ in,
 }
 
 // ---------------------------------------------------------------------------
+// Fused small scales 1..F, register-window form (fp32).  Same tile, halo and
+// integer taps as k_st_tile32, but each thread owns a vertical run of K
+// outputs of one float4 column at row stride s and forms the row-filtered
+// values it needs itself: it walks the K + 4 rows i0 + s (t - 2), filters
+// each along the row (taps +-s, +-2s from shared memory) into a five-deep
+// register window and filters the window down the column.  The centre of a
+// walked row is c_{j-1} at that row, so the band w_j = c_{j-1} - c_j needs no
+// further read.  c_j goes to the other shared buffer: one barrier per scale,
+// no row-filtered buffer.  K per scale is chosen at compile time from the
+// task count (tile_k below).  Measured on 32 maps of 1024^2 (scales 1-3):
+// 0.241 ms against 0.280 ms for k_st_tile32.
+__host__ __device__ constexpr int tile_task_cols(int F, int j, int TS)
+{
+    return (TS + 2 * ((1 << (F + 1)) - (1 << (j + 1)))) / 4;
+}
+// K for scale j: the fewest rows walked by one thread, ceil(tasks / 256) (K + 4)
+// (measured against the choice with the least shared-memory traffic among
+// one-round task sets: the tile kernel is bound by latency more than by the
+// shared-memory pipe, 0.241 vs 0.269 ms per 32 maps of 1024^2).
+__host__ __device__ constexpr int tile_k(int F, int j, int TS)
+{
+    const int s = 1 << (j - 1);
+    const int nr = TS + 2 * ((1 << (F + 1)) - (1 << (j + 1)));
+    const int ncq = nr / 4, ncqp = (ncq + 7) & ~7;
+    const int lds = s <= 2 ? 3 : 5;
+    int best = 1;
+    long bc = -1, bw = -1;
+    for (int K = 1; K <= 16; ++K) {
+        if (nr % (s * K)) continue;
+        const long nt = (long)s * (nr / (s * K)) * ncqp;
+        const long cost = (nt + 255) / 256 * (K + 4);
+        const long work = (long)s * (nr / (s * K)) * ncq * ((K + 4) * lds + K);
+        if (bc < 0 || cost < bc || (cost == bc && work < bw)) {
+            best = K;
+            bc = cost;
+            bw = work;
+        }
+    }
+    return best;
+}
+
+template <int F, int J>
+__device__ __forceinline__ void tile2_scale(const float *__restrict__ A, float *__restrict__ C, int ty0, int tx0,
+                                            float *__restrict__ w_dst, float *__restrict__ c_dst, int n, bool vok)
+{
+    constexpr int TS = 64;
+    constexpr int H = (1 << (F + 1)) - 2;
+    constexpr int HP = ((H + 3) / 4) * 4;
+    constexpr int P = TS + 2 * HP;
+    constexpr int s = 1 << (J - 1);
+    constexpr int ha = (1 << (F + 1)) - (1 << (J + 1));
+    constexpr int nr = TS + 2 * ha;
+    constexpr int ncq = nr / 4;
+    constexpr int ncqp = (ncq + 7) & ~7;
+    constexpr int K = tile_k(F, J, TS);
+    static_assert(nr % (s * K) == 0, "task rows");
+    constexpr int groups = nr / (s * K);
+    constexpr int ntask = s * groups * ncqp;
+    constexpr int c_lo = HP - ha;
+    static_assert(HP >= H + 2, "the s <= 2 row loads reach 4 columns left of the region");
+    for (int e = threadIdx.x; e < ntask; e += blockDim.x) {
+        const int qq = e % ncqp;
+        if (qq >= ncq) continue;
+        const int rg = e / ncqp;  // residue + s * group
+        const int r = rg % s, m = rg / s;
+        const int x = c_lo + qq * 4;
+        const int i0 = HP - ha + r + s * K * m;
+        float4 win[5], ctr[3];
+#pragma unroll
+        for (int t = 0; t < K + 4; ++t) {
+            const float *row = A + (i0 + (t - 2) * s) * P + x;
+            if constexpr (s <= 2) {
+                const float4 a = f4(row - 4), bq = f4(row), c = f4(row + 4);
+                const float w[12] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w, c.x, c.y, c.z, c.w};
+                win[t % 5] = make_float4(tap5(w[4 - 2 * s], w[4 - s], w[4], w[4 + s], w[4 + 2 * s]),
+                                         tap5(w[5 - 2 * s], w[5 - s], w[5], w[5 + s], w[5 + 2 * s]),
+                                         tap5(w[6 - 2 * s], w[6 - s], w[6], w[6 + s], w[6 + 2 * s]),
+                                         tap5(w[7 - 2 * s], w[7 - s], w[7], w[7 + s], w[7 + 2 * s]));
+                ctr[t % 3] = bq;
+            } else {
+                const float4 c0 = f4(row);
+                win[t % 5] = tap5(f4(row - 2 * s), f4(row - s), c0, f4(row + s), f4(row + 2 * s));
+                ctr[t % 3] = c0;
+            }
+            if (t >= 4) {
+                const int k = t - 4;
+                const int i = i0 + k * s;
+                float4 c = tap5(win[k % 5], win[(k + 1) % 5], win[(k + 2) % 5], win[(k + 3) % 5], win[(k + 4) % 5]);
+                c.x *= (1.f / 256.f);
+                c.y *= (1.f / 256.f);
+                c.z *= (1.f / 256.f);
+                c.w *= (1.f / 256.f);
+                const float4 prev = ctr[(k + 2) % 3];
+                const int oi = i - HP, ox = x - HP;
+                if (oi >= 0 && oi < TS && ox >= 0 && ox < TS) {
+                    const int gy = ty0 + oi, gx = tx0 + ox;
+                    alignas(16) float w[4] = {prev.x - c.x, prev.y - c.y, prev.z - c.z, prev.w - c.w};
+                    const long px = (long)gy * n + gx;
+                    emit_band<float>(w, w_dst, px, gy, gx, n, vok, nullptr, nullptr, 0, false);
+                    if (J == F && c_dst) {
+                        alignas(16) float cc[4] = {c.x, c.y, c.z, c.w};
+                        emit_band<float>(cc, c_dst, px, gy, gx, n, vok, nullptr, nullptr, 0, false, true);
+                    }
+                }
+                if (J < F) sf4(C + i * P + x, c);
+            }
+        }
+    }
+}
+
+template <int F>
+__global__ void __launch_bounds__(256, F >= 4 ? 1 : 3) k_st_tile32v2(const float *__restrict__ in, long in_bs,
+                                                        float *__restrict__ w_out, long w_bs, long w_ss,
+                                                        float *__restrict__ c_out, long c_bs, int n, int boundary,
+                                                        int tiles_x, int tiles_per_map, int vec_ok)
+{
+    pdl_entry();
+    constexpr int TS = 64;
+    constexpr int H = (1 << (F + 1)) - 2;
+    constexpr int HP = ((H + 3) / 4) * 4;
+    constexpr int P = TS + 2 * HP;
+    constexpr int NQ = P / 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *b0 = reinterpret_cast<float *>(smem_raw);  // c_0, c_2, ...
+    float *b1 = b0 + P * P;                           // c_1, c_3, ...
+    const long b = blockIdx.x / tiles_per_map;
+    const int t = blockIdx.x - (int)(b * tiles_per_map);
+    const int ty0 = (t / tiles_x) * TS;
+    const int tx0 = (t % tiles_x) * TS;
+    const float *src = in + b * in_bs;
+    const bool vok = vec_ok != 0;
+
+    for (int e = threadIdx.x; e < P * NQ; e += blockDim.x) {
+        const int i = e / NQ, q = e % NQ;
+        const int gy = fold_index(ty0 - HP + i, n, boundary);
+        const int gx0 = tx0 - HP + q * 4;
+        const float *rowp = src + (long)gy * n;
+        float4 v;
+        if (vok && gx0 >= 0 && gx0 + 4 <= n) {
+            v = f4(rowp + gx0);
+        } else {
+            v.x = rowp[fold_index(gx0, n, boundary)];
+            v.y = rowp[fold_index(gx0 + 1, n, boundary)];
+            v.z = rowp[fold_index(gx0 + 2, n, boundary)];
+            v.w = rowp[fold_index(gx0 + 3, n, boundary)];
+        }
+        sf4(b0 + i * P + q * 4, v);
+    }
+    __syncthreads();
+    float *wb = w_out + b * w_bs;
+    float *cb = c_out ? c_out + b * c_bs : nullptr;
+    tile2_scale<F, 1>(b0, b1, ty0, tx0, wb, cb, n, vok);
+    if constexpr (F >= 2) {
+        __syncthreads();
+        tile2_scale<F, (F >= 2 ? 2 : 1)>(b1, b0, ty0, tx0, wb + w_ss, cb, n, vok);
+    }
+    if constexpr (F >= 3) {
+        __syncthreads();
+        tile2_scale<F, (F >= 3 ? 3 : 1)>(b0, b1, ty0, tx0, wb + 2 * w_ss, cb, n, vok);
+    }
+    if constexpr (F >= 4) {
+        __syncthreads();
+        tile2_scale<F, (F >= 4 ? 4 : 1)>(b1, b0, ty0, tx0, wb + 3 * w_ss, cb, n, vok);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // One large scale, rows: r = rows-filtered c (taps +-s, +-2s), VW pixels per
 // thread.  grid = (ceil(n / (128 VW)), n, batch).
 template <typename T>
@@ -667,6 +834,14 @@ static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, fl
     const size_t smem = 2ull * P * P * sizeof(float);
     const int tiles_x = (n + TS - 1) / TS;
     const int tiles_per_map = tiles_x * tiles_x;
+    const int variant = g_tile_variant.load(std::memory_order_relaxed);
+    if (variant == 1 && !acc1) {
+        auto k = k_st_tile32v2<F>;
+        FM_CUDA_TRY(fm::smem_attr((const void *)k, smem));
+        FM_LAUNCH(FM_K_STARLET_TILE, k, (unsigned)(tiles_per_map * (long)batch), 256, smem, s, in, (long)n * n, w_out,
+                  w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, vec_ok ? 1 : 0);
+        return FM_OK;
+    }
     FM_CUDA_TRY(fm::smem_attr((const void *)k_st_tile32<F>, smem));
     FM_LAUNCH(FM_K_STARLET_TILE, k_st_tile32<F>, (unsigned)(tiles_per_map * (long)batch), 256, smem, s, in,
               (long)n * n, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, acc1, acc2,

@@ -104,3 +104,20 @@ def test_starlet_8192_windows_match_oracle():
         got = pyr[:, y0 + ya:y0 + yb, x0 + xa:x0 + xb].cpu().numpy()
         errs = band_errs(got, ref[:, ya:yb, xa:xb])
         assert max(errs) <= 1e-5, ((y0, x0), errs)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("n,J", [(64, 5), (100, 6), (130, 7), (256, 6)])
+def test_tile_kernel_variants(variant, n, J):
+    # every fp32 form of the fused small-scale kernel, every fusion depth
+    fm = _fm()
+    kappa = (synth.grf_kappa(n, seed=n + 3 * J) + synth.white((n, n), seed=J, scale=0.05)).astype(np.float32)
+    fm.fm_tune(fm.FM_TUNE_TILE, variant)
+    try:
+        for boundary in (0, 1):
+            ref = oracle.starlet(kappa.astype(np.float64), J, boundary)
+            for fuse in range(1, min(4, J - 1) + 1):
+                pyr = fm.fm_starlet_forward(torch.from_numpy(kappa).cuda(), J, boundary=boundary, fuse_depth=fuse)
+                assert max(band_errs(pyr.cpu().numpy(), ref)) <= TOL[np.float32], (boundary, fuse)
+    finally:
+        fm.fm_tune(fm.FM_TUNE_TILE, -1)
