@@ -221,7 +221,7 @@ int64_t fm_launch_count(void);     /* kernels launched by this library so far */
  *                        flight keep most of them in L2); 0 = no chunking
  *   FM_TUNE_GRAPHS       1 = replay batched calls from cached CUDA graphs
  *                        (default), 0 = launch every kernel each call
- *   FM_TUNE_CHUNK_STREAMS number of streams chunks alternate on (1 or 2,
+ *   FM_TUNE_CHUNK_STREAMS number of streams chunks alternate on (1 to 4,
  *                        default 2)
  *   FM_TUNE_PDL          1 = launch kernels as programmatic dependents of
  *                        the previous kernel in their stream (default), 0 = off

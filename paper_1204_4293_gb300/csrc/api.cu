@@ -280,7 +280,7 @@ int fm_starlet_forward(const void *kappa, void *pyramid, int n, int J, int batch
     cudaStream_t s = (cudaStream_t)stream;
     Scratch sc;
     if ((st = scratch_alloc(sc, starlet_scratch_elems(n, J, batch, cfg) * esize(cfg), s))) return st;
-    return launch_starlet(kappa, pyramid, (long)J * n * n, n, J, batch, cfg, sc.p, nullptr, nullptr, s);
+    return launch_starlet(kappa, pyramid, (long)J * n * n, n, J, batch, cfg, sc.p, s);
 }
 
 }  // extern "C"
@@ -296,10 +296,11 @@ namespace fm {
 // recorded once into a CUDA graph per (pointers, sizes, config) and replayed.
 namespace {
 
+constexpr int kMaxChunkStreams = 4;
 struct DevStreams {
-    cudaStream_t cap = nullptr;        // origin stream for graph capture
-    cudaStream_t s[2] = {nullptr, nullptr};
-    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    cudaStream_t cap = nullptr;  // origin stream for graph capture
+    cudaStream_t s[kMaxChunkStreams] = {};
+    cudaEvent_t fork = nullptr, join[kMaxChunkStreams] = {};
 };
 std::mutex g_ds_mu;  // guards g_ds and serialises multi-stream submission
 std::unordered_map<int, DevStreams> g_ds;
@@ -311,7 +312,7 @@ int dev_streams(DevStreams **out)
     DevStreams &d = g_ds[dev];
     if (!d.cap) {
         FM_CUDA_TRY(cudaStreamCreateWithFlags(&d.cap, cudaStreamNonBlocking));
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < kMaxChunkStreams; ++k) {
             FM_CUDA_TRY(cudaStreamCreateWithFlags(&d.s[k], cudaStreamNonBlocking));
             FM_CUDA_TRY(cudaEventCreateWithFlags(&d.join[k], cudaEventDisableTiming));
         }
@@ -362,11 +363,11 @@ int run_chunk(const char *g1, const char *g2, char *pyr, int n, int J, int b0, i
     int r = launch_ks(g1 + b0 * nn * es, g2 + b0 * nn * es, (long)nn, kap, nullptr, work, n, bc, cfg.precision, false,
                       0, 0, false, s);
     if (r != FM_OK) return r;
-    return launch_starlet(kap, pyr + (size_t)b0 * J * nn * es, (long)J * nn, n, J, bc, cfg, st, nullptr, nullptr, s);
+    return launch_starlet(kap, pyr + (size_t)b0 * J * nn * es, (long)J * nn, n, J, bc, cfg, st, s);
 }
 
-// All chunks, forked from `origin` onto the two internal streams and joined
-// back.  Caller holds g_ds_mu.
+// All chunks, forked from `origin` onto the internal streams (round robin
+// over p.slots of them) and joined back.  Caller holds g_ds_mu.
 int run_chunks(const void *g1, const void *g2, void *pyr, int n, int J, int batch, const fm_config &cfg,
                const ChunkPlan &p, char *scratch, cudaStream_t origin, DevStreams &ds)
 {
@@ -536,12 +537,12 @@ int noise_submit(const void *g1, const void *g2, double *var_out, void *snr_out,
         // rotates it with its own realisation index r0 + entry; the batch's
         // bands are then summed into S1, S2 by one reduction pass
         if ((r = launch_ks(g1, g2, 0, kap, nullptr, work, n, b, cfg.precision, false, seed, r0, true, s))) return r;
-        if ((r = launch_starlet(kap, pyr, (long)J * nn, n, J, b, cfg, st, nullptr, nullptr, s))) return r;
+        if ((r = launch_starlet(kap, pyr, (long)J * nn, n, J, b, cfg, st, s))) return r;
         if ((r = launch_noise_accum(pyr, b, (long)J * nn, nn, J - 1, s1, s2, cfg.precision, s))) return r;
     }
     if (snr_out) {
         if ((r = launch_ks(g1, g2, nn, kap, nullptr, work, n, 1, cfg.precision, false, 0, 0, false, s))) return r;
-        if ((r = launch_starlet(kap, pyr, (long)J * nn, n, J, 1, cfg, st, nullptr, nullptr, s))) return r;
+        if ((r = launch_starlet(kap, pyr, (long)J * nn, n, J, 1, cfg, st, s))) return r;
     }
     return launch_noise_finalize(s1, s2, snr_out ? pyr : nullptr, var_out, snr_out, nb, R, cfg.precision, s);
 }
@@ -796,7 +797,9 @@ int fm_tune(int knob, int64_t value)
     switch (knob) {
     case FM_TUNE_CHUNK_BYTES: g_chunk_bytes.store(value < 0 ? kDefaultChunkBytes : value); return FM_OK;
     case FM_TUNE_GRAPHS: g_use_graphs.store(value < 0 ? 1 : (value != 0)); return FM_OK;
-    case FM_TUNE_CHUNK_STREAMS: g_chunk_streams.store(value < 0 ? 2 : (value >= 2 ? 2 : 1)); return FM_OK;
+    case FM_TUNE_CHUNK_STREAMS:
+        g_chunk_streams.store(value < 0 ? 2 : (int)(value < 1 ? 1 : value > kMaxChunkStreams ? kMaxChunkStreams : value));
+        return FM_OK;
     case FM_TUNE_PDL: g_pdl.store(value < 0 ? 1 : (value != 0)); return FM_OK;
     case FM_TUNE_TILE:
         if (value > 1) return einval("FM_TUNE_TILE takes 0 or 1");

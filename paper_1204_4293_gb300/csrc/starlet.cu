@@ -13,8 +13,6 @@
 //   st_col  : c_j = columns-filtered r, w_j = c_{j-1} - c_j; c_j may overwrite
 //             c_{j-1} in place (each thread reads and writes only its own
 //             pixel of that array).
-// In noise mode the band values are not stored; each band's S1 += w and
-// S2 += w^2 are accumulated in FP64 instead (Sec. 1).
 #include "common.cuh"
 
 namespace fm {
@@ -27,17 +25,6 @@ template <typename T> struct B3 {
         return h0 * (m2 + p2) + h1 * (m1 + p1) + h2 * c;
     }
 };
-
-__device__ __forceinline__ void acc_band(double *s1, double *s2, long i, double w, bool atomic)
-{
-    if (atomic) {
-        atomicAdd(s1 + i, w);
-        atomicAdd(s2 + i, w * w);
-    } else {
-        s1[i] += w;
-        s2[i] += w * w;
-    }
-}
 
 // 16-byte vectors: 4 floats or 2 doubles
 template <typename T> struct Vec16;
@@ -68,23 +55,15 @@ template <typename T> __device__ __forceinline__ void st16cs(T *p, const T (&d)[
     __stcs(reinterpret_cast<V *>(p), *reinterpret_cast<const V *>(d));
 }
 
-// Store (or, in noise mode, accumulate) VW consecutive band values at
-// global pixel (gy, gx..gx+VW-1) of band `band` (1-based).  Band values are
-// final outputs and use streaming stores; `keep` selects plain stores (for
-// arrays a later kernel reads).
+// Store VW consecutive values at global pixel (gy, gx..gx+VW-1).  Band
+// values are final outputs and use streaming stores; `keep` selects plain
+// stores (for arrays a later kernel reads).
 template <typename T>
 __device__ __forceinline__ void emit_band(const T (&w)[16 / sizeof(T)], T *dst, long px, int gy, int gx, int n,
-                                          bool vec_ok, double *acc1, double *acc2, long acc_off, bool atomic,
-                                          bool keep = false)
+                                          bool vec_ok, bool keep = false)
 {
     constexpr int VW = 16 / sizeof(T);
     if (gy >= n) return;
-    if (acc1) {
-#pragma unroll
-        for (int t = 0; t < VW; ++t)
-            if (gx + t < n) acc_band(acc1, acc2, acc_off + px + t, (double)w[t], atomic);
-        return;
-    }
     if (vec_ok && gx + VW <= n) {
         if (keep)
             st16(dst + px, w);
@@ -105,8 +84,7 @@ __device__ __forceinline__ void emit_band(const T (&w)[16 / sizeof(T)], T *dst, 
 template <typename T, int F, int TS>
 __global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long in_bs, T *__restrict__ w_out, long w_bs,
                                                  long w_ss, T *__restrict__ c_out, long c_bs, int n, int boundary,
-                                                 int tiles_x, int tiles_per_map, double *__restrict__ acc1,
-                                                 double *__restrict__ acc2, int acc_atomic, int vec_ok)
+                                                 int tiles_x, int tiles_per_map, int vec_ok)
 {
     pdl_entry();
     constexpr int VW = 16 / sizeof(T);
@@ -202,9 +180,8 @@ __global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long 
                 if (oi >= 0 && oi < TS && ox >= 0 && ox < TS) {
                     const int gy = ty0 + oi, gx = tx0 + ox;
                     const long px = (long)gy * n + gx;
-                    emit_band<T>(w, w_out + b * w_bs + (long)(j - 1) * w_ss, px, gy, gx, n, vok, acc1, acc2,
-                                 (long)(j - 1) * nn, acc_atomic != 0);
-                    if (j == F && c_out) emit_band<T>(cj, c_out + b * c_bs, px, gy, gx, n, vok, nullptr, nullptr, 0, false, true);
+                    emit_band<T>(w, w_out + b * w_bs + (long)(j - 1) * w_ss, px, gy, gx, n, vok);
+                    if (j == F && c_out) emit_band<T>(cj, c_out + b * c_bs, px, gy, gx, n, vok, true);
                 }
                 if (j < F) st16(A + i * P + x, cj);
             }
@@ -238,8 +215,7 @@ template <int F>
 __global__ void __launch_bounds__(256) k_st_tile32(const float *__restrict__ in, long in_bs, float *__restrict__ w_out,
                                                    long w_bs, long w_ss, float *__restrict__ c_out, long c_bs, int n,
                                                    int boundary, int tiles_x, int tiles_per_map,
-                                                   double *__restrict__ acc1, double *__restrict__ acc2,
-                                                   int acc_atomic, int vec_ok)
+                                                   int vec_ok)
 {
     pdl_entry();
     constexpr int TS = 64;
@@ -341,11 +317,10 @@ __global__ void __launch_bounds__(256) k_st_tile32(const float *__restrict__ in,
                         const int gy = ty0 + oi, gx = tx0 + ox;
                         alignas(16) float w[4] = {prev.x - c.x, prev.y - c.y, prev.z - c.z, prev.w - c.w};
                         const long px = (long)gy * n + gx;
-                        emit_band<float>(w, w_out + b * w_bs + (long)(j - 1) * w_ss, px, gy, gx, n, vok, acc1, acc2,
-                                         (long)(j - 1) * nn, acc_atomic != 0);
+                        emit_band<float>(w, w_out + b * w_bs + (long)(j - 1) * w_ss, px, gy, gx, n, vok);
                         if (j == F && c_out) {
                             alignas(16) float cc[4] = {c.x, c.y, c.z, c.w};
-                            emit_band<float>(cc, c_out + b * c_bs, px, gy, gx, n, vok, nullptr, nullptr, 0, false, true);
+                            emit_band<float>(cc, c_out + b * c_bs, px, gy, gx, n, vok, true);
                         }
                     }
                     if (j < F) sf4(ap, c);
@@ -455,10 +430,10 @@ __device__ __forceinline__ void tile2_scale(const float *__restrict__ A, float *
                     const int gy = ty0 + oi, gx = tx0 + ox;
                     alignas(16) float w[4] = {prev.x - c.x, prev.y - c.y, prev.z - c.z, prev.w - c.w};
                     const long px = (long)gy * n + gx;
-                    emit_band<float>(w, w_dst, px, gy, gx, n, vok, nullptr, nullptr, 0, false);
+                    emit_band<float>(w, w_dst, px, gy, gx, n, vok);
                     if (J == F && c_dst) {
                         alignas(16) float cc[4] = {c.x, c.y, c.z, c.w};
-                        emit_band<float>(cc, c_dst, px, gy, gx, n, vok, nullptr, nullptr, 0, false, true);
+                        emit_band<float>(cc, c_dst, px, gy, gx, n, vok, true);
                     }
                 }
                 if (J < F) sf4(C + i * P + x, c);
@@ -574,8 +549,7 @@ __global__ void __launch_bounds__(128) k_st_row(const T *__restrict__ c, long c_
 template <typename T, int KR>
 __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T *c_prev, long prev_bs, T *c_next,
                                                 long next_bs, T *__restrict__ w_out, long w_bs, int n, int s,
-                                                int boundary, int band, double *__restrict__ acc1,
-                                                double *__restrict__ acc2, int acc_atomic, int vec_ok)
+                                                int boundary, int vec_ok)
 {
     pdl_entry();
     constexpr int VW = 16 / sizeof(T);
@@ -618,8 +592,8 @@ __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T
                                  win[(k + 4) % 5][u]);
             w[u] = prev[u] - cj[u];
         }
-        emit_band<T>(w, w_out + b * w_bs, px, y, x, n, vok, acc1, acc2, (long)(band - 1) * nn, acc_atomic != 0);
-        if (c_next) emit_band<T>(cj, c_next + b * next_bs, px, y, x, n, vok, nullptr, nullptr, 0, false, true);
+        emit_band<T>(w, w_out + b * w_bs, px, y, x, n, vok);
+        if (c_next) emit_band<T>(cj, c_next + b * next_bs, px, y, x, n, vok, true);
     }
 }
 
@@ -692,8 +666,7 @@ template <typename T, int W, int NR>
 __global__ void __launch_bounds__(512) k_st_cols_multi(const T *__restrict__ c_a, long ca_bs,
                                                        const T *__restrict__ u_in, long u_ks, T *__restrict__ w_out,
                                                        long w_bs, long w_ss, T *__restrict__ c_out, long c_bs, int n,
-                                                       int a, int K, int boundary, double *__restrict__ acc1,
-                                                       double *__restrict__ acc2, int acc_atomic)
+                                                       int a, int K, int boundary)
 {
     pdl_entry();
     constexpr int VW = 16 / sizeof(T);
@@ -756,8 +729,7 @@ __global__ void __launch_bounds__(512) k_st_cols_multi(const T *__restrict__ c_a
                 prev[m][uu] = cj[uu];
             }
             const long px = (long)yy * n + xs;
-            emit_band<T>(w, w_out + b * w_bs + (long)(band - 1) * w_ss, px, yy, xs, n, true, acc1, acc2,
-                         (long)(band - 1) * nn, acc_atomic != 0);
+            emit_band<T>(w, w_out + b * w_bs + (long)(band - 1) * w_ss, px, yy, xs, n, true);
         }
         __syncthreads();  // bufA is reloaded next
     }
@@ -807,7 +779,7 @@ size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg)
 
 template <typename T, int F, int TS>
 static int tile_launch(const T *in, T *w_out, long w_bs, long w_ss, T *c_out, long c_bs, int n, int boundary,
-                       int batch, double *acc1, double *acc2, bool vec_ok, cudaStream_t s)
+                       int batch, bool vec_ok, cudaStream_t s)
 {
     constexpr int H = (1 << (F + 1)) - 2;
     constexpr int HP = ((H + 3) / 4) * 4;
@@ -818,14 +790,13 @@ static int tile_launch(const T *in, T *w_out, long w_bs, long w_ss, T *c_out, lo
     auto k = k_st_tile<T, F, TS>;
     FM_CUDA_TRY(fm::smem_attr((const void *)k, smem));
     FM_LAUNCH(FM_K_STARLET_TILE, k, (unsigned)(tiles_per_map * (long)batch), 256, smem, s, in, (long)n * n, w_out,
-              w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, acc1, acc2, batch > 1 ? 1 : 0,
-              vec_ok ? 1 : 0);
+              w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, vec_ok ? 1 : 0);
     return FM_OK;
 }
 
 template <int F>
 static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, float *c_out, long c_bs, int n,
-                         int boundary, int batch, double *acc1, double *acc2, bool vec_ok, cudaStream_t s)
+                         int boundary, int batch, bool vec_ok, cudaStream_t s)
 {
     constexpr int TS = 64;
     constexpr int H = (1 << (F + 1)) - 2;
@@ -835,7 +806,7 @@ static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, fl
     const int tiles_x = (n + TS - 1) / TS;
     const int tiles_per_map = tiles_x * tiles_x;
     const int variant = g_tile_variant.load(std::memory_order_relaxed);
-    if (variant == 1 && !acc1) {
+    if (variant == 1) {
         auto k = k_st_tile32v2<F>;
         FM_CUDA_TRY(fm::smem_attr((const void *)k, smem));
         FM_LAUNCH(FM_K_STARLET_TILE, k, (unsigned)(tiles_per_map * (long)batch), 256, smem, s, in, (long)n * n, w_out,
@@ -844,32 +815,31 @@ static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, fl
     }
     FM_CUDA_TRY(fm::smem_attr((const void *)k_st_tile32<F>, smem));
     FM_LAUNCH(FM_K_STARLET_TILE, k_st_tile32<F>, (unsigned)(tiles_per_map * (long)batch), 256, smem, s, in,
-              (long)n * n, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, acc1, acc2,
-              batch > 1 ? 1 : 0, vec_ok ? 1 : 0);
+              (long)n * n, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, vec_ok ? 1 : 0);
     return FM_OK;
 }
 
 template <typename T>
 static int tile_dispatch(int f, const T *in, T *w_out, long w_bs, long w_ss, T *c_out, long c_bs, int n,
-                         int boundary, int batch, double *acc1, double *acc2, bool vec_ok, cudaStream_t s)
+                         int boundary, int batch, bool vec_ok, cudaStream_t s)
 {
     constexpr int TS = sizeof(T) == 4 ? 64 : 32;
     if constexpr (sizeof(T) == 4) {
         const float *fi = (const float *)in;
         float *fw = (float *)w_out, *fc = (float *)c_out;
         switch (f) {
-        case 1: return tile32_launch<1>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
-        case 2: return tile32_launch<2>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
-        case 3: return tile32_launch<3>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
-        case 4: return tile32_launch<4>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
+        case 1: return tile32_launch<1>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, vec_ok, s);
+        case 2: return tile32_launch<2>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, vec_ok, s);
+        case 3: return tile32_launch<3>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, vec_ok, s);
+        case 4: return tile32_launch<4>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, vec_ok, s);
         }
         return FM_EINVAL;
     }
     switch (f) {
-    case 1: return tile_launch<T, 1, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
-    case 2: return tile_launch<T, 2, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
-    case 3: return tile_launch<T, 3, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
-    case 4: return tile_launch<T, 4, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, acc1, acc2, vec_ok, s);
+    case 1: return tile_launch<T, 1, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, vec_ok, s);
+    case 2: return tile_launch<T, 2, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, vec_ok, s);
+    case 3: return tile_launch<T, 3, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, vec_ok, s);
+    case 4: return tile_launch<T, 4, TS>(in, w_out, w_bs, w_ss, c_out, c_bs, n, boundary, batch, vec_ok, s);
     }
     return FM_EINVAL;
 }
@@ -878,7 +848,7 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 template <typename T>
 static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int batch, const fm_config &cfg,
-                        T *scratch, double *acc1, double *acc2, cudaStream_t s)
+                        T *scratch, cudaStream_t s)
 {
     constexpr int VW = 16 / sizeof(T);
     constexpr int KR = 8;
@@ -887,13 +857,12 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
     const int bnd = cfg.boundary;
     T *A = scratch;
     T *Bb = scratch ? scratch + (long)batch * nn : nullptr;
-    const bool noise = acc1 != nullptr;
-    T *last = noise ? nullptr : pyr + (long)(J - 1) * nn;  // slot of the smooth array
-    const bool vec_ok = n % VW == 0 && aligned16(kappa) && (noise || aligned16(pyr)) && (!scratch || aligned16(scratch));
+    T *last = pyr + (long)(J - 1) * nn;  // slot of the smooth array
+    const bool vec_ok = n % VW == 0 && aligned16(kappa) && aligned16(pyr) && (!scratch || aligned16(scratch));
     if (f >= 1) {
         T *c_out = f == J - 1 ? last : A;
         const long c_bs = f == J - 1 ? pyr_bs : nn;
-        int st = tile_dispatch<T>(f, kappa, pyr, pyr_bs, nn, c_out, c_bs, n, bnd, batch, acc1, acc2, vec_ok, s);
+        int st = tile_dispatch<T>(f, kappa, pyr, pyr_bs, nn, c_out, c_bs, n, bnd, batch, vec_ok, s);
         if (st != FM_OK) return st;
     }
     const int K = J - 1 - f;  // large scales left after the tile kernel
@@ -908,13 +877,12 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
         const size_t csm = 2ull * n * Wc * sizeof(T);
         const unsigned cgrid = (unsigned)((long)batch * (n / Wc));
         const int cthreads = n * (Wc / VW) / NR;
-        T *w_base = noise ? nullptr : pyr;
 #define FM_COLS_MULTI(WW)                                                                                          \
     do {                                                                                                            \
         auto kc = k_st_cols_multi<T, WW, NR>;                                                                       \
         FM_CUDA_TRY(fm::smem_attr((const void *)kc, csm));               \
-        FM_LAUNCH(FM_K_STARLET_COL, kc, cgrid, cthreads, csm, s, A, nn, U, (long)batch * nn, w_base, pyr_bs, nn,     \
-                  last, pyr_bs, n, f, K, bnd, acc1, acc2, batch > 1 ? 1 : 0);                                      \
+        FM_LAUNCH(FM_K_STARLET_COL, kc, cgrid, cthreads, csm, s, A, nn, U, (long)batch * nn, pyr, pyr_bs, nn, last,  \
+                  pyr_bs, n, f, K, bnd);                                                                           \
     } while (0)
         switch (Wc) {
         case 16: FM_COLS_MULTI(16); break;
@@ -937,20 +905,19 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
                   vec_ok ? 1 : 0);
         const unsigned gy = (unsigned)(sp * ((((n + sp - 1) / sp) + KR - 1) / KR));
         FM_LAUNCH(FM_K_STARLET_COL, (k_st_col<T, KR>), dim3(gx, gy, batch), 128, 0, s, Bb, c_prev, nn, c_next,
-                  next_bs, noise ? nullptr : pyr + (long)(j - 1) * nn, pyr_bs, n, sp, bnd, j, acc1, acc2,
-                  batch > 1 ? 1 : 0, vec_ok ? 1 : 0);
+                  next_bs, pyr + (long)(j - 1) * nn, pyr_bs, n, sp, bnd, vec_ok ? 1 : 0);
     }
     return FM_OK;
 }
 
 int launch_starlet(const void *kappa, void *pyr, long pyr_bstride, int n, int J, int batch, const fm_config &cfg,
-                   void *scratch, double *acc_s1, double *acc_s2, cudaStream_t s)
+                   void *scratch, cudaStream_t s)
 {
     if (cfg.precision == FM_F64)
         return starlet_impl<double>((const double *)kappa, (double *)pyr, pyr_bstride, n, J, batch, cfg,
-                                    (double *)scratch, acc_s1, acc_s2, s);
+                                    (double *)scratch, s);
     return starlet_impl<float>((const float *)kappa, (float *)pyr, pyr_bstride, n, J, batch, cfg, (float *)scratch,
-                               acc_s1, acc_s2, s);
+                               s);
 }
 
 }  // namespace fm

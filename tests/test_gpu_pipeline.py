@@ -86,3 +86,31 @@ def test_map_starlet_8192_reconstruction_and_ks():
     rms = kap.double().pow(2).mean().sqrt().item()
     assert (pyr.double().sum(0) - kE.double()).abs().max().item() / rms < 1e-5
     assert (kE - kap).abs().max().item() / rms < 1e-5
+
+
+@pytest.mark.parametrize("streams", [1, 2, 3, 4])
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_chunk_plans_give_identical_pyramids(streams, graphs):
+    # 7 maps in chunks of 2 (a ragged last chunk) on 1..4 streams, replayed
+    # from a graph or launched eagerly: bit-identical to one unchunked pass
+    fm = _fm()
+    n, J, batch = 256, 6, 7
+    g1 = torch.empty((batch, n, n), device="cuda").normal_(0, 0.1)
+    g2 = torch.empty_like(g1).normal_(0, 0.1)
+    fm.fm_tune(fm.FM_TUNE_CHUNK_BYTES, 0)
+    try:
+        ref = fm.fm_map_starlet(g1, g2, J)
+        per_map = n * n * 4 * 5  # complex work buffer, kappa, two starlet scratch arrays
+        fm.fm_tune(fm.FM_TUNE_CHUNK_BYTES, 2 * per_map + per_map // 2)  # chunks of 2 maps
+        fm.fm_tune(fm.FM_TUNE_CHUNK_STREAMS, streams)
+        fm.fm_tune(fm.FM_TUNE_GRAPHS, graphs)
+        out = torch.full_like(ref, float("nan"))
+        for _ in range(2):  # record, then replay
+            fm.fm_map_starlet(g1, g2, J, out=out)
+        assert torch.equal(out, ref)
+    finally:
+        for knob in (fm.FM_TUNE_CHUNK_BYTES, fm.FM_TUNE_CHUNK_STREAMS, fm.FM_TUNE_GRAPHS):
+            fm.fm_tune(knob, -1)
+        fm.fm_trim()
+    o = oracle.map_starlet(g1[batch - 1].double().cpu().numpy(), g2[batch - 1].double().cpu().numpy(), J)
+    assert max(band_errs(ref[batch - 1].cpu().numpy(), o)) <= 1e-5
