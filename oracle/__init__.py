@@ -12,6 +12,7 @@ Each wrapper names the paper passage its C function follows:
   map_direct_masked        eq. shearmap with pixel weights for missing data
                            (Sec. 4.3, Sec. 4.5)
   map_noise                Sec. 1 and Sec. 5.1 (randomised-data noise maps)
+  map_noise_expected       Sec. 1: exact expectation of that variance (periodic)
   u_/q_ filters            eq. sch, eq. mexhat, the starlet U and Q (Sec. 4)
 """
 from __future__ import annotations
@@ -71,6 +72,7 @@ def _load():
             "oracle_map_direct_at": (None, [_D, _D, _I, _I, c_int, _D, c_int, c_int, c_double, c_int, c_double]),
             "oracle_map_direct_masked_at": (None, [_D, _D, _D, _I, _I, c_int, _D, _D, c_int, c_int, c_double, c_int,
                                                     c_double]),
+            "oracle_map_noise_expected_at": (None, [_D, _D, _I, _I, c_int, _D, c_int, c_int]),
             "oracle_splitmix64": (c_u64, [c_u64, c_u64]),
             "oracle_noise_u": (c_double, [c_u64, c_int, c_int, c_int, c_int]),
             "oracle_rotate_shear": (None, [_D, _D, _D, _D, c_int, c_int, c_u64]),
@@ -275,3 +277,24 @@ def map_noise(g1, g2, J, R, seed, boundary=MIRROR, with_snr=True):
     _load().oracle_map_noise(_p(a), _p(b), _p(var), _p(snr) if with_snr else None, n, int(J), int(R),
                              int(seed) & (2**64 - 1), int(boundary))
     return var, snr
+
+
+def map_noise_expected_at(g1, g2, J, ys, xs):
+    """Exact expected noise variance of bands 1..J-1 (periodic boundary) at
+    listed pixels: [J-1, npts]."""
+    a = _in(g1)
+    n = _pow2_n(a)
+    b = _in(g2, n)
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    out = np.empty((J - 1, len(ys)))
+    _load().oracle_map_noise_expected_at(_p(a), _p(b), ys.ctypes.data_as(_I), xs.ctypes.data_as(_I), len(ys),
+                                         _p(out), n, int(J))
+    return out
+
+
+def map_noise_expected(g1, g2, J):
+    """Exact expected noise variance over the whole map: [J-1, n, n]."""
+    n = _pow2_n(_in(g1))
+    ys, xs = np.mgrid[0:n, 0:n]
+    return map_noise_expected_at(g1, g2, J, ys.ravel(), xs.ravel()).reshape(J - 1, n, n)

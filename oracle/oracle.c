@@ -494,3 +494,44 @@ void oracle_map_noise(const double *g1, const double *g2, double *var_out, doubl
     free(r1);
     free(r2);
 }
+
+/* Exact expectation of the noise variance (Sec. 1): with a uniform phase per
+ * pixel, KS followed by starlet band j is (periodic boundary) the convolution
+ * w_j(x) = sum_y Re[K_j(x - y) gamma(y)] with a complex kernel K_j, and
+ *   Var[w_j(x)] = 1/2 sum_y |K_j(x - y)|^2 |gamma(y)|^2
+ * because E[Re(z e^{i phi})^2] = |z|^2 / 2 and distinct pixels are
+ * independent.  K_j is read off the pipeline's response to a unit shear at
+ * pixel 0: Re K_j from gamma = (delta, 0), -Im K_j from gamma = (0, delta).
+ * Evaluated at listed pixels; out[(j-1) * npts + p], j = 1..J-1.  Periodic
+ * boundary only (the convolution form needs shift invariance). */
+void oracle_map_noise_expected_at(const double *g1, const double *g2, const int *ys, const int *xs, int npts,
+                                  double *out, int n, int J)
+{
+    size_t nn = (size_t)n * n;
+    double *d = (double *)calloc(nn, sizeof(double));
+    double *z = (double *)calloc(nn, sizeof(double));
+    double *pa = (double *)malloc(sizeof(double) * (size_t)J * nn);
+    double *pb = (double *)malloc(sizeof(double) * (size_t)J * nn);
+    d[0] = 1.0;
+    oracle_map_starlet(d, z, pa, n, J, 1);
+    oracle_map_starlet(z, d, pb, n, J, 1);
+    for (int j = 0; j < J - 1; ++j)
+        for (int p = 0; p < npts; ++p) {
+            int y = ys[p], x = xs[p];
+            double acc = 0.0;
+            for (int yy = 0; yy < n; ++yy)
+                for (int xx = 0; xx < n; ++xx) {
+                    /* offset x - y, wrapped onto the periodic grid */
+                    int dy = ((y - yy) % n + n) % n, dx = ((x - xx) % n + n) % n;
+                    size_t ki = (size_t)j * nn + (size_t)dy * n + dx;
+                    double k2 = pa[ki] * pa[ki] + pb[ki] * pb[ki];
+                    size_t gi = (size_t)yy * n + xx;
+                    acc += k2 * (g1[gi] * g1[gi] + g2[gi] * g2[gi]);
+                }
+            out[(size_t)j * npts + p] = 0.5 * acc;
+        }
+    free(d);
+    free(z);
+    free(pa);
+    free(pb);
+}
