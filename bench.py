@@ -282,6 +282,10 @@ def side_legs(fm, torch, n, J, g1, g2):
     fm.fm_map_noise(s1, s2, J, 8, seed=3)
     t_noise = cuda_time(torch, lambda: fm.fm_map_noise(s1, s2, J, R, seed=3), 1)
     out["noise"] = {"R": R, "ms": t_noise, "value": n * n * J * R / (t_noise * 1e-3) / 1e6, "unit": UNIT}
+    # the exact expectation of that variance (periodic boundary): one FFT pipeline
+    t_exp = cuda_time(torch, lambda: fm.fm_map_noise_expected(s1, s2, J), 5)
+    out["noise_expected"] = {"ms": t_exp, "boundary": "periodic",
+                             "vs_monte_carlo_R1000": t_noise / t_exp}
     return out
 
 

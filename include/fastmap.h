@@ -155,6 +155,18 @@ int fm_map_direct_masked(const void *g1, const void *g2, const void *weight, lon
 int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
                  const fm_config *cfg, void *stream);
 
+/* ---- exact expected noise variance (Sec. 1) -----------------------------------
+ * The expectation of fm_map_noise's variance over the random rotation: with a
+ * uniform phase per pixel, Var[w_j(x)] = 1/2 sum_y |K_j(x - y)|^2 |gamma(y)|^2,
+ * K_j the complex kernel of KS followed by band j.  One FFT pipeline instead
+ * of R realisations; not the paper's Monte-Carlo procedure but its limit.
+ * Needs the periodic boundary (cfg->boundary = FM_PERIODIC; mirror edges make
+ * the pipeline position dependent, FM_EINVAL).  var_out [(J-1)][n][n] in the
+ * element type of cfg->precision; one map; n a power of two.  Scratch:
+ * about (2J + 6J) n^2 elements, stream-ordered. */
+int fm_map_noise_expected(const void *g1, const void *g2, void *var_out, int n, int J, const fm_config *cfg,
+                          void *stream);
+
 /* ---- Kaiser-Squires inversion without device allocation --------------------
  * No counterpart in the paper: an engineering variant of fm_ks_invert for
  * callers that cannot allocate device memory where they run the inversion

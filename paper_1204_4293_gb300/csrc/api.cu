@@ -748,6 +748,48 @@ int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out,
     return map_noise_run(g1, g2, var_out, snr_out, n, J, R, seed, cfg, (cudaStream_t)stream, true);
 }
 
+// Exact expected noise variance (Sec. 1), periodic boundary:
+// Var_j = 1/2 |K_j|^2 (*) |gamma|^2 (circular convolution).  K_j is the
+// pipeline's response to unit shears at pixel 0 (Re K_j from gamma1, -Im K_j
+// from gamma2); the convolution runs through the FFT pipeline: the spectra of
+// |K_j|^2, then rows FFT of |gamma|^2 (broadcast to the J - 1 bands) -> columns
+// FFT -> times the band's spectrum -> inverse -> real part / 2.
+int fm_map_noise_expected(const void *g1, const void *g2, void *var_out, int n, int J, const fm_config *cfgp,
+                          void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if ((st = check_fft_n(n))) return st;
+    if ((st = check_J(n, J))) return st;
+    if (cfg.boundary != FM_PERIODIC)
+        return einval("fm_map_noise_expected needs cfg->boundary = FM_PERIODIC: with mirror edges KS + starlet is "
+                      "not a convolution");
+    if (!g1 || !g2 || !var_out) return einval("null pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int prec = cfg.precision;
+    const size_t es = prec == FM_F64 ? 8 : 4;
+    const long nn = (long)n * n;
+    const int nb = J - 1;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t b_delta = up(2 * nn * es), b_pyr = up((size_t)2 * J * nn * es), b_q = up((size_t)nb * nn * es),
+                 b_p = up(nn * es), b_spec = up((size_t)nb * nn * 2 * es);
+    Scratch sc;
+    if ((st = scratch_alloc(sc, 2 * b_delta + b_pyr + b_q + b_p + 2 * b_spec, s))) return st;
+    char *base = static_cast<char *>(sc.p);
+    char *g1d = base, *g2d = g1d + b_delta, *pyr = g2d + b_delta, *q = pyr + b_pyr, *p = q + b_q, *spec = p + b_p,
+         *work = spec + b_spec;
+    if ((st = launch_unit_shears(g1d, g2d, nn, prec, s))) return st;
+    if ((st = map_starlet_run(g1d, g2d, pyr, n, J, 2, cfg, s))) return st;
+    // |K_j|^2 = (Re K_j)^2 + (Im K_j)^2 from the two responses [2][J][n][n]
+    if ((st = launch_modulus2(pyr, nn, pyr + (size_t)J * nn * es, nn, q, nn, nb, prec, s))) return st;
+    if ((st = launch_modulus2(g1, 0, g2, 0, p, nn, 1, prec, s))) return st;
+    if ((st = launch_fft_op(q, nullptr, nn, nullptr, nullptr, spec, n, nb, prec, FFT_OP_SPECTRUM, nullptr, 1.0, 0, 0,
+                            false, s)))
+        return st;
+    return launch_fft_op(p, nullptr, 0, var_out, nullptr, work, n, nb, prec, FFT_OP_FILTER, spec, 0.5, 0, 0, false, s);
+}
+
 int fm_band_moments(const void *pyramid, double *moments, int n, int J, int batch, const fm_config *cfgp,
                     void *stream)
 {

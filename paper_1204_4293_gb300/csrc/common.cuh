@@ -153,11 +153,28 @@ int launch_starlet(const void *kappa, void *pyr, long pyr_bstride, int n, int J,
                    void *scratch, cudaStream_t s);
 int launch_ks32(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int n,
                 int batch, bool forward, uint64_t seed, int r0, bool rotate, const float2 *tw, cudaStream_t s);
+// Spectral operation of the column pass of the 2-D FFT pipeline
+// rows FFT -> columns FFT -> op -> columns IFFT -> rows IFFT (Re, Im):
+//   FFT_OP_KS_INV   multiply by conj(D)  (KS inversion, Sec. 4.5)
+//   FFT_OP_KS_FWD   multiply by D        (shear of a convergence map)
+//   FFT_OP_FILTER   multiply by the spectrum filt[b][ky][kx] (a periodic
+//                   convolution; outputs times out_scale)
+//   FFT_OP_SPECTRUM stop after the columns FFT: `work` holds the spectrum
+enum { FFT_OP_KS_INV = 0, FFT_OP_KS_FWD = 1, FFT_OP_FILTER = 2, FFT_OP_SPECTRUM = 3 };
+int launch_fft_op(const void *in1, const void *in2, long in_bstride, void *out1, void *out2, void *work, int n,
+                  int batch, int precision, int op, const void *filt, double out_scale, uint64_t rot_seed, int rot_r0,
+                  bool rotate, cudaStream_t s);
+int launch_fft32(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int n,
+                 int batch, int op, const float2 *filt, float out_scale, uint64_t seed, int r0, bool rotate,
+                 const float2 *tw, cudaStream_t s);
 size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg);
 int launch_map_direct(const void *g1, const void *g2, const void *weight, long w_bs, void *map, void *coverage, int n,
                       int batch, int filter, double theta, int ell, double cut, int precision, cudaStream_t s);
 int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
                   const fm_config &cfg, cudaStream_t s, bool allow_graph);
+int launch_modulus2(const void *a, long a_bs, const void *b, long b_bs, void *out, long nn, int count, int precision,
+                    cudaStream_t s);
+int launch_unit_shears(void *g1d, void *g2d, long nn, int precision, cudaStream_t s);
 int launch_band_moments(const void *pyr, double *moments, int n, int J, int batch, int precision, void *scratch,
                         cudaStream_t s);
 int launch_noise_accum(const void *pyr, int nb, long pyr_bs, long nn, int bands, double *s1, double *s2,

@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T *__restrict__ in1, co
 // cols_ks: one CTA holds a strip of W = 1 << logw columns of one map.
 template <typename T, int E>
 __global__ void __launch_bounds__(1024) k_cols_ks(cplx_t<T> *__restrict__ work, int n, int logn, int logw,
-                                                  const cplx_t<T> *__restrict__ tw, int forward)
+                                                  const cplx_t<T> *__restrict__ tw, int op,
+                                                  const cplx_t<T> *__restrict__ filt)
 {
     pdl_entry();
     using V = cplx_t<T>;
@@ -158,21 +159,34 @@ __global__ void __launch_bounds__(1024) k_cols_ks(cplx_t<T> *__restrict__ work, 
     }
     __syncthreads();
     smem_fft<E, false, true, false>(buf, n, logn, logw, 1, W, tw, threadIdx.x, blockDim.x);
+    if (op == FFT_OP_SPECTRUM) {  // the 2-D spectrum [ky][kx] is the result
+        for (int idx = threadIdx.x; idx < n * W; idx += blockDim.x) {
+            const int r = idx >> logw, c = idx & (W - 1);
+            base[(long)r * n + c] = buf[idx];
+        }
+        return;
+    }
     // kappa_hat = conj(D) gamma_hat (inverse) or gamma_hat = D kappa_hat (forward),
-    // D = (k1 + i k2)^2 / |k|^2 = (k1^2 - k2^2 + 2 i k1 k2) / (k1^2 + k2^2), D(0) = 0.
+    // D = (k1 + i k2)^2 / |k|^2 = (k1^2 - k2^2 + 2 i k1 k2) / (k1^2 + k2^2), D(0) = 0;
+    // or the given spectrum filt[b][ky][kx].
     const int half = n >> 1;
     for (int idx = threadIdx.x; idx < n * W; idx += blockDim.x) {
         const int r = idx >> logw, c = idx & (W - 1);
-        const int k2 = r < half ? r : r - n;
         const int xi = x0 + c;
-        const int k1 = xi < half ? xi : xi - n;
-        const int den = k1 * k1 + k2 * k2;
-        V d = cmake<V>((T)0, (T)0);
-        if (den != 0) {
-            const T inv = (T)1 / (T)den;
-            const T re = (T)(k1 * k1 - k2 * k2) * inv;
-            const T im = (T)(2 * k1 * k2) * inv;
-            d = cmake<V>(re, forward ? im : -im);
+        V d;
+        if (op == FFT_OP_FILTER) {
+            d = filt[b * (long)n * n + (long)r * n + xi];
+        } else {
+            const int k2 = r < half ? r : r - n;
+            const int k1 = xi < half ? xi : xi - n;
+            const int den = k1 * k1 + k2 * k2;
+            d = cmake<V>((T)0, (T)0);
+            if (den != 0) {
+                const T inv = (T)1 / (T)den;
+                const T re = (T)(k1 * k1 - k2 * k2) * inv;
+                const T im = (T)(2 * k1 * k2) * inv;
+                d = cmake<V>(re, op == FFT_OP_KS_FWD ? im : -im);
+            }
         }
         buf[idx] = cmul(buf[idx], d);
     }
@@ -220,7 +234,7 @@ __global__ void __launch_bounds__(1024) k_rows_inv(const cplx_t<T> *__restrict__
 // ---------------------------------------------------------------------------
 template <typename T>
 static int ks_impl(const T *in1, const T *in2, long in_bstride, T *out1, T *out2, cplx_t<T> *work, int n, int batch,
-                   bool forward, uint64_t seed, int r0, bool rotate, cudaStream_t s)
+                   int op, const cplx_t<T> *filt, T out_scale, uint64_t seed, int r0, bool rotate, cudaStream_t s)
 {
     using V = cplx_t<T>;
     int st = FM_OK;
@@ -255,28 +269,40 @@ static int ks_impl(const T *in1, const T *in2, long in_bstride, T *out1, T *out2
 
     FM_LAUNCH(FM_K_FFT_ROWS_FWD, krf, row_grid, row_threads, row_smem, s, in1, in2, in_bstride, work, n, logn,
               lognvec, total_rows, tw, seed, r0, rotate ? 1 : 0);
-    FM_LAUNCH(FM_K_FFT_COLS_KS, kcs, col_grid, col_threads, col_smem, s, work, n, logn, logw, tw, forward ? 1 : 0);
-    const T scale = (T)1 / ((T)n * (T)n);
+    FM_LAUNCH(FM_K_FFT_COLS_KS, kcs, col_grid, col_threads, col_smem, s, work, n, logn, logw, tw, op, filt);
+    if (op == FFT_OP_SPECTRUM) return FM_OK;
+    const T scale = out_scale / ((T)n * (T)n);
     FM_LAUNCH(FM_K_FFT_ROWS_INV, kri, row_grid, row_threads, row_smem, s, work, out1, out2, n, logn, lognvec,
               total_rows, tw, scale);
     return FM_OK;
 }
 
-int launch_ks(const void *in1, const void *in2, long in_bstride, void *out1, void *out2, void *work, int n, int batch,
-              int precision, bool forward, uint64_t rot_seed, int rot_r0, bool rotate, cudaStream_t s)
+int launch_fft_op(const void *in1, const void *in2, long in_bstride, void *out1, void *out2, void *work, int n,
+                  int batch, int precision, int op, const void *filt, double out_scale, uint64_t rot_seed, int rot_r0,
+                  bool rotate, cudaStream_t s)
 {
     if (precision == FM_F64)
         return ks_impl<double>((const double *)in1, (const double *)in2, in_bstride, (double *)out1, (double *)out2,
-                               (double2 *)work, n, batch, forward, rot_seed, rot_r0, rotate, s);
+                               (double2 *)work, n, batch, op, (const double2 *)filt, out_scale, rot_seed, rot_r0,
+                               rotate, s);
     if (n >= 32) {  // register-resident radix-32 path (fft32.cu)
         int st = FM_OK;
         const float2 *tw = static_cast<const float2 *>(twiddles(n, FM_F32, s, &st));
         if (!tw) return st;
-        return launch_ks32((const float *)in1, (const float *)in2, in_bstride, (float *)out1, (float *)out2,
-                           (float2 *)work, n, batch, forward, rot_seed, rot_r0, rotate, tw, s);
+        return launch_fft32((const float *)in1, (const float *)in2, in_bstride, (float *)out1, (float *)out2,
+                            (float2 *)work, n, batch, op, (const float2 *)filt, (float)out_scale, rot_seed, rot_r0,
+                            rotate, tw, s);
     }
     return ks_impl<float>((const float *)in1, (const float *)in2, in_bstride, (float *)out1, (float *)out2,
-                          (float2 *)work, n, batch, forward, rot_seed, rot_r0, rotate, s);
+                          (float2 *)work, n, batch, op, (const float2 *)filt, (float)out_scale, rot_seed, rot_r0,
+                          rotate, s);
+}
+
+int launch_ks(const void *in1, const void *in2, long in_bstride, void *out1, void *out2, void *work, int n, int batch,
+              int precision, bool forward, uint64_t rot_seed, int rot_r0, bool rotate, cudaStream_t s)
+{
+    return launch_fft_op(in1, in2, in_bstride, out1, out2, work, n, batch, precision,
+                         forward ? FFT_OP_KS_FWD : FFT_OP_KS_INV, nullptr, 1.0, rot_seed, rot_r0, rotate, s);
 }
 
 }  // namespace fm

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_inv32(const float2 *__restrict_
 
 template <int LOGN>
 __global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, const float2 *__restrict__ tw,
-                                                   int forward)
+                                                   int op, const float2 *__restrict__ filt)
 {
     pdl_entry();
     using P = Plan32<LOGN>;
@@ -177,22 +177,36 @@ __global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, co
 #pragma unroll
     for (int r = 0; r < 32; ++r) v[r] = base[(long)(j + r * P::TV) * N];
     fft_vec<LOGN, W, false>(v, sm32, c, j, tw);
+    if (op == FFT_OP_SPECTRUM) {  // the 2-D spectrum [ky][kx] is the result
+#pragma unroll
+        for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+            for (int r = 0; r < P::RL; ++r) base[(long)(j + m * P::TV + r * P::NSL) * N] = v[m * P::RL + r];
+        return;
+    }
     // kappa_hat = conj(D) gamma_hat (inverse KS) or D kappa_hat (forward KS),
-    // D = (k1^2 - k2^2 + 2 i k1 k2) / (k1^2 + k2^2), D(0) = 0
+    // D = (k1^2 - k2^2 + 2 i k1 k2) / (k1^2 + k2^2), D(0) = 0; or the given
+    // spectrum filt[b][ky][kx]
     const int xi = x0 + c;
     const int k1 = xi < N / 2 ? xi : xi - N;
+    const float2 *fb = filt ? filt + b * (long)N * N + xi : nullptr;
 #pragma unroll
     for (int m = 0; m < P::ML; ++m)
 #pragma unroll
         for (int r = 0; r < P::RL; ++r) {
             const int yi = j + m * P::TV + r * P::NSL;
-            const int k2 = yi < N / 2 ? yi : yi - N;
-            const int den = k1 * k1 + k2 * k2;
-            float2 d = make_float2(0.f, 0.f);
-            if (den != 0) {
-                const float inv = 1.f / (float)den;
-                const float im = (float)(2 * k1 * k2) * inv;
-                d = make_float2((float)(k1 * k1 - k2 * k2) * inv, forward ? im : -im);
+            float2 d;
+            if (op == FFT_OP_FILTER) {
+                d = fb[(long)yi * N];
+            } else {
+                const int k2 = yi < N / 2 ? yi : yi - N;
+                const int den = k1 * k1 + k2 * k2;
+                d = make_float2(0.f, 0.f);
+                if (den != 0) {
+                    const float inv = 1.f / (float)den;
+                    const float im = (float)(2 * k1 * k2) * inv;
+                    d = make_float2((float)(k1 * k1 - k2 * k2) * inv, op == FFT_OP_KS_FWD ? im : -im);
+                }
             }
             v[m * P::RL + r] = cmul(v[m * P::RL + r], d);
         }
@@ -217,7 +231,8 @@ __global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, co
 // ---------------------------------------------------------------------------
 template <int LOGN>
 static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int batch,
-                     bool forward, uint64_t seed, int r0, bool rotate, const float2 *tw, cudaStream_t s)
+                     int op, const float2 *filt, float out_scale, uint64_t seed, int r0, bool rotate,
+                     const float2 *tw, cudaStream_t s)
 {
     using P = Plan32<LOGN>;
     constexpr int RPC = P::TV >= 256 ? 1 : 256 / P::TV;
@@ -232,8 +247,9 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
     FM_CUDA_TRY(fm::smem_attr((const void *)k_cols_ks32<LOGN>, col_smem));
     FM_LAUNCH(FM_K_FFT_ROWS_FWD, k_rows_fwd32<LOGN>, row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs, work,
               total_rows, tw, seed, r0, rotate ? 1 : 0);
-    FM_LAUNCH(FM_K_FFT_COLS_KS, k_cols_ks32<LOGN>, col_grid, col_threads, col_smem, s, work, tw, forward ? 1 : 0);
-    const float scale = 1.f / ((float)P::N * (float)P::N);
+    FM_LAUNCH(FM_K_FFT_COLS_KS, k_cols_ks32<LOGN>, col_grid, col_threads, col_smem, s, work, tw, op, filt);
+    if (op == FFT_OP_SPECTRUM) return FM_OK;
+    const float scale = out_scale / ((float)P::N * (float)P::N);
     FM_LAUNCH(FM_K_FFT_ROWS_INV, k_rows_inv32<LOGN>, row_grid, RPC * P::TV, row_smem, s, work, out1, out2,
               total_rows, tw, scale);
     return FM_OK;
@@ -241,21 +257,32 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
 
 // n = 32 .. 8192 (power of two); other sizes return FM_EINVAL to the caller,
 // which then uses the generic shared-memory Stockham kernels.
+int launch_fft32(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int n,
+                 int batch, int op, const float2 *filt, float out_scale, uint64_t seed, int r0, bool rotate,
+                 const float2 *tw, cudaStream_t s)
+{
+#define FM_KS32(L) \
+    ks32_impl<L>(in1, in2, in_bs, out1, out2, work, batch, op, filt, out_scale, seed, r0, rotate, tw, s)
+    switch (n) {
+    case 32: return FM_KS32(5);
+    case 64: return FM_KS32(6);
+    case 128: return FM_KS32(7);
+    case 256: return FM_KS32(8);
+    case 512: return FM_KS32(9);
+    case 1024: return FM_KS32(10);
+    case 2048: return FM_KS32(11);
+    case 4096: return FM_KS32(12);
+    case 8192: return FM_KS32(13);
+    }
+#undef FM_KS32
+    return FM_EINVAL;
+}
+
 int launch_ks32(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int n,
                 int batch, bool forward, uint64_t seed, int r0, bool rotate, const float2 *tw, cudaStream_t s)
 {
-    switch (n) {
-    case 32: return ks32_impl<5>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
-    case 64: return ks32_impl<6>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
-    case 128: return ks32_impl<7>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
-    case 256: return ks32_impl<8>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
-    case 512: return ks32_impl<9>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
-    case 1024: return ks32_impl<10>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
-    case 2048: return ks32_impl<11>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
-    case 4096: return ks32_impl<12>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
-    case 8192: return ks32_impl<13>(in1, in2, in_bs, out1, out2, work, batch, forward, seed, r0, rotate, tw, s);
-    }
-    return FM_EINVAL;
+    return launch_fft32(in1, in2, in_bs, out1, out2, work, n, batch, forward ? FFT_OP_KS_FWD : FFT_OP_KS_INV,
+                        nullptr, 1.f, seed, r0, rotate, tw, s);
 }
 
 }  // namespace fm

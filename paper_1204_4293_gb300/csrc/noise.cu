@@ -1,5 +1,6 @@
-// noise.cu -- finalize step of the randomised-shear noise maps (Sec. 1):
-// per-pixel, per-band unbiased variance from FP64 sums and the S/N map.
+// noise.cu -- randomised-shear noise maps (Sec. 1): the FP64 accumulation of
+// the bands over realisations, the per-pixel unbiased variance and S/N, and
+// the elementwise helpers of the exact expected variance.
 #include "common.cuh"
 
 namespace fm {
@@ -79,6 +80,58 @@ int launch_noise_finalize(const double *s1, const double *s2, const void *wdata,
     else
         FM_LAUNCH(FM_K_NOISE_FINAL, k_noise_final<float>, (unsigned)g, 256, 0, s, s1, s2, (const float *)wdata, var,
                   (float *)snr, nelem, R);
+    return FM_OK;
+}
+
+// ---- exact expected variance (periodic boundary) ----------------------------
+// out[c][p] = a[c][p]^2 + b[c][p]^2, c < count, p < nn (|K_j|^2 from the two
+// delta responses; |gamma|^2 from the shear)
+template <typename T>
+__global__ void __launch_bounds__(256) k_modulus2(const T *__restrict__ a, long a_bs, const T *__restrict__ b,
+                                                  long b_bs, T *__restrict__ out, long nn, int count)
+{
+    pdl_entry();
+    const long total = nn * count;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+        const long c = i / nn, p = i - c * nn;
+        const T x = a[c * a_bs + p], y = b[c * b_bs + p];
+        out[i] = x * x + y * y;
+    }
+}
+
+// unit shear at pixel 0: gamma1 of map 0 and gamma2 of map 1 (arrays zeroed before)
+template <typename T> __global__ void k_unit_shears(T *g1d, T *g2d, long nn)
+{
+    pdl_entry();
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        g1d[0] = (T)1;
+        g2d[nn] = (T)1;
+    }
+}
+
+int launch_modulus2(const void *a, long a_bs, const void *b, long b_bs, void *out, long nn, int count, int precision,
+                    cudaStream_t s)
+{
+    long g = (nn * count + 255) / 256;
+    if (g > 152L * 16) g = 152L * 16;
+    if (precision == FM_F64)
+        FM_LAUNCH(0, k_modulus2<double>, (unsigned)g, 256, 0, s, (const double *)a, a_bs,
+                  (const double *)b, b_bs, (double *)out, nn, count);
+    else
+        FM_LAUNCH(0, k_modulus2<float>, (unsigned)g, 256, 0, s, (const float *)a, a_bs,
+                  (const float *)b, b_bs, (float *)out, nn, count);
+    return FM_OK;
+}
+
+int launch_unit_shears(void *g1d, void *g2d, long nn, int precision, cudaStream_t s)
+{
+    const size_t es = precision == FM_F64 ? 8 : 4;
+    FM_CUDA_TRY(cudaMemsetAsync(g1d, 0, 2 * nn * es, s));
+    FM_CUDA_TRY(cudaMemsetAsync(g2d, 0, 2 * nn * es, s));
+    if (precision == FM_F64)
+        FM_LAUNCH(0, k_unit_shears<double>, 1, 32, 0, s, (double *)g1d, (double *)g2d, nn);
+    else
+        FM_LAUNCH(0, k_unit_shears<float>, 1, 32, 0, s, (float *)g1d, (float *)g2d, nn);
     return FM_OK;
 }
 

@@ -60,6 +60,7 @@ _SIGS = {
     "fm_map_direct": (_I, [_P, _P, _P, _I, _I, _D, _I, _D, _CFG, _P]),
     "fm_map_direct_masked": (_I, [_P, _P, _P, ctypes.c_long, _P, _P, _I, _I, _I, _D, _I, _D, _CFG, _P]),
     "fm_map_noise": (_I, [_P, _P, _P, _P, _I, _I, _I, _U64, _CFG, _P]),
+    "fm_map_noise_expected": (_I, [_P, _P, _P, _I, _I, _CFG, _P]),
     "fm_band_moments": (_I, [_P, _P, _I, _I, _I, _CFG, _P]),
     "fm_serve_create": (_I, [_SZ, _I, ctypes.POINTER(ctypes.c_void_p)]),
     "fm_serve_submit": (_I, [_P, ctypes.POINTER(fm_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -232,6 +233,19 @@ def fm_map_direct_masked(g1, g2, weight, filt, theta, ell=3, cut_over_theta=0.0,
                                      float(theta), int(ell), float(cut_over_theta), ctypes.byref(c),
                                      _stream(stream)), "fm_map_direct_masked")
     return m, cov
+
+
+def fm_map_noise_expected(g1, g2, J, out=None, stream=None):
+    """Exact expected noise variance of bands 1..J-1 (periodic boundary):
+    [J-1, n, n] in the maps' dtype."""
+    n, batch = _maps(g1, g2)
+    if batch != 1 or g1.dim() != 2:
+        raise ValueError("fm_map_noise_expected takes one [n, n] map")
+    var = torch.empty((J - 1, n, n), dtype=g1.dtype, device=g1.device) if out is None else out
+    c = _cfg(_prec(g1), FM_PERIODIC)
+    _check(_lib.fm_map_noise_expected(_ptr(g1), _ptr(g2), _ptr(var), n, J, ctypes.byref(c), _stream(stream)),
+           "fm_map_noise_expected")
+    return var
 
 
 def fm_map_noise(g1, g2, J, R, seed, boundary=FM_MIRROR, with_snr=True, fuse_depth=0, stream=None):

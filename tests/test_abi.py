@@ -58,6 +58,11 @@ def test_validation_before_any_device_work(fm):
     assert lib.fm_map_direct(None, None, None, 64, 7, 2.0, 3, 0.0, cfg, None) == fm.FM_EINVAL
     assert lib.fm_map_direct(None, None, None, 64, 0, -1.0, 3, 0.0, cfg, None) == fm.FM_EINVAL
     assert lib.fm_map_noise(None, None, None, None, 64, 4, 1, 0, cfg, None) == fm.FM_EINVAL
+    assert lib.fm_map_noise_expected(1, 1, 1, 64, 4, cfg, None) == fm.FM_EINVAL  # mirror boundary
+    assert b"PERIODIC" in lib.fm_last_error()
+    per = fm._cfg(0, fm.FM_PERIODIC)
+    assert lib.fm_map_noise_expected(1, 1, 1, 48, 4, ctypes.byref(per), None) == fm.FM_EINVAL
+    assert lib.fm_map_noise_expected(None, 1, 1, 64, 4, ctypes.byref(per), None) == fm.FM_EINVAL
     assert lib.fm_map_direct_masked(None, None, None, 0, None, None, 64, 1, 1, 4.0, 3, 0.0, cfg, None) == fm.FM_EINVAL
     assert lib.fm_map_direct_masked(1, 1, 1, -1, 1, None, 64, 1, 1, 4.0, 3, 0.0, cfg, None) == fm.FM_EINVAL
     assert lib.fm_map_direct_masked(1, 1, 1, 0, 1, None, 64, 0, 1, 4.0, 3, 0.0, cfg, None) == fm.FM_EINVAL
