@@ -107,9 +107,12 @@ int fm_map_starlet(const void *g1, const void *g2, void *pyramid, int n, int J, 
                    void *stream);
 
 /* Same as fm_map_starlet with HOST buffers (pinned host memory is fastest):
- * copies g1, g2 in, computes, copies the pyramid back, all queued on
- * `stream`; the host buffers must stay valid until the stream reaches that
- * point.  Device buffers are stream-ordered scratch. */
+ * the batch streams through the library's chunk slots (see fm_tune) so that
+ * each chunk's copy in, compute and copy out overlap those of the others;
+ * the work forks from `stream` and joins back into it, so the results are in
+ * pyramid_host once `stream` reaches that point, and the host buffers must
+ * stay valid until then.  Device buffers are stream-ordered scratch of the
+ * chunks in flight (not the whole batch). */
 int fm_map_starlet_host(const void *g1_host, const void *g2_host, void *pyramid_host, int n, int J, int batch,
                         const fm_config *cfg, void *stream);
 

@@ -650,6 +650,49 @@ int map_starlet_run(const void *g1, const void *g2, void *pyramid, int n, int J,
     return map_starlet_dev(g1, g2, pyramid, n, J, batch, cfg, s);
 }
 
+// Host buffers: the chunks of the batch stream through the slots of the
+// internal streams; each copies its shear in, runs KS + starlet and copies its
+// pyramid out.  A slot's next chunk follows its previous copy out on the same
+// stream, so with two or more slots the copies of one chunk overlap the
+// compute of another and the two copy directions overlap each other.
+static int map_starlet_host_run(const char *g1h, const char *g2h, char *pyrh, int n, int J, int batch,
+                                const fm_config &cfg, cudaStream_t origin)
+{
+    ChunkPlan p = plan_chunks(n, J, batch, cfg);
+    const size_t es = esize(cfg), nn = (size_t)n * n;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t in_b = up((size_t)p.C * nn * es), pyr_b = up((size_t)p.C * J * nn * es);
+    const size_t slot_b = p.slot_b + 2 * in_b + pyr_b;
+    int st = FM_OK;
+    if (!twiddles(n, cfg.precision, origin, &st)) return st;
+    Scratch sc;  // freed on `origin` after the join below
+    if ((st = scratch_alloc(sc, slot_b * p.slots, origin))) return st;
+    std::lock_guard<std::mutex> lk(g_ds_mu);
+    DevStreams *ds = nullptr;
+    if ((st = dev_streams(&ds))) return st;
+    FM_CUDA_TRY(cudaEventRecord(ds->fork, origin));
+    for (int k = 0; k < p.slots; ++k) FM_CUDA_TRY(cudaStreamWaitEvent(ds->s[k], ds->fork, 0));
+    int i = 0;
+    for (int b0 = 0; b0 < batch; b0 += p.C, ++i) {
+        const int k = i % p.slots;
+        const int bc = batch - b0 < p.C ? batch - b0 : p.C;
+        cudaStream_t sk = ds->s[k];
+        char *slot = static_cast<char *>(sc.p) + (size_t)k * slot_b;
+        char *d1 = slot + p.slot_b, *d2 = d1 + in_b, *dp = d2 + in_b;
+        const size_t map_b = (size_t)bc * nn * es;
+        FM_CUDA_TRY(cudaMemcpyAsync(d1, g1h + (size_t)b0 * nn * es, map_b, cudaMemcpyHostToDevice, sk));
+        FM_CUDA_TRY(cudaMemcpyAsync(d2, g2h + (size_t)b0 * nn * es, map_b, cudaMemcpyHostToDevice, sk));
+        if ((st = run_chunk(d1, d2, dp, n, J, 0, bc, cfg, p, slot, sk))) return st;
+        FM_CUDA_TRY(cudaMemcpyAsync(pyrh + (size_t)b0 * J * nn * es, dp, (size_t)J * map_b, cudaMemcpyDeviceToHost,
+                                    sk));
+    }
+    for (int k = 0; k < p.slots; ++k) {
+        FM_CUDA_TRY(cudaEventRecord(ds->join[k], ds->s[k]));
+        FM_CUDA_TRY(cudaStreamWaitEvent(origin, ds->join[k], 0));
+    }
+    return FM_OK;
+}
+
 }  // namespace fm
 
 extern "C" {
@@ -677,17 +720,8 @@ int fm_map_starlet_host(const void *g1_host, const void *g2_host, void *pyramid_
     if ((st = check_J(n, J))) return st;
     if (batch < 1) return einval("batch must be >= 1");
     if (!g1_host || !g2_host || !pyramid_host) return einval("null pointer");
-    cudaStream_t s = (cudaStream_t)stream;
-    const size_t map_bytes = (size_t)batch * n * n * esize(cfg);
-    Scratch gin, pyr;
-    if ((st = scratch_alloc(gin, 2 * map_bytes, s))) return st;
-    if ((st = scratch_alloc(pyr, (size_t)J * map_bytes, s))) return st;
-    char *d1 = static_cast<char *>(gin.p);
-    FM_CUDA_TRY(cudaMemcpyAsync(d1, g1_host, map_bytes, cudaMemcpyHostToDevice, s));
-    FM_CUDA_TRY(cudaMemcpyAsync(d1 + map_bytes, g2_host, map_bytes, cudaMemcpyHostToDevice, s));
-    if ((st = map_starlet_dev(d1, d1 + map_bytes, pyr.p, n, J, batch, cfg, s, false))) return st;
-    FM_CUDA_TRY(cudaMemcpyAsync(pyramid_host, pyr.p, (size_t)J * map_bytes, cudaMemcpyDeviceToHost, s));
-    return FM_OK;
+    return map_starlet_host_run(static_cast<const char *>(g1_host), static_cast<const char *>(g2_host),
+                                static_cast<char *>(pyramid_host), n, J, batch, cfg, (cudaStream_t)stream);
 }
 
 int fm_map_direct(const void *g1, const void *g2, void *map, int n, int filter, double theta_px, int ell,

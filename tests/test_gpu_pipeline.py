@@ -114,3 +114,29 @@ def test_chunk_plans_give_identical_pyramids(streams, graphs):
         fm.fm_trim()
     o = oracle.map_starlet(g1[batch - 1].double().cpu().numpy(), g2[batch - 1].double().cpu().numpy(), J)
     assert max(band_errs(ref[batch - 1].cpu().numpy(), o)) <= 1e-5
+
+
+@pytest.mark.parametrize("streams", [1, 2, 4])
+@pytest.mark.parametrize("dtype,pinned", [(torch.float32, True), (torch.float64, True), (torch.float32, False)])
+def test_host_pipeline_over_chunk_slots(streams, dtype, pinned):
+    # 7 maps in chunks of 2 through 1, 2 or 4 slots: copy in, compute and copy
+    # out per chunk; equals the device-buffer call
+    fm = _fm()
+    n, J, batch = 128, 5, 7
+    g1 = torch.randn(batch, n, n, dtype=dtype).mul_(0.1)
+    g2 = torch.randn(batch, n, n, dtype=dtype).mul_(0.1)
+    out = torch.full((batch, J, n, n), float("nan"), dtype=dtype)
+    if pinned:
+        g1, g2, out = g1.pin_memory(), g2.pin_memory(), out.pin_memory()
+    es = 8 if dtype == torch.float64 else 4
+    per_map = n * n * es * 5
+    fm.fm_tune(fm.FM_TUNE_CHUNK_BYTES, 2 * per_map + per_map // 2)
+    fm.fm_tune(fm.FM_TUNE_CHUNK_STREAMS, streams)
+    try:
+        fm.fm_map_starlet_host(g1, g2, J, out)
+        torch.cuda.synchronize()
+    finally:
+        fm.fm_tune(fm.FM_TUNE_CHUNK_BYTES, -1)
+        fm.fm_tune(fm.FM_TUNE_CHUNK_STREAMS, -1)
+    dev = fm.fm_map_starlet(g1.cuda(), g2.cuda(), J).cpu()
+    assert torch.equal(out, dev)
