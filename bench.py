@@ -163,8 +163,11 @@ def make_inputs(fm, torch, n, batch, seed, dtype, distinct=None, alpha=2.0):
 
 
 def cuda_time(torch, fn, reps):
+    """Mean device time of fn over `reps` calls after one untimed call (which
+    records any CUDA graph the call replays)."""
     s = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
     torch.cuda.synchronize()
     e0.record(s)
     for _ in range(reps):
@@ -279,8 +282,7 @@ def side_legs(fm, torch, n, J, g1, g2):
     out["serving"] = serving_leg(fm, torch)
     # batched noise maps: R realisations of KS + starlet with FP64 accumulation
     R = 1000
-    fm.fm_map_noise(s1, s2, J, 8, seed=3)
-    t_noise = cuda_time(torch, lambda: fm.fm_map_noise(s1, s2, J, R, seed=3), 1)
+    t_noise = cuda_time(torch, lambda: fm.fm_map_noise(s1, s2, J, R, seed=3), 2)
     out["noise"] = {"R": R, "ms": t_noise, "value": n * n * J * R / (t_noise * 1e-3) / 1e6, "unit": UNIT}
     # the exact expectation of that variance (periodic boundary): one FFT pipeline
     t_exp = cuda_time(torch, lambda: fm.fm_map_noise_expected(s1, s2, J), 5)
