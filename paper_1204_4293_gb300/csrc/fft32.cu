@@ -12,10 +12,12 @@
 // table.
 //
 //   rows_fwd32 : (gamma1 + i gamma2) [rotated for noise maps] -> row FFT
-//   cols_ks32  : column FFT -> x conj(D) (or D) -> column inverse FFT, on a
-//                strip of W columns; for n = 1024 the forward output is
-//                already in the inverse's input order, so it stays in registers
-//   rows_inv32 : row inverse FFT -> (Re, Im) * 1/n^2
+//   cols_ks32  : column FFT -> x conj(D) (or D, or a given spectrum) ->
+//                column inverse FFT, on a strip of W columns; for n = 1024 the
+//                forward output is already in the inverse's input order, so it
+//                stays in registers.  The spectrum-only mode stores the 2-D
+//                spectrum after the forward transform.
+//   rows_inv32 : row inverse FFT -> (Re, Im) * scale / n^2
 #include "common.cuh"
 #include "dft.cuh"
 #include "rng.cuh"

@@ -6,13 +6,19 @@
 // and stores the aperture-mass map w_j = c_{j-1} - c_j (theta = 2^j px).
 //
 // Kernels:
-//   st_tile : scales j0..j1 fused on a 2-D tile held in shared memory with a
-//             halo of sum_j 2^j pixels per side; reads c_{j0-1} once, writes
-//             w_j0..w_j1 and c_j1.  Used for the small scales.
+//   st_tile32v2 : (fp32, default) scales 1..F fused on a 64 x 64 tile held in
+//             shared memory with a halo of sum_j 2^j pixels per side; each
+//             thread row-filters the rows of its column run into a register
+//             window and filters that down the column; reads kappa once,
+//             writes w_1..w_F and c_F.
+//   st_tile32 / st_tile : the same scales with a row-filtered shared buffer
+//             (fp32 alternative behind a tuning knob / fp64 and generic).
 //   st_row  : r = rows-filtered c_{j-1} for one (large) scale.
 //   st_col  : c_j = columns-filtered r, w_j = c_{j-1} - c_j; c_j may overwrite
 //             c_{j-1} in place (each thread reads and writes only its own
 //             pixel of that array).
+//   st_rows_multi / st_cols_multi : every large scale in two kernels (the
+//             row and column filters commute); optional, slower here.
 #include "common.cuh"
 
 namespace fm {
