@@ -470,21 +470,38 @@ __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3) k_st_tile32v2(const float
     const float *src = in + b * in_bs;
     const bool vok = vec_ok != 0;
 
-    for (int e = threadIdx.x; e < P * NQ; e += blockDim.x) {
-        const int i = e / NQ, q = e % NQ;
-        const int gy = fold_index(ty0 - HP + i, n, boundary);
-        const int gx0 = tx0 - HP + q * 4;
-        const float *rowp = src + (long)gy * n;
-        float4 v;
-        if (vok && gx0 >= 0 && gx0 + 4 <= n) {
-            v = f4(rowp + gx0);
-        } else {
-            v.x = rowp[fold_index(gx0, n, boundary)];
-            v.y = rowp[fold_index(gx0 + 1, n, boundary)];
-            v.z = rowp[fold_index(gx0 + 2, n, boundary)];
-            v.w = rowp[fold_index(gx0 + 3, n, boundary)];
+    if (vok && ty0 >= HP && tx0 >= HP && ty0 + TS + HP <= n && tx0 + TS + HP <= n) {
+        // interior tile: no folding; every thread's loads are in flight together
+        constexpr int IT = (P * NQ + 255) / 256;
+        const float *org = src + (long)(ty0 - HP) * n + (tx0 - HP);
+        float4 v[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const int e = threadIdx.x + it * 256;
+            if (e < P * NQ) v[it] = f4(org + (long)(e / NQ) * n + (e % NQ) * 4);
         }
-        sf4(b0 + i * P + q * 4, v);
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const int e = threadIdx.x + it * 256;
+            if (e < P * NQ) sf4(b0 + (e / NQ) * P + (e % NQ) * 4, v[it]);
+        }
+    } else {
+        for (int e = threadIdx.x; e < P * NQ; e += blockDim.x) {
+            const int i = e / NQ, q = e % NQ;
+            const int gy = fold_index(ty0 - HP + i, n, boundary);
+            const int gx0 = tx0 - HP + q * 4;
+            const float *rowp = src + (long)gy * n;
+            float4 v;
+            if (vok && gx0 >= 0 && gx0 + 4 <= n) {
+                v = f4(rowp + gx0);
+            } else {
+                v.x = rowp[fold_index(gx0, n, boundary)];
+                v.y = rowp[fold_index(gx0 + 1, n, boundary)];
+                v.z = rowp[fold_index(gx0 + 2, n, boundary)];
+                v.w = rowp[fold_index(gx0 + 3, n, boundary)];
+            }
+            sf4(b0 + i * P + q * 4, v);
+        }
     }
     __syncthreads();
     float *wb = w_out + b * w_bs;
