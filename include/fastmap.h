@@ -232,6 +232,11 @@ size_t fm_request_scratch_bytes(const fm_request *req);
 const char *fm_status_string(int status);
 const char *fm_last_error(void);   /* message of the calling thread's last error */
 int64_t fm_launch_count(void);     /* kernels launched by this library so far */
+/* 1 if a kernel on the current device gave up waiting for a bulk tensor copy
+ * (an iteration-bounded wait that ran out; its outputs are then missing),
+ * else 0; clears the flag.  Synchronises with the device.  FM_EINVAL if no
+ * device is usable. */
+int fm_device_error(void);
 
 /* Tuning knobs (process-wide; value < 0 restores the default):
  *   FM_TUNE_CHUNK_BYTES  budget of one chunk's intermediates in batched
@@ -243,6 +248,9 @@ int64_t fm_launch_count(void);     /* kernels launched by this library so far */
  *                        default 2)
  *   FM_TUNE_PDL          1 = launch kernels as programmatic dependents of
  *                        the previous kernel in their stream (default), 0 = off
+ *   FM_TUNE_TMA          1 = interior tiles of the fused small-scale starlet
+ *                        kernel load their halo by one bulk tensor copy
+ *                        (default), 0 = by per-thread 16-byte loads
  *   FM_TUNE_TILE         fp32 kernel of the fused small starlet scales:
  *                        0 = row-filtered shared buffer, 1 = register
  *                        window (default) */
@@ -251,6 +259,7 @@ int64_t fm_launch_count(void);     /* kernels launched by this library so far */
 #define FM_TUNE_CHUNK_STREAMS 3
 #define FM_TUNE_PDL 4
 #define FM_TUNE_TILE 5
+#define FM_TUNE_TMA 6
 int fm_tune(int knob, int64_t value);
 
 /* Batched fm_map_starlet calls (when chunked) and fm_map_noise calls are

@@ -39,6 +39,7 @@ static int einval(const std::string &msg)
 std::atomic<int64_t> g_launches{0};
 std::atomic<int> g_pdl{1};
 std::atomic<int> g_tile_variant{1};
+std::atomic<int> g_use_tma{1};
 
 namespace {
 struct Prof {
@@ -430,7 +431,8 @@ static int map_starlet_dev(const void *g1, const void *g2, void *pyramid, int n,
         if ((st = scratch_alloc(sc, p.slot_b * p.slots, s))) return st;
         return run_chunks(g1, g2, pyramid, n, J, batch, cfg, p, (char *)sc.p, s, *ds);
     }
-    GraphKey key{g1, g2, pyramid, n, J, batch, 0, cfg, p.C, p.slots, g_pdl.load() | (g_tile_variant.load() << 1)};
+    GraphKey key{g1, g2, pyramid, n, J, batch, 0, cfg, p.C, p.slots,
+                 g_pdl.load() | (g_tile_variant.load() << 1) | (g_use_tma.load() << 3)};
     FM_CUDA_TRY(cudaGetDevice(&key.dev));
     GraphEntry *hit = nullptr;
     for (auto &e : g_graphs)
@@ -607,7 +609,7 @@ int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out
     DevStreams *ds = nullptr;
     if ((st = dev_streams(&ds))) return st;
     NoiseKey key{g1, g2, var_out, snr_out, n, J, R, 0, seed, cfg, L.p.C, L.slots,
-                 g_pdl.load() | (g_tile_variant.load() << 1)};
+                 g_pdl.load() | (g_tile_variant.load() << 1) | (g_use_tma.load() << 3)};
     FM_CUDA_TRY(cudaGetDevice(&key.dev));
     NoiseGraph *hit = nullptr;
     for (auto &e : g_noise_graphs)
@@ -894,6 +896,7 @@ int fm_tune(int knob, int64_t value)
         g_chunk_streams.store(value < 0 ? 2 : (int)(value < 1 ? 1 : value > kMaxChunkStreams ? kMaxChunkStreams : value));
         return FM_OK;
     case FM_TUNE_PDL: g_pdl.store(value < 0 ? 1 : (value != 0)); return FM_OK;
+    case FM_TUNE_TMA: g_use_tma.store(value < 0 ? 1 : (value != 0)); return FM_OK;
     case FM_TUNE_TILE:
         if (value > 1) return einval("FM_TUNE_TILE takes 0 or 1");
         g_tile_variant.store(value < 0 ? 1 : (int)value);
@@ -915,6 +918,13 @@ int fm_profile_select(int kid)
     g_prof.pending = nullptr;
     g_prof_kid.store(kid);
     return FM_OK;
+}
+
+int fm_device_error(void)
+{
+    const int v = starlet_wait_error(true);
+    if (v < 0) return einval("fm_device_error: no device");
+    return v;
 }
 
 int fm_profile_read(double *total_ms, int64_t *launches)

@@ -19,9 +19,49 @@
 //             pixel of that array).
 //   st_rows_multi / st_cols_multi : every large scale in two kernels (the
 //             row and column filters commute); optional, slower here.
+#include <cuda.h>  // CUtensorMap (type only; the encoder is fetched from the driver at run time)
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 
 namespace fm {
+
+// ---- bulk tensor copies (TMA) with an mbarrier --------------------------------
+// Set by a kernel whose wait on a bulk copy ran out of iterations (the copy
+// never arrived); read and cleared by fm_device_error.
+__device__ int g_starlet_wait_error;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// box of the 3-D tensor map at (x, y, z) into shared memory (128-byte aligned)
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+constexpr int kMaxWaitIters = 1 << 20;  // bound on polls of one bulk copy
 
 template <typename T> struct B3 {
     // h = [1, 4, 6, 4, 1] / 16
@@ -106,7 +146,6 @@ __global__ void __launch_bounds__(256) k_st_tile(const T *__restrict__ in, long 
     const int ty0 = (t / tiles_x) * TS;
     const int tx0 = (t % tiles_x) * TS;
     const T *src = in + b * in_bs;
-    const long nn = (long)n * n;
     const bool vok = vec_ok != 0;
 
     for (int e = threadIdx.x; e < P * NQ; e += blockDim.x) {
@@ -237,7 +276,6 @@ __global__ void __launch_bounds__(256) k_st_tile32(const float *__restrict__ in,
     const int ty0 = (t / tiles_x) * TS;
     const int tx0 = (t % tiles_x) * TS;
     const float *src = in + b * in_bs;
-    const long nn = (long)n * n;
     const bool vok = vec_ok != 0;
 
     for (int e = threadIdx.x; e < P * NQ; e += blockDim.x) {
@@ -448,11 +486,20 @@ __device__ __forceinline__ void tile2_scale(const float *__restrict__ A, float *
     }
 }
 
+// Shared memory: 128 bytes of alignment slack, two P x P buffers, one mbarrier.
+template <int F> constexpr size_t tile2_smem()
+{
+    constexpr int H = (1 << (F + 1)) - 2, HP = ((H + 3) / 4) * 4, P = 64 + 2 * HP;
+    return 128 + 2ull * P * P * sizeof(float) + 8;
+}
+
+// tmap (when use_tma): kappa as a 3-D tensor {n, n, batch} of fp32 with a
+// P x P x 1 box; interior tiles then arrive by one bulk tensor copy.
 template <int F>
-__global__ void __launch_bounds__(256, F >= 4 ? 1 : 3) k_st_tile32v2(const float *__restrict__ in, long in_bs,
-                                                        float *__restrict__ w_out, long w_bs, long w_ss,
-                                                        float *__restrict__ c_out, long c_bs, int n, int boundary,
-                                                        int tiles_x, int tiles_per_map, int vec_ok)
+__global__ void __launch_bounds__(256, F >= 4 ? 1 : 3)
+    k_st_tile32v2(const float *__restrict__ in, long in_bs, float *__restrict__ w_out, long w_bs, long w_ss,
+                  float *__restrict__ c_out, long c_bs, int n, int boundary, int tiles_x, int tiles_per_map,
+                  int vec_ok, const __grid_constant__ CUtensorMap tmap, int use_tma)
 {
     pdl_entry();
     constexpr int TS = 64;
@@ -461,8 +508,10 @@ __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3) k_st_tile32v2(const float
     constexpr int P = TS + 2 * HP;
     constexpr int NQ = P / 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *b0 = reinterpret_cast<float *>(smem_raw);  // c_0, c_2, ...
-    float *b1 = b0 + P * P;                           // c_1, c_3, ...
+    // bulk tensor copies want a 128-byte aligned destination
+    float *b0 = reinterpret_cast<float *>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));  // c_0, c_2, ...
+    float *b1 = b0 + P * P;                                                                      // c_1, c_3, ...
+    uint64_t *bar = reinterpret_cast<uint64_t *>(b1 + P * P);
     const long b = blockIdx.x / tiles_per_map;
     const int t = blockIdx.x - (int)(b * tiles_per_map);
     const int ty0 = (t / tiles_x) * TS;
@@ -470,7 +519,22 @@ __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3) k_st_tile32v2(const float
     const float *src = in + b * in_bs;
     const bool vok = vec_ok != 0;
 
-    if (vok && ty0 >= HP && tx0 >= HP && ty0 + TS + HP <= n && tx0 + TS + HP <= n) {
+    const bool interior = vok && ty0 >= HP && tx0 >= HP && ty0 + TS + HP <= n && tx0 + TS + HP <= n;
+    if (interior && use_tma) {
+        // one bulk tensor copy of the P x P halo box, completion on the mbarrier
+        if (threadIdx.x == 0) mbar_init(bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(bar, (uint32_t)(P * P * sizeof(float)));
+            tma_load_3d(b0, &tmap, tx0 - HP, ty0 - HP, (int)b, bar);
+        }
+        bool done = false;
+        for (int it = 0; it < kMaxWaitIters && !done; ++it) done = mbar_try_wait(bar, 0);
+        if (__syncthreads_or(!done)) {  // the copy never completed: report and leave, the whole CTA together
+            if (threadIdx.x == 0) atomicExch(&g_starlet_wait_error, 1);
+            return;
+        }
+    } else if (interior) {
         // interior tile: no folding; every thread's loads are in flight together
         constexpr int IT = (P * NQ + 255) / 256;
         const float *org = src + (long)(ty0 - HP) * n + (tx0 - HP);
@@ -817,6 +881,41 @@ static int tile_launch(const T *in, T *w_out, long w_bs, long w_ss, T *c_out, lo
     return FM_OK;
 }
 
+// 3-D fp32 tensor map {n, n, batch} (batch stride bs elements) with a
+// box_x x box_y x 1 box, through the driver's encoder (fetched once).
+// Returns false when the encoder is missing or refuses the layout.
+static bool encode_map3d_f32(CUtensorMap *map, const float *base, int n, int batch, long bs, int box_x, int box_y)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode || (reinterpret_cast<uintptr_t>(base) & 15) || n % 4 || (bs * 4) % 16) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)n * 4, (cuuint64_t)bs * 4};  // bytes, dims 1 and 2
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int starlet_wait_error(bool clear)
+{
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_starlet_wait_error, sizeof(int)) != cudaSuccess) return -1;
+    if (clear && v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_starlet_wait_error, &z, sizeof(int));
+    }
+    return v;
+}
+
 template <int F>
 static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, float *c_out, long c_bs, int n,
                          int boundary, int batch, bool vec_ok, cudaStream_t s)
@@ -831,9 +930,15 @@ static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, fl
     const int variant = g_tile_variant.load(std::memory_order_relaxed);
     if (variant == 1) {
         auto k = k_st_tile32v2<F>;
-        FM_CUDA_TRY(fm::smem_attr((const void *)k, smem));
-        FM_LAUNCH(FM_K_STARLET_TILE, k, (unsigned)(tiles_per_map * (long)batch), 256, smem, s, in, (long)n * n, w_out,
-                  w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, vec_ok ? 1 : 0);
+        const size_t smem2 = tile2_smem<F>();
+        FM_CUDA_TRY(fm::smem_attr((const void *)k, smem2));
+        CUtensorMap map;
+        const int use_tma = g_use_tma.load(std::memory_order_relaxed) && vec_ok && n >= 2 * TS + 2 * HP &&
+                            encode_map3d_f32(&map, in, n, batch, (long)n * n, P, P);
+        if (!use_tma) memset(&map, 0, sizeof(map));
+        FM_LAUNCH(FM_K_STARLET_TILE, k, (unsigned)(tiles_per_map * (long)batch), 256, smem2, s, in, (long)n * n,
+                  w_out, w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, vec_ok ? 1 : 0, map,
+                  use_tma);
         return FM_OK;
     }
     FM_CUDA_TRY(fm::smem_attr((const void *)k_st_tile32<F>, smem));

@@ -71,6 +71,7 @@ _SIGS = {
     "fm_status_string": (ctypes.c_char_p, [_I]),
     "fm_last_error": (ctypes.c_char_p, []),
     "fm_launch_count": (ctypes.c_int64, []),
+    "fm_device_error": (_I, []),
     "fm_profile_select": (_I, [_I]),
     "fm_tune": (_I, [_I, ctypes.c_int64]),
     "fm_trim": (_I, []),
@@ -262,7 +263,7 @@ def fm_map_noise(g1, g2, J, R, seed, boundary=FM_MIRROR, with_snr=True, fuse_dep
     return var, snr
 
 
-FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS, FM_TUNE_CHUNK_STREAMS, FM_TUNE_PDL, FM_TUNE_TILE = 1, 2, 3, 4, 5
+FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS, FM_TUNE_CHUNK_STREAMS, FM_TUNE_PDL, FM_TUNE_TILE, FM_TUNE_TMA = 1, 2, 3, 4, 5, 6
 
 
 def fm_tune(knob: int, value: int) -> None:
@@ -291,6 +292,14 @@ def fm_trim() -> None:
 
 def fm_launch_count() -> int:
     return int(_lib.fm_launch_count())
+
+
+def fm_device_error() -> int:
+    """1 if a kernel gave up waiting for a bulk copy since the last call."""
+    v = int(_lib.fm_device_error())
+    if v < 0:
+        _check(v, "fm_device_error")
+    return v
 
 
 def fm_profile_select(kernel: str | int) -> None:

@@ -121,3 +121,24 @@ def test_tile_kernel_variants(variant, n, J):
                 assert max(band_errs(pyr.cpu().numpy(), ref)) <= TOL[np.float32], (boundary, fuse)
     finally:
         fm.fm_tune(fm.FM_TUNE_TILE, -1)
+
+
+@pytest.mark.parametrize("n,J,batch", [(256, 5, 3), (1024, 7, 2), (200, 4, 1)])
+def test_bulk_copy_halo_equals_thread_loads(n, J, batch):
+    # interior tiles take their halo by one bulk tensor copy (default) or by
+    # per-thread loads: identical pyramids, no wait ran out
+    fm = _fm()
+    maps = np.stack([synth.grf_kappa(n, seed=7 + b) for b in range(batch)]).astype(np.float32)
+    kap = torch.from_numpy(maps).cuda()
+    fm.fm_tune(fm.FM_TUNE_TMA, 1)
+    with_tma = fm.fm_starlet_forward(kap, J)
+    fm.fm_tune(fm.FM_TUNE_TMA, 0)
+    try:
+        without = fm.fm_starlet_forward(kap, J)
+    finally:
+        fm.fm_tune(fm.FM_TUNE_TMA, -1)
+    torch.cuda.synchronize()
+    assert fm.fm_device_error() == 0
+    assert torch.equal(with_tma, without)
+    ref = oracle.starlet(maps[batch - 1].astype(np.float64), J)
+    assert max(band_errs(with_tma[batch - 1].cpu().numpy(), ref)) <= 1e-5
