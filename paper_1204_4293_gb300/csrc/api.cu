@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace fm {
 
@@ -209,6 +210,28 @@ static int check_J(int n, int J)
 // in fp32) near 64 MB so it stays in L2
 // realisations per batched pass: enough maps per launch to fill the GPU
 // (~256 MB of per-realisation working set), at most 32
+bool encode_map3d_f32(CUtensorMap *map, const void *base, const uint64_t dims[3], const uint64_t strides[2],
+                      const uint32_t box[3])
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    if (!encode || (reinterpret_cast<uintptr_t>(base) & 15) || strides[0] % 16 || strides[1] % 16) return false;
+    const cuuint64_t d[3] = {dims[0], dims[1], dims[2]};
+    const cuuint64_t st[2] = {strides[0], strides[1]};
+    const cuuint32_t bx[3] = {box[0], box[1], box[2]};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), d, st, bx, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 size_t map_starlet_scratch_bytes(int n, int J, int batch, const fm_config &cfg)
 {
     const size_t es = esize(cfg), nn = (size_t)n * n;
@@ -922,9 +945,9 @@ int fm_profile_select(int kid)
 
 int fm_device_error(void)
 {
-    const int v = starlet_wait_error(true);
-    if (v < 0) return einval("fm_device_error: no device");
-    return v;
+    const int a = starlet_wait_error(true), b = fft_wait_error(true);
+    if (a < 0 || b < 0) return einval("fm_device_error: no device");
+    return a | b;
 }
 
 int fm_profile_read(double *total_ms, int64_t *launches)

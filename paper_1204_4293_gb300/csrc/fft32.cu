@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "dft.cuh"
 #include "rng.cuh"
+#include "tma.cuh"
 
 namespace fm {
 
@@ -91,22 +92,56 @@ __device__ __forceinline__ void fft_vec(float2 (&v)[32], float2 *sm, int c, int 
     }
 }
 
+// With use_tma (n >= 64; in_bs = n^2, or in_bs = 0 with RPC <= n), the CTA's
+// rows of gamma1 (m1) and gamma2 (m2) arrive by bulk tensor copies into the
+// exchange buffer, viewed as [RPC][n] floats per array, before the first
+// pass reads them.
 template <int LOGN>
 __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__ in1, const float *__restrict__ in2,
                                                        long in_bs, float2 *__restrict__ work, long total_rows,
                                                        const float2 *__restrict__ tw, uint64_t seed, int r0,
-                                                       int rotate)
+                                                       int rotate, const __grid_constant__ CUtensorMap m1,
+                                                       const __grid_constant__ CUtensorMap m2, int use_tma)
 {
     pdl_entry();
     using P = Plan32<LOGN>;
     constexpr int RPC = P::TV >= 256 ? 1 : 256 / P::TV;
     extern __shared__ __align__(16) float2 sm32[];
+    __shared__ uint64_t bar;
+    float2 *smb = align128<float2>(sm32);
     const int vr = threadIdx.x / P::TV, j = threadIdx.x % P::TV;
     const long row = (long)blockIdx.x * RPC + vr;
-    float2 *sm = sm32 + vr * (P::N + P::N / 32);
+    float2 *sm = smb + vr * (P::N + P::N / 32);
     const bool live = row < total_rows;
     float2 v[32];
-    if (live) {
+    bool staged = false;
+    if constexpr (P::NPASS > 1) {
+        if (use_tma) {
+            float *st1 = reinterpret_cast<float *>(smb), *st2 = st1 + RPC * P::N;
+            if (threadIdx.x == 0) mbar_init(&bar, 1);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const long row0 = (long)blockIdx.x * RPC;
+                const int z = (int)(in_bs == 0 ? (row0 & (P::N - 1)) : row0);
+                mbar_expect_tx(&bar, (uint32_t)(RPC * P::N * sizeof(float) * (in2 ? 2 : 1)));
+                tma_load_3d(st1, &m1, 0, 0, z, &bar);
+                if (in2) tma_load_3d(st2, &m2, 0, 0, z, &bar);
+            }
+            if (!tma_wait_all(&bar, 0)) return;  // the copies never completed (flagged)
+            const long b = row >> LOGN;
+            const int y = (int)(row & (P::N - 1));
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const int x = j + r * P::TV;
+                float a = st1[vr * P::N + x];
+                float cc = in2 ? st2[vr * P::N + x] : 0.f;
+                if (rotate) rotate_shear(a, cc, seed, r0 + b, y, x, P::N);
+                v[r] = make_float2(a, cc);
+            }
+            staged = true;  // fft_vec's first barrier orders these reads before the exchange writes
+        }
+    }
+    if (!staged && live) {
         const long b = row >> LOGN;
         const int y = (int)(row & (P::N - 1));
         const float *p1 = in1 + b * in_bs + (long)y * P::N;
@@ -119,7 +154,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__
             if (rotate) rotate_shear(a, cc, seed, r0 + b, y, x, P::N);
             v[r] = make_float2(a, cc);
         }
-    } else {
+    } else if (!staged) {
 #pragma unroll
         for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
     }
@@ -133,23 +168,46 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__
     }
 }
 
+// With use_tma (n >= 64, every CTA's RPC rows inside the batch), the CTA's
+// complex rows arrive by one bulk tensor copy (mw: the work buffer as floats)
+// into the exchange buffer, viewed as [RPC][n] float2.
 template <int LOGN>
 __global__ void __launch_bounds__(256, 2) k_rows_inv32(const float2 *__restrict__ work, float *__restrict__ out1,
                                                        float *__restrict__ out2, long total_rows,
-                                                       const float2 *__restrict__ tw, float scale)
+                                                       const float2 *__restrict__ tw, float scale,
+                                                       const __grid_constant__ CUtensorMap mw, int use_tma)
 {
     pdl_entry();
     using P = Plan32<LOGN>;
     constexpr int RPC = P::TV >= 256 ? 1 : 256 / P::TV;
     extern __shared__ __align__(16) float2 sm32[];
+    __shared__ uint64_t bar;
+    float2 *smb = align128<float2>(sm32);
     const int vr = threadIdx.x / P::TV, j = threadIdx.x % P::TV;
     const long row = (long)blockIdx.x * RPC + vr;
-    float2 *sm = sm32 + vr * (P::N + P::N / 32);
+    float2 *sm = smb + vr * (P::N + P::N / 32);
     const bool live = row < total_rows;
     float2 v[32];
-    const float2 *src = work + row * P::N;
+    bool staged = false;
+    if constexpr (P::NPASS > 1) {
+        if (use_tma) {
+            if (threadIdx.x == 0) mbar_init(&bar, 1);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                mbar_expect_tx(&bar, (uint32_t)(RPC * P::N * sizeof(float2)));
+                tma_load_3d(smb, &mw, 0, 0, (int)((long)blockIdx.x * RPC), &bar);
+            }
+            if (!tma_wait_all(&bar, 0)) return;  // the copy never completed (flagged)
 #pragma unroll
-    for (int r = 0; r < 32; ++r) v[r] = live ? src[j + r * P::TV] : make_float2(0.f, 0.f);
+            for (int r = 0; r < 32; ++r) v[r] = smb[vr * P::N + j + r * P::TV];
+            staged = true;  // fft_vec's first barrier orders these reads before the exchange writes
+        }
+    }
+    if (!staged) {
+        const float2 *src = work + row * P::N;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = live ? src[j + r * P::TV] : make_float2(0.f, 0.f);
+    }
     fft_vec<LOGN, 1, true>(v, sm, 0, j, tw);
     if (live) {
 #pragma unroll
@@ -242,20 +300,46 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
     constexpr int RPC = P::TV >= 256 ? 1 : 256 / P::TV;
     const long total_rows = (long)batch * P::N;
     const unsigned row_grid = (unsigned)((total_rows + RPC - 1) / RPC);
-    const size_t row_smem = P::NPASS > 1 ? (size_t)RPC * (P::N + P::N / 32) * sizeof(float2) : 0;
+    // exchange buffer (which also stages the TMA rows: RPC n floats per input
+    // array or RPC n float2 <= RPC (n + n/32) float2) + 128 bytes of alignment
+    const size_t row_smem = P::NPASS > 1 ? (size_t)RPC * (P::N + P::N / 32) * sizeof(float2) + 128 : 0;
     const int col_threads = P::W * P::TV;
     const size_t col_smem = P::NPASS > 1 ? (size_t)(P::N * P::W + P::N * P::W / 32 + 1) * sizeof(float2) : 0;
     const unsigned col_grid = (unsigned)((long)batch * (P::N / P::W));
     FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_fwd32<LOGN>, row_smem));
     FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_inv32<LOGN>, row_smem));
     FM_CUDA_TRY(fm::smem_attr((const void *)k_cols_ks32<LOGN>, col_smem));
+    // bulk tensor copies of whole row groups (RPC consecutive rows of the
+    // batch): n >= 64; the input rows either contiguous over the batch
+    // (in_bs = n^2) or one broadcast map (in_bs = 0) holding a CTA's rows
+    CUtensorMap m1, m2, mw;
+    memset(&m1, 0, sizeof(m1));
+    memset(&m2, 0, sizeof(m2));
+    memset(&mw, 0, sizeof(mw));
+    int tma_in = 0, tma_out = 0;
+    if (P::NPASS > 1 && g_use_tma.load(std::memory_order_relaxed)) {
+        const long nn = (long)P::N * P::N;
+        const uint32_t d0 = P::N < 256 ? P::N : 256;
+        const uint64_t rows = in_bs == 0 ? (uint64_t)P::N : (uint64_t)total_rows;
+        const uint64_t dims[3] = {d0, (uint64_t)(P::N / d0), rows};
+        const uint64_t strides[2] = {(uint64_t)d0 * 4, (uint64_t)P::N * 4};
+        const uint32_t box[3] = {d0, (uint32_t)(P::N / d0), (uint32_t)RPC};
+        // a broadcast map needs each CTA's rows inside it (RPC <= n, i.e. n >= 128)
+        tma_in = (in_bs == nn || (in_bs == 0 && RPC <= P::N)) && encode_map3d_f32(&m1, in1, dims, strides, box) &&
+                 (!in2 || encode_map3d_f32(&m2, in2, dims, strides, box));
+        const uint32_t e0 = 2 * P::N < 256 ? 2 * P::N : 256;
+        const uint64_t wdims[3] = {e0, (uint64_t)(2 * P::N / e0), (uint64_t)total_rows};
+        const uint64_t wstrides[2] = {(uint64_t)e0 * 4, (uint64_t)P::N * 8};
+        const uint32_t wbox[3] = {e0, (uint32_t)(2 * P::N / e0), (uint32_t)RPC};
+        tma_out = encode_map3d_f32(&mw, work, wdims, wstrides, wbox);
+    }
     FM_LAUNCH(FM_K_FFT_ROWS_FWD, k_rows_fwd32<LOGN>, row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs, work,
-              total_rows, tw, seed, r0, rotate ? 1 : 0);
+              total_rows, tw, seed, r0, rotate ? 1 : 0, m1, m2, tma_in);
     FM_LAUNCH(FM_K_FFT_COLS_KS, k_cols_ks32<LOGN>, col_grid, col_threads, col_smem, s, work, tw, op, filt);
     if (op == FFT_OP_SPECTRUM) return FM_OK;
     const float scale = out_scale / ((float)P::N * (float)P::N);
     FM_LAUNCH(FM_K_FFT_ROWS_INV, k_rows_inv32<LOGN>, row_grid, RPC * P::TV, row_smem, s, work, out1, out2,
-              total_rows, tw, scale);
+              total_rows, tw, scale, mw, tma_out);
     return FM_OK;
 }
 
@@ -281,6 +365,8 @@ int launch_fft32(const float *in1, const float *in2, long in_bs, float *out1, fl
 #undef FM_KS32
     return FM_EINVAL;
 }
+
+int fft_wait_error(bool clear) { return wait_error_flag(clear); }
 
 int launch_ks32(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int n,
                 int batch, bool forward, uint64_t seed, int r0, bool rotate, const float2 *tw, cudaStream_t s)

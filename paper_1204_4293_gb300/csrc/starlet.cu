@@ -19,49 +19,10 @@
 //             pixel of that array).
 //   st_rows_multi / st_cols_multi : every large scale in two kernels (the
 //             row and column filters commute); optional, slower here.
-#include <cuda.h>  // CUtensorMap (type only; the encoder is fetched from the driver at run time)
-#include <cudaTypedefs.h>
-
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace fm {
-
-// ---- bulk tensor copies (TMA) with an mbarrier --------------------------------
-// Set by a kernel whose wait on a bulk copy ran out of iterations (the copy
-// never arrived); read and cleared by fm_device_error.
-__device__ int g_starlet_wait_error;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// box of the 3-D tensor map at (x, y, z) into shared memory (128-byte aligned)
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
-constexpr int kMaxWaitIters = 1 << 20;  // bound on polls of one bulk copy
 
 template <typename T> struct B3 {
     // h = [1, 4, 6, 4, 1] / 16
@@ -508,9 +469,8 @@ __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3)
     constexpr int P = TS + 2 * HP;
     constexpr int NQ = P / 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // bulk tensor copies want a 128-byte aligned destination
-    float *b0 = reinterpret_cast<float *>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));  // c_0, c_2, ...
-    float *b1 = b0 + P * P;                                                                      // c_1, c_3, ...
+    float *b0 = align128<float>(smem_raw);  // c_0, c_2, ... (a bulk copy destination)
+    float *b1 = b0 + P * P;                 // c_1, c_3, ...
     uint64_t *bar = reinterpret_cast<uint64_t *>(b1 + P * P);
     const long b = blockIdx.x / tiles_per_map;
     const int t = blockIdx.x - (int)(b * tiles_per_map);
@@ -528,12 +488,7 @@ __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3)
             mbar_expect_tx(bar, (uint32_t)(P * P * sizeof(float)));
             tma_load_3d(b0, &tmap, tx0 - HP, ty0 - HP, (int)b, bar);
         }
-        bool done = false;
-        for (int it = 0; it < kMaxWaitIters && !done; ++it) done = mbar_try_wait(bar, 0);
-        if (__syncthreads_or(!done)) {  // the copy never completed: report and leave, the whole CTA together
-            if (threadIdx.x == 0) atomicExch(&g_starlet_wait_error, 1);
-            return;
-        }
+        if (!tma_wait_all(bar, 0)) return;  // the copy never completed (flagged)
     } else if (interior) {
         // interior tile: no folding; every thread's loads are in flight together
         constexpr int IT = (P * NQ + 255) / 256;
@@ -881,40 +836,7 @@ static int tile_launch(const T *in, T *w_out, long w_bs, long w_ss, T *c_out, lo
     return FM_OK;
 }
 
-// 3-D fp32 tensor map {n, n, batch} (batch stride bs elements) with a
-// box_x x box_y x 1 box, through the driver's encoder (fetched once).
-// Returns false when the encoder is missing or refuses the layout.
-static bool encode_map3d_f32(CUtensorMap *map, const float *base, int n, int batch, long bs, int box_x, int box_y)
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            fn = nullptr;
-        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }();
-    if (!encode || (reinterpret_cast<uintptr_t>(base) & 15) || n % 4 || (bs * 4) % 16) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)batch};
-    const cuuint64_t strides[2] = {(cuuint64_t)n * 4, (cuuint64_t)bs * 4};  // bytes, dims 1 and 2
-    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-int starlet_wait_error(bool clear)
-{
-    int v = 0;
-    if (cudaMemcpyFromSymbol(&v, g_starlet_wait_error, sizeof(int)) != cudaSuccess) return -1;
-    if (clear && v) {
-        const int z = 0;
-        cudaMemcpyToSymbol(g_starlet_wait_error, &z, sizeof(int));
-    }
-    return v;
-}
+int starlet_wait_error(bool clear) { return wait_error_flag(clear); }
 
 template <int F>
 static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, float *c_out, long c_bs, int n,
@@ -933,8 +855,11 @@ static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, fl
         const size_t smem2 = tile2_smem<F>();
         FM_CUDA_TRY(fm::smem_attr((const void *)k, smem2));
         CUtensorMap map;
+        const uint64_t dims[3] = {(uint64_t)n, (uint64_t)n, (uint64_t)batch};
+        const uint64_t strides[2] = {(uint64_t)n * 4, (uint64_t)n * n * 4};
+        const uint32_t box[3] = {(uint32_t)P, (uint32_t)P, 1};
         const int use_tma = g_use_tma.load(std::memory_order_relaxed) && vec_ok && n >= 2 * TS + 2 * HP &&
-                            encode_map3d_f32(&map, in, n, batch, (long)n * n, P, P);
+                            encode_map3d_f32(&map, in, dims, strides, box);
         if (!use_tma) memset(&map, 0, sizeof(map));
         FM_LAUNCH(FM_K_STARLET_TILE, k, (unsigned)(tiles_per_map * (long)batch), 256, smem2, s, in, (long)n * n,
                   w_out, w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, vec_ok ? 1 : 0, map,

@@ -54,3 +54,26 @@ def test_ks_8192_sampled_rows():
     rms = kappa.double().pow(2).mean().sqrt().item()
     assert (kE - kappa).abs().max().item() / rms < 1e-5
     assert kB.abs().max().item() / rms < 1e-5
+
+
+@pytest.mark.parametrize("n,batch", [(64, 3), (1024, 2), (4096, 1)])
+def test_bulk_copy_rows_equal_thread_loads(n, batch):
+    # the row FFT kernels take their rows by bulk tensor copies (default) or
+    # by per-thread loads: identical results, also for the rotated noise rows
+    # (one broadcast input map), and no wait ran out
+    fm = _fm()
+    g1 = torch.empty((batch, n, n), device="cuda").normal_(0, 0.1)
+    g2 = torch.empty_like(g1).normal_(0, 0.1)
+    outs = {}
+    for tma in (1, 0):
+        fm.fm_tune(fm.FM_TUNE_TMA, tma)
+        try:
+            kE, kB = fm.fm_ks_invert(g1, g2, with_b=True)
+            var, _ = fm.fm_map_noise(g1[0], g2[0], 4, 3, seed=5, with_snr=False)
+            outs[tma] = (kE, kB, var)
+        finally:
+            fm.fm_tune(fm.FM_TUNE_TMA, -1)
+    torch.cuda.synchronize()
+    assert fm.fm_device_error() == 0
+    for a, b in zip(outs[1], outs[0]):
+        assert torch.equal(a, b)
