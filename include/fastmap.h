@@ -248,9 +248,10 @@ int fm_device_error(void);
  *                        default 2)
  *   FM_TUNE_PDL          1 = launch kernels as programmatic dependents of
  *                        the previous kernel in their stream (default), 0 = off
- *   FM_TUNE_TMA          1 = interior tiles of the fused small-scale starlet
- *                        kernel load their halo by one bulk tensor copy
- *                        (default), 0 = by per-thread 16-byte loads
+ *   FM_TUNE_TMA          mask of the loads done by bulk tensor copies (TMA)
+ *                        instead of per-thread loads: 1 = the halo of the
+ *                        fused small-scale starlet tiles, 2 = the input rows
+ *                        of the row FFT, 4 = those of the row inverse FFT
  *   FM_TUNE_TILE         fp32 kernel of the fused small starlet scales:
  *                        0 = row-filtered shared buffer, 1 = register
  *                        window (default) */

@@ -40,7 +40,10 @@ static int einval(const std::string &msg)
 std::atomic<int64_t> g_launches{0};
 std::atomic<int> g_pdl{1};
 std::atomic<int> g_tile_variant{1};
-std::atomic<int> g_use_tma{1};
+// bulk tensor copies: 1 = starlet tile halo, 2 = row FFT input rows, 4 = row
+// IFFT input rows
+constexpr int kDefaultTma = 7;
+std::atomic<int> g_use_tma{kDefaultTma};
 
 namespace {
 struct Prof {
@@ -919,7 +922,10 @@ int fm_tune(int knob, int64_t value)
         g_chunk_streams.store(value < 0 ? 2 : (int)(value < 1 ? 1 : value > kMaxChunkStreams ? kMaxChunkStreams : value));
         return FM_OK;
     case FM_TUNE_PDL: g_pdl.store(value < 0 ? 1 : (value != 0)); return FM_OK;
-    case FM_TUNE_TMA: g_use_tma.store(value < 0 ? 1 : (value != 0)); return FM_OK;
+    case FM_TUNE_TMA:
+        if (value > 7) return einval("FM_TUNE_TMA is a mask of 1, 2 and 4");
+        g_use_tma.store(value < 0 ? kDefaultTma : (int)value);
+        return FM_OK;
     case FM_TUNE_TILE:
         if (value > 1) return einval("FM_TUNE_TILE takes 0 or 1");
         g_tile_variant.store(value < 0 ? 1 : (int)value);

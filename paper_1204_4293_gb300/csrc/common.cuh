@@ -39,7 +39,7 @@ void prof_after(int kid, cudaStream_t s);
 // next kernel's CTAs be scheduled into SMs this grid leaves idle in its tail.
 extern std::atomic<int> g_pdl;
 extern std::atomic<int> g_tile_variant;
-extern std::atomic<int> g_use_tma;  // halo of interior starlet tiles by bulk tensor copy (1) or plain loads (0)
+extern std::atomic<int> g_use_tma;  // bulk tensor copies: 1 tile halo, 2 row FFT rows, 4 row IFFT rows
 int starlet_wait_error(bool clear);  // 1 if a kernel gave up waiting on a bulk copy (see fm_device_error)
 int fft_wait_error(bool clear);  // fp32 fused-scale tile kernel: 0 = smem row buffer, 1 = register window
 __device__ __forceinline__ void pdl_entry()

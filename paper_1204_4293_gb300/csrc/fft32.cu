@@ -317,7 +317,8 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
     memset(&m2, 0, sizeof(m2));
     memset(&mw, 0, sizeof(mw));
     int tma_in = 0, tma_out = 0;
-    if (P::NPASS > 1 && g_use_tma.load(std::memory_order_relaxed)) {
+    const int tma_mode = g_use_tma.load(std::memory_order_relaxed);
+    if (P::NPASS > 1 && (tma_mode & 6)) {
         const long nn = (long)P::N * P::N;
         const uint32_t d0 = P::N < 256 ? P::N : 256;
         const uint64_t rows = in_bs == 0 ? (uint64_t)P::N : (uint64_t)total_rows;
@@ -325,13 +326,13 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
         const uint64_t strides[2] = {(uint64_t)d0 * 4, (uint64_t)P::N * 4};
         const uint32_t box[3] = {d0, (uint32_t)(P::N / d0), (uint32_t)RPC};
         // a broadcast map needs each CTA's rows inside it (RPC <= n, i.e. n >= 128)
-        tma_in = (in_bs == nn || (in_bs == 0 && RPC <= P::N)) && encode_map3d_f32(&m1, in1, dims, strides, box) &&
-                 (!in2 || encode_map3d_f32(&m2, in2, dims, strides, box));
+        tma_in = (tma_mode & 2) && (in_bs == nn || (in_bs == 0 && RPC <= P::N)) &&
+                 encode_map3d_f32(&m1, in1, dims, strides, box) && (!in2 || encode_map3d_f32(&m2, in2, dims, strides, box));
         const uint32_t e0 = 2 * P::N < 256 ? 2 * P::N : 256;
         const uint64_t wdims[3] = {e0, (uint64_t)(2 * P::N / e0), (uint64_t)total_rows};
         const uint64_t wstrides[2] = {(uint64_t)e0 * 4, (uint64_t)P::N * 8};
         const uint32_t wbox[3] = {e0, (uint32_t)(2 * P::N / e0), (uint32_t)RPC};
-        tma_out = encode_map3d_f32(&mw, work, wdims, wstrides, wbox);
+        tma_out = (tma_mode & 4) && encode_map3d_f32(&mw, work, wdims, wstrides, wbox);
     }
     FM_LAUNCH(FM_K_FFT_ROWS_FWD, k_rows_fwd32<LOGN>, row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs, work,
               total_rows, tw, seed, r0, rotate ? 1 : 0, m1, m2, tma_in);

@@ -860,7 +860,7 @@ static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, fl
         const uint64_t dims[3] = {(uint64_t)n, (uint64_t)n, (uint64_t)batch};
         const uint64_t strides[2] = {(uint64_t)n * 4, (uint64_t)n * n * 4};
         const uint32_t box[3] = {(uint32_t)P, (uint32_t)P, 1};
-        const int use_tma = g_use_tma.load(std::memory_order_relaxed) && vec_ok && n >= 2 * TS + 2 * HP &&
+        const int use_tma = (g_use_tma.load(std::memory_order_relaxed) & 1) && vec_ok && n >= 2 * TS + 2 * HP &&
                             encode_map3d_f32(&map, in, dims, strides, box);
         if (!use_tma) memset(&map, 0, sizeof(map));
         FM_LAUNCH(FM_K_STARLET_TILE, k, (unsigned)(tiles_per_map * (long)batch), 256, smem2, s, in, (long)n * n,
