@@ -251,7 +251,10 @@ int fm_device_error(void);
  *   FM_TUNE_TMA          mask of the loads done by bulk tensor copies (TMA)
  *                        instead of per-thread loads: 1 = the halo of the
  *                        fused small-scale starlet tiles, 2 = the input rows
- *                        of the row FFT, 4 = those of the row inverse FFT
+ *                        of the row FFT, 4 = those of the row inverse FFT,
+ *                        8 / 16 = the window rows / the c_{j-1} rows of the
+ *                        large-scale column pass (fp32 maps of 4096^2 and
+ *                        up); default 31
  *   FM_TUNE_TILE         fp32 kernel of the fused small starlet scales:
  *                        0 = row-filtered shared buffer, 1 = register
  *                        window (default) */

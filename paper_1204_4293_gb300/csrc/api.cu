@@ -41,8 +41,9 @@ std::atomic<int64_t> g_launches{0};
 std::atomic<int> g_pdl{1};
 std::atomic<int> g_tile_variant{1};
 // bulk tensor copies: 1 = starlet tile halo, 2 = row FFT input rows, 4 = row
-// IFFT input rows
-constexpr int kDefaultTma = 7;
+// IFFT input rows, 8 = large-scale column window rows, 16 = its c_{j-1} rows
+// (the last two on maps of 4096^2 and up)
+constexpr int kDefaultTma = 31;
 std::atomic<int> g_use_tma{kDefaultTma};
 
 namespace {
@@ -213,8 +214,7 @@ static int check_J(int n, int J)
 // in fp32) near 64 MB so it stays in L2
 // realisations per batched pass: enough maps per launch to fill the GPU
 // (~256 MB of per-realisation working set), at most 32
-bool encode_map3d_f32(CUtensorMap *map, const void *base, const uint64_t dims[3], const uint64_t strides[2],
-                      const uint32_t box[3])
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
         void *fn = nullptr;
@@ -225,14 +225,40 @@ bool encode_map3d_f32(CUtensorMap *map, const void *base, const uint64_t dims[3]
             fn = nullptr;
         return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }();
-    if (!encode || (reinterpret_cast<uintptr_t>(base) & 15) || strides[0] % 16 || strides[1] % 16) return false;
-    const cuuint64_t d[3] = {dims[0], dims[1], dims[2]};
-    const cuuint64_t st[2] = {strides[0], strides[1]};
-    const cuuint32_t bx[3] = {box[0], box[1], box[2]};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), d, st, bx, estr,
+    return encode;
+}
+
+static bool encode_map_f32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
+                           const uint64_t *strides, const uint32_t *box)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+    cuuint64_t d[5], st[4];
+    cuuint32_t bx[5], estr[5];
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        bx[i] = box[i];
+        estr[i] = 1;
+        if (i + 1 < rank) {
+            if (strides[i] % 16) return false;
+            st[i] = strides[i];
+        }
+    }
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void *>(base), d, st, bx, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_map3d_f32(CUtensorMap *map, const void *base, const uint64_t dims[3], const uint64_t strides[2],
+                      const uint32_t box[3])
+{
+    return encode_map_f32(map, base, 3, dims, strides, box);
+}
+
+bool encode_map5d_f32(CUtensorMap *map, const void *base, const uint64_t dims[5], const uint64_t strides[4],
+                      const uint32_t box[5])
+{
+    return encode_map_f32(map, base, 5, dims, strides, box);
 }
 
 size_t map_starlet_scratch_bytes(int n, int J, int batch, const fm_config &cfg)
@@ -923,7 +949,7 @@ int fm_tune(int knob, int64_t value)
         return FM_OK;
     case FM_TUNE_PDL: g_pdl.store(value < 0 ? 1 : (value != 0)); return FM_OK;
     case FM_TUNE_TMA:
-        if (value > 7) return einval("FM_TUNE_TMA is a mask of 1, 2 and 4");
+        if (value > 31) return einval("FM_TUNE_TMA is a mask of 1, 2, 4, 8 and 16");
         g_use_tma.store(value < 0 ? kDefaultTma : (int)value);
         return FM_OK;
     case FM_TUNE_TILE:

@@ -590,10 +590,15 @@ __global__ void __launch_bounds__(256) k_st_row(const T *__restrict__ c, long c_
 // window: KR + 4 row loads for KR outputs.  c_j = column-filtered r,
 // w_j = c_{j-1} - c_j, c_j written over c_{j-1} when they alias.
 // grid = (ceil(n / (128 VW)), s * ceil(n / (s KR)), batch).
+// tma (fp32, n a multiple of 512, 512 columns per CTA): bit 0 = the KR + 4
+// window rows of r arrive by one bulk tensor copy (mr: r as {256, n/256, s,
+// n/s, batch}, box {256, 2, 1, KR + 4, 1}), bit 1 = the KR rows of c_{j-1}
+// likewise (mp); row groups whose window leaves the map use plain loads.
 template <typename T, int KR>
 __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T *c_prev, long prev_bs, T *c_next,
                                                 long next_bs, T *__restrict__ w_out, long w_bs, int n, int s,
-                                                int boundary, int vec_ok)
+                                                int boundary, int vec_ok, const __grid_constant__ CUtensorMap mr,
+                                                const __grid_constant__ CUtensorMap mp, int tma)
 {
     pdl_entry();
     constexpr int VW = 16 / sizeof(T);
@@ -602,6 +607,48 @@ __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T
     const int r0 = blockIdx.y % s, m = blockIdx.y / s;
     const long b = blockIdx.z;
     const long nn = (long)n * n;
+    if constexpr (sizeof(T) == 4) {
+        const int mb = m * KR;
+        if (tma && mb >= 2 && r0 + s * (mb + KR + 1) < n) {
+            extern __shared__ __align__(16) unsigned char smem_raw[];
+            __shared__ uint64_t bar;
+            float *sr = align128<float>(smem_raw);  // [KR + 4][512] window rows
+            float *sp = sr + (KR + 4) * 512;        // [KR][512] rows of c_{j-1}
+            const int x0 = blockIdx.x * 512, xl = threadIdx.x * 4;
+            if (threadIdx.x == 0) mbar_init(&bar, 1);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                mbar_expect_tx(&bar, ((tma & 1) ? (KR + 4) * 2048u : 0u) + ((tma & 2) ? KR * 2048u : 0u));
+                if (tma & 1) tma_load_5d(sr, &mr, 0, x0 / 256, r0, mb - 2, (int)b, &bar);
+                if (tma & 2) tma_load_5d(sp, &mp, 0, x0 / 256, r0, mb, (int)b, &bar);
+            }
+            if (!tma_wait_all(&bar, 0)) return;  // the copies never completed (flagged)
+            const float *rb = reinterpret_cast<const float *>(r) + b * nn;
+            float4 win[5];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                win[u] = (tma & 1) ? f4(sr + u * 512 + xl) : f4(rb + (long)(r0 + s * (mb + u - 2)) * n + x);
+#pragma unroll
+            for (int k = 0; k < KR; ++k) {
+                const int y = r0 + s * (mb + k);
+                win[(k + 4) % 5] = (tma & 1) ? f4(sr + (k + 4) * 512 + xl) : f4(rb + (long)(y + 2 * s) * n + x);
+                const long px = (long)y * n + x;
+                const float4 p4 =
+                    (tma & 2) ? f4(sp + k * 512 + xl) : f4(reinterpret_cast<const float *>(c_prev) + b * prev_bs + px);
+                // the same arithmetic as the plain-load path below
+                const float4 &a = win[k % 5], &bq = win[(k + 1) % 5], &c = win[(k + 2) % 5],
+                             &d = win[(k + 3) % 5], &e = win[(k + 4) % 5];
+                alignas(16) float cj[4] = {B3<float>::apply(a.x, bq.x, c.x, d.x, e.x),
+                                           B3<float>::apply(a.y, bq.y, c.y, d.y, e.y),
+                                           B3<float>::apply(a.z, bq.z, c.z, d.z, e.z),
+                                           B3<float>::apply(a.w, bq.w, c.w, d.w, e.w)};
+                alignas(16) float w[4] = {p4.x - cj[0], p4.y - cj[1], p4.z - cj[2], p4.w - cj[3]};
+                emit_band<float>(w, reinterpret_cast<float *>(w_out) + b * w_bs, px, y, x, n, true);
+                if (c_next) emit_band<float>(cj, reinterpret_cast<float *>(c_next) + b * next_bs, px, y, x, n, true, true);
+            }
+            return;
+        }
+    }
     const bool vok = vec_ok && x + VW <= n;
     const T *rb = r + b * nn;
     auto load_row = [&](int yy, T (&d)[VW]) {
@@ -964,8 +1011,27 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
         FM_LAUNCH(FM_K_STARLET_ROW, k_st_row<T>, dim3(gxr, n, batch), rt, 0, s, c_prev, nn, Bb, n, sp, bnd,
                   vec_ok ? 1 : 0);
         const unsigned gy = (unsigned)(sp * ((((n + sp - 1) / sp) + KR - 1) / KR));
-        FM_LAUNCH(FM_K_STARLET_COL, (k_st_col<T, KR>), dim3(gx, gy, batch), 128, 0, s, Bb, c_prev, nn, c_next,
-                  next_bs, pyr + (long)(j - 1) * nn, pyr_bs, n, sp, bnd, vec_ok ? 1 : 0);
+        CUtensorMap mr, mp;
+        memset(&mr, 0, sizeof(mr));
+        memset(&mp, 0, sizeof(mp));
+        int tma = 0;
+        const int mask = g_use_tma.load(std::memory_order_relaxed);
+        // only for maps of 4096^2 and up, whose arrays do not stay in L2: there
+        // the copies cut 16 x 4096^2 (J = 9) from 11.75 to 11.40 ms, while on
+        // the L2-resident chunks of 1024^2 maps they cost 0.835 -> 0.849 ms
+        if (sizeof(T) == 4 && vec_ok && n >= 4096 && n % 512 == 0 && (mask & 24)) {
+            // r and c_{j-1} viewed as {256, n/256, sp, n/sp, batch}: a box picks
+            // 512 columns of rows r0 + sp (m0 .. m0 + rows - 1)
+            const uint64_t dims[5] = {256, (uint64_t)n / 256, (uint64_t)sp, (uint64_t)(n / sp), (uint64_t)batch};
+            const uint64_t str[4] = {1024, (uint64_t)n * 4, (uint64_t)sp * n * 4, (uint64_t)nn * 4};
+            const uint32_t box_r[5] = {256, 2, 1, KR + 4, 1}, box_p[5] = {256, 2, 1, KR, 1};
+            if ((mask & 8) && encode_map5d_f32(&mr, Bb, dims, str, box_r)) tma |= 1;
+            if ((mask & 16) && encode_map5d_f32(&mp, c_prev, dims, str, box_p)) tma |= 2;
+        }
+        const size_t csm = tma ? 128 + (size_t)(2 * KR + 4) * 512 * sizeof(float) : 0;
+        if (tma) FM_CUDA_TRY(fm::smem_attr((const void *)k_st_col<T, KR>, csm));
+        FM_LAUNCH(FM_K_STARLET_COL, (k_st_col<T, KR>), dim3(gx, gy, batch), 128, csm, s, Bb, c_prev, nn, c_next,
+                  next_bs, pyr + (long)(j - 1) * nn, pyr_bs, n, sp, bnd, vec_ok ? 1 : 0, mr, mp, tma);
     }
     return FM_OK;
 }

@@ -56,6 +56,16 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
+// box of a 5-D tensor map at (c0 .. c4) into shared memory (128-byte aligned)
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
 // every thread polls phase `parity` of bar; false (for the whole CTA) when
 // the bound ran out, after flagging it.  Every thread of the CTA must call it.
 __device__ __forceinline__ bool tma_wait_all(uint64_t *bar, uint32_t parity)
@@ -87,5 +97,8 @@ static inline int wait_error_flag(bool clear)
 // the layout (then the caller loads without it).
 bool encode_map3d_f32(CUtensorMap *map, const void *base, const uint64_t dims[3], const uint64_t strides[2],
                       const uint32_t box[3]);
+// the same for rank 5 (strides of dims 1..4)
+bool encode_map5d_f32(CUtensorMap *map, const void *base, const uint64_t dims[5], const uint64_t strides[4],
+                      const uint32_t box[5]);
 
 }  // namespace fm

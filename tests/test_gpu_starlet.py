@@ -123,14 +123,15 @@ def test_tile_kernel_variants(variant, n, J):
         fm.fm_tune(fm.FM_TUNE_TILE, -1)
 
 
-@pytest.mark.parametrize("n,J,batch", [(256, 5, 3), (1024, 7, 2), (200, 4, 1)])
+@pytest.mark.parametrize("n,J,batch", [(256, 5, 3), (1024, 7, 2), (200, 4, 1), (4096, 9, 1)])
 def test_bulk_copy_halo_equals_thread_loads(n, J, batch):
-    # interior tiles take their halo by one bulk tensor copy (default) or by
+    # interior tiles take their halo, and interior column-pass row groups
+    # their window and c_{j-1} rows, by bulk tensor copies (default) or by
     # per-thread loads: identical pyramids, no wait ran out
     fm = _fm()
     maps = np.stack([synth.grf_kappa(n, seed=7 + b) for b in range(batch)]).astype(np.float32)
     kap = torch.from_numpy(maps).cuda()
-    fm.fm_tune(fm.FM_TUNE_TMA, 1)
+    fm.fm_tune(fm.FM_TUNE_TMA, 31)
     with_tma = fm.fm_starlet_forward(kap, J)
     fm.fm_tune(fm.FM_TUNE_TMA, 0)
     try:
