@@ -38,10 +38,18 @@ void prof_after(int kid, cudaStream_t s);
 // finished (a no-op when launched without the attribute) and then lets the
 // next kernel's CTAs be scheduled into SMs this grid leaves idle in its tail.
 extern std::atomic<int> g_pdl;
+// fp32 fused-scale tile kernel: 0 = shared row-filtered buffer, 1 = register window
 extern std::atomic<int> g_tile_variant;
-extern std::atomic<int> g_use_tma;  // bulk tensor copies: 1 tile halo, 2 row FFT rows, 4 row IFFT rows
-int starlet_wait_error(bool clear);  // 1 if a kernel gave up waiting on a bulk copy (see fm_device_error)
-int fft_wait_error(bool clear);  // fp32 fused-scale tile kernel: 0 = smem row buffer, 1 = register window
+// bulk tensor copies (mask): 1 = starlet tile halo, 2 = row FFT input rows,
+// 4 = row IFFT input rows, 8 = large-scale column window rows, 16 = its
+// c_{j-1} rows (the last two on maps of 4096^2 and up)
+constexpr int kDefaultTma = 31;
+extern std::atomic<int> g_use_tma;
+extern std::atomic<int> g_prof_kid;  // kernel id whose launches are being timed (0: none)
+// 1 if a kernel of that file gave up waiting on a bulk copy (see fm_device_error)
+int starlet_wait_error(bool clear);
+int fft_wait_error(bool clear);
+int einval(const std::string &msg);  // records msg as the last error, returns FM_EINVAL
 __device__ __forceinline__ void pdl_entry()
 {
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
@@ -173,6 +181,13 @@ int launch_fft32(const float *in1, const float *in2, long in_bs, float *out1, fl
 size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg);
 int launch_map_direct(const void *g1, const void *g2, const void *weight, long w_bs, void *map, void *coverage, int n,
                       int batch, int filter, double theta, int ell, double cut, int precision, cudaStream_t s);
+// batched pipeline (pipeline.cu)
+int map_starlet_run(const void *g1, const void *g2, void *pyramid, int n, int J, int batch, const fm_config &cfg,
+                    cudaStream_t s);
+int map_starlet_host_run(const char *g1h, const char *g2h, char *pyrh, int n, int J, int batch, const fm_config &cfg,
+                         cudaStream_t origin);
+size_t noise_scratch_bytes(int n, int J, int R, const fm_config &cfg, bool with_snr);
+size_t map_starlet_scratch_bytes(int n, int J, int batch, const fm_config &cfg);
 int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
                   const fm_config &cfg, cudaStream_t s, bool allow_graph);
 int launch_modulus2(const void *a, long a_bs, const void *b, long b_bs, void *out, long nn, int count, int precision,

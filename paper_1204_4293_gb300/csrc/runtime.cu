@@ -1,0 +1,287 @@
+// runtime.cu -- shared services of libfastmap: the calling thread's last
+// error, launch counting and the per-kernel profiling hooks, per-device
+// twiddle tables, stream-ordered scratch, dynamic shared-memory attributes,
+// the driver's tensor-map encoder (TMA), and the diagnostic C entry points.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+#include "tma.cuh"
+
+namespace fm {
+
+// ---- errors -----------------------------------------------------------------
+static thread_local std::string t_last_error;
+
+void set_error(const std::string &msg) { t_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // allocation failures are not sticky; clear them
+        return FM_ENOMEM;
+    }
+    return FM_ECUDA;
+}
+
+int einval(const std::string &msg)
+{
+    set_error(msg);
+    return FM_EINVAL;
+}
+
+// ---- launch accounting and profiling ------------------------------------------
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_pdl{1};
+std::atomic<int> g_tile_variant{1};
+std::atomic<int> g_use_tma{kDefaultTma};
+
+namespace {
+struct Prof {
+    std::mutex mu;
+    int kid = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pairs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t pending = nullptr;
+    cudaEvent_t get()
+    {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+Prof g_prof;
+}  // namespace
+std::atomic<int> g_prof_kid{0};
+
+void prof_before(int kid, cudaStream_t s)
+{
+    if (kid == 0 || g_prof_kid.load(std::memory_order_relaxed) != kid) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    g_prof.pending = g_prof.get();
+    cudaEventRecord(g_prof.pending, s);
+}
+
+void prof_after(int kid, cudaStream_t s)
+{
+    if (kid == 0 || g_prof_kid.load(std::memory_order_relaxed) != kid) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (!g_prof.pending) return;
+    cudaEvent_t e = g_prof.get();
+    cudaEventRecord(e, s);
+    g_prof.pairs.emplace_back(g_prof.pending, e);
+    g_prof.pending = nullptr;
+}
+
+// ---- twiddle tables ------------------------------------------------------------
+namespace {
+std::mutex g_tw_mu;
+std::unordered_map<uint64_t, void *> g_tw;  // key: device, precision, n
+}  // namespace
+
+const void *twiddles(int n, int precision, cudaStream_t s, int *status)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        *status = cuda_fail(e, "cudaGetDevice");
+        return nullptr;
+    }
+    const uint64_t key = ((uint64_t)dev << 40) | ((uint64_t)precision << 32) | (uint64_t)n;
+    std::lock_guard<std::mutex> lk(g_tw_mu);
+    auto it = g_tw.find(key);
+    if (it != g_tw.end()) return it->second;
+    // exp(-2 pi i t / n) in FP64 on the host, rounded once to the element type
+    const size_t esz = precision == FM_F64 ? 16 : 8;
+    std::vector<unsigned char> host((size_t)n * esz);
+    for (int t = 0; t < n; ++t) {
+        const double ang = -2.0 * M_PI * (double)t / (double)n;
+        const double c = cos(ang), sn = sin(ang);
+        if (precision == FM_F64) {
+            double v[2] = {c, sn};
+            memcpy(&host[(size_t)t * esz], v, esz);
+        } else {
+            float v[2] = {(float)c, (float)sn};
+            memcpy(&host[(size_t)t * esz], v, esz);
+        }
+    }
+    void *d = nullptr;
+    e = cudaMalloc(&d, host.size());
+    if (e == cudaSuccess) e = cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (d) cudaFree(d);
+        *status = cuda_fail(e, "twiddle table");
+        return nullptr;
+    }
+    (void)s;
+    g_tw[key] = d;
+    return d;
+}
+
+// ---- kernel attributes -------------------------------------------------------------
+namespace {
+std::mutex g_attr_mu;
+std::unordered_map<uint64_t, size_t> g_attr;  // (device, kernel) -> smem bytes set
+}  // namespace
+
+cudaError_t smem_attr(const void *kernel, size_t bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t key = ((uint64_t)(uintptr_t)kernel) ^ ((uint64_t)dev << 56);
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto it = g_attr.find(key);
+    if (it != g_attr.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) g_attr[key] = bytes;
+    return e;
+}
+
+// ---- scratch -------------------------------------------------------------------
+int scratch_alloc(Scratch &sc, size_t bytes, cudaStream_t s)
+{
+    sc.s = s;
+    if (bytes == 0) return FM_OK;
+    static std::once_flag pool_once;
+    std::call_once(pool_once, [] {
+        // keep freed stream-ordered memory in the pool instead of returning it
+        // to the driver after every call (a setting of this process only)
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+    cudaError_t e = cudaMallocAsync(&sc.p, bytes, s);
+    if (e != cudaSuccess) {
+        sc.p = nullptr;
+        return cuda_fail(e, "cudaMallocAsync (scratch)");
+    }
+    return FM_OK;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }();
+    return encode;
+}
+
+static bool encode_map_f32(CUtensorMap *map, const void *base, int rank, const uint64_t *dims,
+                           const uint64_t *strides, const uint32_t *box)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+    cuuint64_t d[5], st[4];
+    cuuint32_t bx[5], estr[5];
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        bx[i] = box[i];
+        estr[i] = 1;
+        if (i + 1 < rank) {
+            if (strides[i] % 16) return false;
+            st[i] = strides[i];
+        }
+    }
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void *>(base), d, st, bx, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_map3d_f32(CUtensorMap *map, const void *base, const uint64_t dims[3], const uint64_t strides[2],
+                      const uint32_t box[3])
+{
+    return encode_map_f32(map, base, 3, dims, strides, box);
+}
+
+bool encode_map5d_f32(CUtensorMap *map, const void *base, const uint64_t dims[5], const uint64_t strides[4],
+                      const uint32_t box[5])
+{
+    return encode_map_f32(map, base, 5, dims, strides, box);
+}
+
+}  // namespace fm
+
+using namespace fm;
+
+extern "C" {
+
+const char *fm_status_string(int status)
+{
+    switch (status) {
+    case FM_OK: return "ok";
+    case FM_PENDING: return "pending";
+    case FM_EINVAL: return "invalid argument";
+    case FM_ENOMEM: return "out of device memory";
+    case FM_EBUDGET: return "request exceeds the memory budget";
+    case FM_ETIMEOUT: return "timed out";
+    case FM_ECUDA: return "CUDA error";
+    case FM_ENOTFOUND: return "unknown ticket";
+    case FM_EBUSY: return "queue full";
+    }
+    return "unknown status";
+}
+
+const char *fm_last_error(void) { return t_last_error.c_str(); }
+
+int64_t fm_launch_count(void) { return g_launches.load(); }
+
+int fm_profile_select(int kid)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    for (auto &p : g_prof.pairs) {
+        g_prof.pool.push_back(p.first);
+        g_prof.pool.push_back(p.second);
+    }
+    g_prof.pairs.clear();
+    g_prof.pending = nullptr;
+    g_prof_kid.store(kid);
+    return FM_OK;
+}
+
+int fm_device_error(void)
+{
+    const int a = starlet_wait_error(true), b = fft_wait_error(true);
+    if (a < 0 || b < 0) return einval("fm_device_error: no device");
+    return a | b;
+}
+
+int fm_profile_read(double *total_ms, int64_t *launches)
+{
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    double tot = 0;
+    for (auto &p : g_prof.pairs) {
+        cudaError_t e = cudaEventSynchronize(p.second);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float ms = 0;
+        e = cudaEventElapsedTime(&ms, p.first, p.second);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = (int64_t)g_prof.pairs.size();
+    return FM_OK;
+}
+
+}  // extern "C"

@@ -21,11 +21,6 @@
 
 namespace fm {
 
-size_t map_starlet_scratch_bytes(int n, int J, int batch, const fm_config &cfg);
-size_t noise_scratch_bytes(int n, int J, int R, const fm_config &cfg, bool with_snr);
-int map_starlet_run(const void *g1, const void *g2, void *pyramid, int n, int J, int batch, const fm_config &cfg,
-                    cudaStream_t s);
-
 static int64_t now_ns()
 {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
