@@ -402,6 +402,52 @@ def serving_leg(fm, torch, seed=5, nreq=48, lam=200.0, budget_gb=64, slots=8, lo
     # the contract's flat keys: the saturated trace
     out.update({k: out["saturated"][k] for k in ("offered_req_per_s", "achieved_req_per_s", "p50_ms", "p99_ms",
                                                   "mpix_scales_per_s")})
+    # plain-FP64 estimate of the same trace: each distinct (side, R) class timed
+    # once in the plain form (one map, FP64, one starlet scale per pass; the
+    # noise pass at R = 20, scaled to the class's R) and summed over the
+    # trace as one request after another
+    classes = {}
+    for side, R in zip(sides, Rs):
+        classes[(int(side), int(R))] = classes.get((int(side), int(R)), 0) + 1
+    total_s = 0.0
+    for (side, R), count in classes.items():
+        J = int(np.log2(side)) - 2
+        g = (0.1 * torch.randn(2, side, side, device="cuda", dtype=torch.float64)).contiguous()
+        pyr = torch.empty(J, side, side, dtype=torch.float64, device="cuda")
+        ms = cuda_time(torch, lambda: fm.fm_map_starlet(g[0], g[1], J, fuse_depth=-1, out=pyr), 2)
+        if R:
+            rs = min(R, 20)
+            ms += cuda_time(torch, lambda: fm.fm_map_noise(g[0], g[1], J, rs, seed=7, fuse_depth=-1,
+                                                           with_snr=False), 1) * (R / rs)
+        total_s += count * ms / 1e3
+        del g, pyr
+    torch.cuda.empty_cache()
+    out["plain_fp64_estimate"] = {"trace_s": total_s, "achieved_req_per_s": nreq / total_s,
+                                  "sample": "each (side, R) class once; noise at R = 20 scaled to R"}
+    return out
+
+
+def cpu_oracle_configs():
+    """The oracle on the other configurations, one process, reported only:
+    noise maps at 1024^2, J = 7 with R = 20 (scaled to R = 1000) and one
+    4096^2, J = 9 map of KS + starlet."""
+    import oracle
+    from paper_1204_4293_gb300 import synth
+    oracle.build()
+    out = {}
+    g1, g2 = oracle.ks_forward(synth.grf_kappa(1024, seed=3))
+    t0 = time.perf_counter()
+    oracle.map_noise(g1, g2, 7, 20, seed=3, with_snr=False)
+    dt = time.perf_counter() - t0
+    out["noise_1024_R1000_s"] = dt * 1000 / 20
+    out["noise_sample"] = f"R = 20 in {dt:.1f} s, one thread, scaled linearly to R = 1000"
+    g1, g2 = oracle.ks_forward(synth.grf_kappa(4096, alpha=2.5, seed=40))
+    t0 = time.perf_counter()
+    oracle.map_starlet(g1, g2, 9)
+    dt = time.perf_counter() - t0
+    out["map_4096_J9_s"] = dt
+    out["map_4096_value"] = 4096 * 4096 * 9 / dt / 1e6
+    out["unit"] = UNIT
     return out
 
 
@@ -543,6 +589,8 @@ def main():
             line["batched_fp32_over_plain_fp64"] = value / extras["plain_fp64"]["value"]
         if not args.no_cpu and world == 1:
             line["cpu_baseline"] = cpu_oracle_baseline(n, J)
+            if not args.no_side:
+                line["cpu_oracle_other_configs"] = cpu_oracle_configs()
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
