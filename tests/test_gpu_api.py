@@ -88,3 +88,51 @@ def test_serving_rejects_over_budget():
     with fm.Server(mem_budget_bytes=1 << 20, max_slots=2) as sv:
         res = sv.wait(sv.submit(g1, g1, 7, pyr), 30.0)
     assert res.status == fm.FM_EBUDGET
+
+
+def test_graph_cache_eviction_and_trim_keep_results():
+    # more batched calls with distinct keys than the cache keeps (LRU
+    # eviction), then fm_trim and a replay: every result equals the eager one
+    from paper_1204_4293_gb300 import fastmap as fm
+    n, J = 256, 5
+    per_map = n * n * 4 * 5
+    fm.fm_tune(fm.FM_TUNE_CHUNK_BYTES, 2 * per_map)  # chunks of 2 maps: every call below is multi-chunk
+    try:
+        calls = []
+        for batch in (3, 4, 5, 6, 7, 8):
+            g1 = torch.empty((batch, n, n), device="cuda").normal_(0, 0.1)
+            g2 = torch.empty_like(g1).normal_(0, 0.1)
+            calls.append((g1, g2))
+        fm.fm_tune(fm.FM_TUNE_GRAPHS, 0)
+        eager = [fm.fm_map_starlet(g1, g2, J) for g1, g2 in calls]
+        fm.fm_tune(fm.FM_TUNE_GRAPHS, 1)
+        for _ in range(2):  # record (evicting), then replay what is left
+            for (g1, g2), ref in zip(calls, eager):
+                assert torch.equal(fm.fm_map_starlet(g1, g2, J), ref)
+        fm.fm_trim()
+        g1, g2 = calls[0]
+        assert torch.equal(fm.fm_map_starlet(g1, g2, J), eager[0])
+    finally:
+        for knob in (fm.FM_TUNE_CHUNK_BYTES, fm.FM_TUNE_GRAPHS):
+            fm.fm_tune(knob, -1)
+        fm.fm_trim()
+
+
+def test_noise_graph_cache_eviction():
+    # three noise calls with distinct keys (the cache keeps two) recorded and
+    # replayed; each equals the eager call on the same inputs
+    from paper_1204_4293_gb300 import fastmap as fm
+    n, J = 128, 4
+    g1 = torch.empty((n, n), device="cuda").normal_(0, 0.1)
+    g2 = torch.empty_like(g1).normal_(0, 0.1)
+    keys = [(10, 1), (12, 2), (10, 3)]
+    fm.fm_tune(fm.FM_TUNE_GRAPHS, 0)
+    try:
+        eager = [fm.fm_map_noise(g1, g2, J, R, seed=s) for R, s in keys]
+    finally:
+        fm.fm_tune(fm.FM_TUNE_GRAPHS, -1)
+    for _ in range(2):
+        for (R, s), (v_ref, snr_ref) in zip(keys, eager):
+            v, snr = fm.fm_map_noise(g1, g2, J, R, seed=s)
+            assert torch.equal(v, v_ref) and torch.equal(snr, snr_ref)
+    fm.fm_trim()
