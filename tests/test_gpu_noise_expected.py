@@ -100,3 +100,23 @@ def test_mirror_boundary_is_refused():
     var = torch.empty((3, 64, 64), device="cuda")
     st = fm.lib.fm_map_noise_expected(fm._ptr(g), fm._ptr(g), fm._ptr(var), 64, 4, fm.ctypes.byref(c), None)
     assert st == fm.FM_EINVAL
+
+
+def test_noise_maps_at_the_benchmark_size_match_the_expectation():
+    # the noise configuration the benchmark times (1024^2, J = 7, R = 1000, one
+    # CUDA-graph launch), periodic boundary: the Monte-Carlo variance scatters
+    # around the exact expectation (itself checked against the oracle at
+    # sampled 1024^2 pixels above) with the spread of a sample variance
+    fm = _fm()
+    n, J, R = 1024, 7, 1000
+    g1, g2 = _shear(n, 5, np.float32)
+    t1, t2 = torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda()
+    exp = fm.fm_map_noise_expected(t1, t2, J).double()
+    var, snr = fm.fm_map_noise(t1, t2, J, R, seed=9, boundary=fm.FM_PERIODIC)
+    assert fm.fm_device_error() == 0
+    sd = np.sqrt(2.0 / (R - 1))
+    for j in range(J - 1):
+        ratio = (var[j] / exp[j]).cpu().numpy()
+        assert abs(ratio.mean() - 1.0) < 0.5 * sd, (j, ratio.mean())
+        assert 0.8 * sd < ratio.std() < 1.2 * sd, (j, ratio.std())
+    assert torch.isfinite(snr).all()

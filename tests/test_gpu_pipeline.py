@@ -30,10 +30,11 @@ def test_map_starlet_matches_oracle(n, J, batch, dtype):
 
 
 def test_map_starlet_paper_size_batched():
-    # the benchmark's workload: a batch of 1024^2 fp32 shear maps, J = 7;
-    # the oracle checks the first and the last map of the batch in full.
+    # the benchmark's workload and launch configuration: 32 1024^2 fp32 shear
+    # maps, J = 7, in L2-sized chunks on two streams, recorded into a CUDA
+    # graph and replayed; the oracle checks the first and the last map in full
     fm = _fm()
-    n, J, batch = 1024, 7, 8
+    n, J, batch = 1024, 7, 32
     maps = [shear(n, seed=2 + b, dtype=np.float32) for b in (0, batch - 1)]
     g1 = torch.empty((batch, n, n), dtype=torch.float32, device="cuda")
     g2 = torch.empty_like(g1)
@@ -41,7 +42,9 @@ def test_map_starlet_paper_size_batched():
     g2.normal_(0, 0.1)
     g1[0], g2[0] = torch.from_numpy(maps[0][0]), torch.from_numpy(maps[0][1])
     g1[-1], g2[-1] = torch.from_numpy(maps[1][0]), torch.from_numpy(maps[1][1])
-    pyr = fm.fm_map_starlet(g1, g2, J)
+    pyr = fm.fm_map_starlet(g1, g2, J)  # records the graph
+    pyr = fm.fm_map_starlet(g1, g2, J, out=torch.full_like(pyr, float("nan")))  # replays it
+    assert fm.fm_device_error() == 0
     for idx, m in ((0, maps[0]), (batch - 1, maps[1])):
         ref = oracle.map_starlet(m[0].astype(np.float64), m[1].astype(np.float64), J)
         errs = band_errs(pyr[idx].cpu().numpy(), ref)
