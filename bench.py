@@ -35,10 +35,7 @@ METRIC = "starlet Map Mpix*scales/s, batched FP32 vs plain FP64 (<=1e-5 err); %H
 UNIT = "Mpix*scales/s"
 L2_BYTES = 129 * 2 ** 20
 
-FUSE = 3  # starlet scales done by the fused tile kernel (library default)
-
-
-def algo_bytes_per_px_step(kernel, J, fuse=FUSE):
+def algo_bytes_per_px_step(kernel, J, fuse):
     """Algorithmic bytes per map pixel that one step moves through `kernel`
     (fp32): what the kernel must read and write once.  FFT passes move
     complex maps; the KS row passes the real shear / convergence; the tile
@@ -556,7 +553,8 @@ def main():
     if rank == 0:
         peak, peak_src = load_peaks()
         px_step = n * n * B
-        bytes_step = algo_bytes_per_px_step(dom, J) * px_step
+        fuse = fm.fm_starlet_fuse_depth(n, J)  # the library's automatic choice for this size
+        bytes_step = algo_bytes_per_px_step(dom, J, fuse) * px_step
         achieved = bytes_step / (dom_ms * 1e-3) / 1e9
         dom_avg_ms = dom_ms / max(dom_cnt, 1)
         bytes_launch = bytes_step / max(dom_cnt, 1)
@@ -574,7 +572,7 @@ def main():
                          "frac": achieved / peak, "peak_source": f"hbm_gbs ({peak_src})",
                          "traffic": trf * bytes_launch if trf else None,
                          "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": dom_avg_ms,
-                         "launches_per_step": dom_cnt, "timing": "CUDA events around every launch of the "
+                         "launches_per_step": dom_cnt, "fused_scales": fuse, "timing": "CUDA events around every launch of the "
                          "kernel on its launch stream; the same steps launched eagerly with the chunks on "
                          "one stream (graph bypassed, no kernel overlap)"},
             "kernel_breakdown_ms_per_step": {k: v[0] for k, v in per_kind.items()},

@@ -74,8 +74,10 @@ typedef struct {
     int boundary;   /* starlet boundary: FM_MIRROR (0) or FM_PERIODIC (1) */
     int accum;      /* noise accumulators: 0 = FP64 (the only mode) */
     int fuse_depth; /* starlet scales done by the fused 2-D tile kernel:
-                       0 = automatic, k > 0 = scales 1..k, -1 = none (the
-                       plain one-scale-per-pass form) */
+                       0 = automatic (2 for fp32 maps of 1024^2 to 2048^2,
+                       else 3; see fm_starlet_fuse_depth), k > 0 = scales
+                       1..k (at most 4 in fp32, 3 in fp64, J - 1), -1 = none
+                       (the plain one-scale-per-pass form) */
     int large_path; /* scales after the fused ones: 0 = automatic, 1 = one row
                        pass + one column pass per scale, 2 = all large scales
                        in one row kernel + one column-strip kernel */
@@ -100,6 +102,12 @@ int fm_ks_forward(const void *kappa, void *g1, void *g2, int n, int batch, const
  * overlap.  Scratch: up to 2*batch*n*n elements. */
 int fm_starlet_forward(const void *kappa, void *pyramid, int n, int J, int batch, const fm_config *cfg,
                        void *stream);
+
+/* Number of scales the fused tile kernel computes for fm_starlet_forward /
+ * fm_map_starlet with these n, J and cfg (0 = none); the remaining
+ * J - 1 - depth scales take one row and one column pass each.  Host only;
+ * FM_EINVAL on a bad n, J or cfg. */
+int fm_starlet_fuse_depth(int n, int J, const fm_config *cfg);
 
 /* KS inversion then the starlet of kappa_E: the aperture-mass maps of every
  * band from shear in one call (the paper's fast method end to end). */

@@ -101,6 +101,15 @@ int fm_starlet_forward(const void *kappa, void *pyramid, int n, int J, int batch
     return launch_starlet(kappa, pyramid, (long)J * n * n, n, J, batch, cfg, sc.p, s);
 }
 
+int fm_starlet_fuse_depth(int n, int J, const fm_config *cfgp)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if (n < 1) return einval("n must be >= 1");
+    if ((st = check_J(n, J))) return st;
+    return starlet_fuse_depth(n, J, cfg);
+}
 
 int fm_map_starlet(const void *g1, const void *g2, void *pyramid, int n, int J, int batch, const fm_config *cfgp,
                    void *stream)

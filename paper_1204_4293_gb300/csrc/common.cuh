@@ -179,6 +179,7 @@ int launch_fft32(const float *in1, const float *in2, long in_bs, float *out1, fl
                  int batch, int op, const float2 *filt, float out_scale, uint64_t seed, int r0, bool rotate,
                  const float2 *tw, cudaStream_t s);
 size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg);
+int starlet_fuse_depth(int n, int J, const fm_config &cfg);  // scales of the fused tile kernel
 int launch_map_direct(const void *g1, const void *g2, const void *weight, long w_bs, void *map, void *coverage, int n,
                       int batch, int filter, double theta, int ell, double cut, int precision, cudaStream_t s);
 // batched pipeline (pipeline.cu)

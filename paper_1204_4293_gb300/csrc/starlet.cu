@@ -834,12 +834,18 @@ __global__ void __launch_bounds__(512) k_st_cols_multi(const T *__restrict__ c_a
 }
 
 // ---------------------------------------------------------------------------
-// Scales handled by the fused tile kernel: 3 by default; never more than
-// fit a 32 x 32 tile with its halo (two buffers) in 200 KB of shared memory.
-static int auto_fuse(int J, const fm_config &cfg)
+// Scales handled by the fused tile kernel; never more than fit a tile with
+// its halo (two buffers) in shared memory.  Automatic choice, measured on
+// GB300 (fp32 KS + starlet, ms per batch, fusing 1 / 2 / 3 scales):
+// 128 x 256^2 J = 6 0.281 / 0.253 / 0.228, 64 x 512^2 J = 7 0.489 / 0.451
+// / 0.446, 32 x 1024^2 J = 7 0.898 / 0.812 / 0.837, 16 x 2048^2 J = 8
+// 2.216 / 2.051 / 2.151:
+// two scales for 1024^2 and 2048^2 maps, whose chunked large-scale passes
+// run from L2, else three.
+static int auto_fuse(int n, int J, const fm_config &cfg)
 {
     if (cfg.fuse_depth < 0) return 0;
-    int f = cfg.fuse_depth == 0 ? 3 : cfg.fuse_depth;
+    int f = cfg.fuse_depth != 0 ? cfg.fuse_depth : (cfg.precision == FM_F32 && n >= 1024 && n <= 2048 ? 2 : 3);
     const int fmax = cfg.precision == FM_F64 ? 3 : 4;  // tile + halo must fit shared memory
     if (f > fmax) f = fmax;
     if (f > J - 1) f = J - 1;
@@ -858,9 +864,11 @@ static int cols_multi_width(int n, size_t es)
     return w;
 }
 
+int starlet_fuse_depth(int n, int J, const fm_config &cfg) { return auto_fuse(n, J, cfg); }
+
 size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg)
 {
-    const int f = auto_fuse(J, cfg);
+    const int f = auto_fuse(n, J, cfg);
     if (f >= J - 1) return 0;
     const size_t es = cfg.precision == FM_F64 ? 8 : 4;
     const size_t per = (size_t)batch * n * n;
@@ -955,7 +963,7 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
     constexpr int VW = 16 / sizeof(T);
     constexpr int KR = 8;
     const long nn = (long)n * n;
-    const int f = auto_fuse(J, cfg);
+    const int f = auto_fuse(n, J, cfg);
     const int bnd = cfg.boundary;
     T *A = scratch;
     T *Bb = scratch ? scratch + (long)batch * nn : nullptr;

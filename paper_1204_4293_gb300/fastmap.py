@@ -55,6 +55,7 @@ _SIGS = {
     "fm_ks_forward": (_I, [_P, _P, _P, _I, _I, _CFG, _P]),
     "fm_ks_invert_noalloc": (_I, [_P, _P, _P, _P, _I, _I, _CFG, _P]),
     "fm_starlet_forward": (_I, [_P, _P, _I, _I, _I, _CFG, _P]),
+    "fm_starlet_fuse_depth": (_I, [_I, _I, _CFG]),
     "fm_map_starlet": (_I, [_P, _P, _P, _I, _I, _I, _CFG, _P]),
     "fm_map_starlet_host": (_I, [_P, _P, _P, _I, _I, _I, _CFG, _P]),
     "fm_map_direct": (_I, [_P, _P, _P, _I, _I, _D, _I, _D, _CFG, _P]),
@@ -177,6 +178,12 @@ def fm_starlet_forward(kappa, J, boundary=FM_MIRROR, fuse_depth=0, out=None, str
     _check(_lib.fm_starlet_forward(_ptr(kappa), _ptr(pyr), n, J, batch, ctypes.byref(c), _stream(stream)),
            "fm_starlet_forward")
     return pyr
+
+
+def fm_starlet_fuse_depth(n, J, precision=FM_F32, boundary=FM_MIRROR, fuse_depth=0, large_path=0) -> int:
+    """Scales the fused tile kernel computes for an n x n map, J scales (host only)."""
+    c = _cfg(precision, boundary, fuse_depth, large_path)
+    return _check(_lib.fm_starlet_fuse_depth(int(n), int(J), ctypes.byref(c)), "fm_starlet_fuse_depth")
 
 
 def fm_map_starlet(g1, g2, J, boundary=FM_MIRROR, fuse_depth=0, out=None, stream=None, large_path=0):
