@@ -35,21 +35,21 @@ METRIC = "starlet Map Mpix*scales/s, batched FP32 vs plain FP64 (<=1e-5 err); %H
 UNIT = "Mpix*scales/s"
 L2_BYTES = 129 * 2 ** 20
 
-def algo_bytes_per_px_step(kernel, J, fuse):
-    """Algorithmic bytes per map pixel that one step moves through `kernel`
+def algo_bytes_per_px_launch(kernel, fuse):
+    """Algorithmic bytes per map pixel that one launch of `kernel` moves
     (fp32): what the kernel must read and write once.  FFT passes move
     complex maps; the KS row passes the real shear / convergence; the tile
-    kernel reads kappa and writes f bands + c_f; each of the K = J-1-f large
-    scales has a row pass (read c, write r) and a column pass (read r and c,
-    write c and w_j)."""
-    K = J - 1 - fuse
+    kernel reads kappa and writes `fuse` bands + c_fuse; a large scale's row
+    pass reads c and writes r; its column pass reads r and c and writes c
+    and w_j; the fused column + next-row kernel also writes the next r."""
     return {
         "fft_rows_fwd": 8 + 8,
         "fft_cols_ks": 8 + 8,
         "fft_rows_inv": 8 + 4,
         "starlet_tile": 4 + 4 * fuse + 4,
-        "starlet_row": K * (4 + 4),
-        "starlet_col": K * (4 + 4 + 4 + 4),
+        "starlet_row": 4 + 4,
+        "starlet_col": 4 + 4 + 4 + 4,
+        "starlet_colrow": 4 + 4 + 4 + 4 + 4,
     }[kernel]
 
 
@@ -509,7 +509,8 @@ def main():
     # kernel is selected), with the chunks on one stream so kernels do not
     # overlap and each launch's time is its own; the dominant kind gets the
     # roofline
-    kinds = ["fft_rows_fwd", "fft_cols_ks", "fft_rows_inv", "starlet_tile", "starlet_row", "starlet_col"]
+    kinds = ["fft_rows_fwd", "fft_cols_ks", "fft_rows_inv", "starlet_tile", "starlet_row", "starlet_col",
+             "starlet_colrow"]
     per_kind = {}
     prof_steps = max(3, min(args.steps, 20))
     fm.fm_tune(fm.FM_TUNE_CHUNK_STREAMS, 1)
@@ -518,7 +519,8 @@ def main():
         for _ in range(prof_steps):
             step()
         ms, cnt = fm.fm_profile_read()
-        per_kind[k] = (ms / prof_steps, cnt / prof_steps)
+        if cnt:
+            per_kind[k] = (ms / prof_steps, cnt / prof_steps)
     fm.fm_profile_select(0)
     fm.fm_tune(fm.FM_TUNE_CHUNK_STREAMS, -1)
     dom = max(per_kind, key=lambda k: per_kind[k][0])
@@ -554,10 +556,10 @@ def main():
         peak, peak_src = load_peaks()
         px_step = n * n * B
         fuse = fm.fm_starlet_fuse_depth(n, J)  # the library's automatic choice for this size
-        bytes_step = algo_bytes_per_px_step(dom, J, fuse) * px_step
-        achieved = bytes_step / (dom_ms * 1e-3) / 1e9
+        chunks = per_kind["fft_rows_fwd"][1]  # one row-FFT launch per chunk of maps
+        bytes_launch = algo_bytes_per_px_launch(dom, fuse) * px_step / chunks
+        achieved = bytes_launch * dom_cnt / (dom_ms * 1e-3) / 1e9
         dom_avg_ms = dom_ms / max(dom_cnt, 1)
-        bytes_launch = bytes_step / max(dom_cnt, 1)
         trf = ncu_traffic(dom)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

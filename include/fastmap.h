@@ -78,9 +78,14 @@ typedef struct {
                        else 3; see fm_starlet_fuse_depth), k > 0 = scales
                        1..k (at most 4 in fp32, 3 in fp64, J - 1), -1 = none
                        (the plain one-scale-per-pass form) */
-    int large_path; /* scales after the fused ones: 0 = automatic, 1 = one row
-                       pass + one column pass per scale, 2 = all large scales
-                       in one row kernel + one column-strip kernel */
+    int large_path; /* scales after the fused ones: 0 = automatic (3 after
+                       fused small scales on maps up to 256^2, else 1),
+                       1 = one row pass + one column pass per scale, 2 = all
+                       large scales in one row kernel + one column-strip
+                       kernel, 3 = the column pass of each scale fused with
+                       the row pass of the next (one row pass, then one
+                       kernel per scale; the pyramid's smooth-array slot
+                       serves as scratch until its final write) */
 } fm_config;
 
 /* ---- Kaiser-Squires (Sec. 4.5) ---------------------------------------------
@@ -290,6 +295,7 @@ int fm_trim(void);
 #define FM_K_MAP_DIRECT 7
 #define FM_K_NOISE_FINAL 8
 #define FM_K_NOISE_ACCUM 9
+#define FM_K_STARLET_COLROW 10 /* a large scale's column pass + the next scale's row pass */
 
 /* Bracket every later launch of kernel `kid` (0 = none) with CUDA events on
  * its launch stream; fm_profile_read synchronises those events and returns

@@ -546,8 +546,8 @@ __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3)
 // One large scale, rows: r = rows-filtered c (taps +-s, +-2s), VW pixels per
 // thread.  grid = (ceil(n / (blockDim.x VW)), n, batch).
 template <typename T>
-__global__ void __launch_bounds__(256) k_st_row(const T *__restrict__ c, long c_bs, T *__restrict__ r, int n, int s,
-                                                int boundary, int vec_ok)
+__global__ void __launch_bounds__(256) k_st_row(const T *__restrict__ c, long c_bs, T *__restrict__ r, long r_bs,
+                                                int n, int s, int boundary, int vec_ok)
 {
     pdl_entry();
     constexpr int VW = 16 / sizeof(T);
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(256) k_st_row(const T *__restrict__ c, long c_
     const int y = blockIdx.y;
     const long b = blockIdx.z;
     const T *row = c + b * c_bs + (long)y * n;
-    T *dst = r + (b * n + y) * (long)n;
+    T *dst = r + b * r_bs + (long)y * n;
     alignas(16) T o[VW];
     if (vec_ok && s % VW == 0 && x - 2 * s >= 0 && x + VW + 2 * s <= n) {
         alignas(16) T m2[VW]; alignas(16) T m1[VW]; alignas(16) T c0[VW]; alignas(16) T p1[VW]; alignas(16) T p2[VW];
@@ -595,9 +595,10 @@ __global__ void __launch_bounds__(256) k_st_row(const T *__restrict__ c, long c_
 // n/s, batch}, box {256, 2, 1, KR + 4, 1}), bit 1 = the KR rows of c_{j-1}
 // likewise (mp); row groups whose window leaves the map use plain loads.
 template <typename T, int KR>
-__global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T *c_prev, long prev_bs, T *c_next,
-                                                long next_bs, T *__restrict__ w_out, long w_bs, int n, int s,
-                                                int boundary, int vec_ok, const __grid_constant__ CUtensorMap mr,
+__global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, long r_bs, const T *c_prev, long prev_bs,
+                                                T *c_next, long next_bs, T *__restrict__ w_out, long w_bs, int n,
+                                                int s, int boundary, int vec_ok,
+                                                const __grid_constant__ CUtensorMap mr,
                                                 const __grid_constant__ CUtensorMap mp, int tma)
 {
     pdl_entry();
@@ -606,7 +607,6 @@ __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T
     if (x >= n) return;
     const int r0 = blockIdx.y % s, m = blockIdx.y / s;
     const long b = blockIdx.z;
-    const long nn = (long)n * n;
     if constexpr (sizeof(T) == 4) {
         const int mb = m * KR;
         if (tma && mb >= 2 && r0 + s * (mb + KR + 1) < n) {
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T
                 if (tma & 2) tma_load_5d(sp, &mp, 0, x0 / 256, r0, mb, (int)b, &bar);
             }
             if (!tma_wait_all(&bar, 0)) return;  // the copies never completed (flagged)
-            const float *rb = reinterpret_cast<const float *>(r) + b * nn;
+            const float *rb = reinterpret_cast<const float *>(r) + b * r_bs;
             float4 win[5];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T
         }
     }
     const bool vok = vec_ok && x + VW <= n;
-    const T *rb = r + b * nn;
+    const T *rb = r + b * r_bs;
     auto load_row = [&](int yy, T (&d)[VW]) {
         const T *p = rb + (long)fold_index(yy, n, boundary) * n;
         if (vok) {
@@ -685,6 +685,91 @@ __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, const T
         }
         emit_band<T>(w, w_out + b * w_bs, px, y, x, n, vok);
         if (c_next) emit_band<T>(cj, c_next + b * next_bs, px, y, x, n, vok, true);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass of large scale j fused with the row pass of scale j + 1.  A CTA
+// owns KR whole rows y_k = r0 + s (m KR + k) of one map (rows at the stride s
+// of scale j, like k_st_col): each thread runs the column filter down CPT
+// columns of VW pixels (the register window of k_st_col), writes w_j and c_j,
+// and keeps its c_j in shared memory; after one barrier it filters those rows
+// along x at spacing 2s (the row pass of scale j + 1) into r_next.  The row
+// pass then reads c_j from shared memory instead of L2 and needs no launch of
+// its own.  r_next must not alias r (other CTAs still read r's rows).
+// grid = (1, s * ceil(ceil(n / s) / KR), batch), block = n / (VW CPT).
+template <typename T, int KR, int CPT>
+__global__ void __launch_bounds__(256) k_st_colrow(const T *__restrict__ r, long r_bs, const T *c_prev, long prev_bs,
+                                                   T *c_next, long next_bs, T *__restrict__ w_out, long w_bs,
+                                                   T *__restrict__ r_next, long rn_bs, int n, int s, int boundary)
+{
+    pdl_entry();
+    constexpr int VW = 16 / sizeof(T);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *rows = reinterpret_cast<T *>(smem_raw);  // [KR][n]: c_j of the CTA's rows
+    const int r0 = blockIdx.y % s, m = blockIdx.y / s;
+    const long b = blockIdx.z;
+    const T *rb = r + b * r_bs;
+    const int ybase = r0 + s * (m * KR);
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int x = (threadIdx.x + q * blockDim.x) * VW;
+        alignas(16) T win[5][VW];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ld16(win[u], rb + (long)fold_index(ybase + (u - 2) * s, n, boundary) * n + x);
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            const int y = ybase + k * s;
+            if (y >= n) break;
+            ld16(win[(k + 4) % 5], rb + (long)fold_index(y + 2 * s, n, boundary) * n + x);
+            const long px = (long)y * n + x;
+            alignas(16) T prev[VW]; alignas(16) T cj[VW]; alignas(16) T w[VW];
+            ld16(prev, c_prev + b * prev_bs + px);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) {
+                cj[u] = B3<T>::apply(win[k % 5][u], win[(k + 1) % 5][u], win[(k + 2) % 5][u], win[(k + 3) % 5][u],
+                                     win[(k + 4) % 5][u]);
+                w[u] = prev[u] - cj[u];
+            }
+            st16cs(w_out + b * w_bs + px, w);
+            st16(c_next + b * next_bs + px, cj);
+            st16(rows + k * n + x, cj);
+        }
+    }
+    __syncthreads();
+    const int s2 = 2 * s;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int x = (threadIdx.x + q * blockDim.x) * VW;
+        const bool inner = s2 % VW == 0 && x - 2 * s2 >= 0 && x + VW + 2 * s2 <= n;
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            const int y = ybase + k * s;
+            if (y >= n) break;
+            const T *row = rows + k * n;
+            alignas(16) T o[VW];
+            if (inner) {
+                alignas(16) T m2[VW]; alignas(16) T m1[VW]; alignas(16) T c0[VW]; alignas(16) T p1[VW];
+                alignas(16) T p2[VW];
+                ld16(m2, row + x - 2 * s2);
+                ld16(m1, row + x - s2);
+                ld16(c0, row + x);
+                ld16(p1, row + x + s2);
+                ld16(p2, row + x + 2 * s2);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) o[u] = B3<T>::apply(m2[u], m1[u], c0[u], p1[u], p2[u]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < VW; ++u) {
+                    const int xx = x + u;
+                    o[u] = B3<T>::apply(row[fold_index(xx - 2 * s2, n, boundary)],
+                                        row[fold_index(xx - s2, n, boundary)], row[xx],
+                                        row[fold_index(xx + s2, n, boundary)],
+                                        row[fold_index(xx + 2 * s2, n, boundary)]);
+                }
+            }
+            st16(r_next + b * rn_bs + (long)y * n + x, o);
+        }
     }
 }
 
@@ -1011,13 +1096,55 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
     // (128-thread CTAs re-read them from L2: 0.897 -> 0.834 ms per 32-map step)
     const int rt = std::min(256, std::max(32, (n / VW + 31) / 32 * 32));
     const unsigned gxr = (unsigned)((n + rt * VW - 1) / (rt * VW));
+    // Column pass of scale j fused with the row pass of j + 1 (large_path 3;
+    // automatic after fused small scales on maps up to 256^2): whole rows per
+    // CTA, CPT vectors per thread, KRC rows per CTA.  Alone, on a 4-map chunk
+    // of 1024^2 fp32, it takes 14.4-15.7 us against 16.4-18.5 us for the two
+    // kernels, and the launches' summed event times per 32-map batch drop
+    // 0.79 -> 0.70 ms; but in the chunked two-stream pipeline the batch is
+    // slower (0.812 -> 0.855 ms; 16 x 2048^2: 2.05 -> 2.46 ms, KRC = 1: 2.27,
+    // KRC = 4: 2.68; a dedicated scratch map instead of the smooth-array slot
+    // does not help), while 128 x 256^2 gains (0.228 -> 0.222 ms).
+    constexpr int KRC = 2;
+    const int ct = std::min(256, n / VW);
+    const int cpt = ct > 0 && (n / VW) % ct == 0 ? (n / VW) / ct : 0;
+    const size_t rsm = (size_t)KRC * n * sizeof(T);
+    const bool colrow = vec_ok && (cpt == 1 || cpt == 2 || cpt == 4 || cpt == 8) && rsm <= 64 * 1024 &&
+                        (cfg.large_path == 3 || (cfg.large_path == 0 && f >= 1 && n <= 256));
+    // r_j lives in Bb; with the fused kernel the row-filtered maps alternate
+    // between Bb and the pyramid's smooth-array slot (unused until the last
+    // column pass writes c_{J-1} there), placed so that r_{J-1} is in Bb.
+    auto r_in_last = [&](int j) { return colrow && (J - 1 - j) % 2 == 1; };
     for (int j = f + 1; j <= J - 1; ++j) {
         const int sp = 1 << (j - 1);
         const T *c_prev = j == 1 ? kappa : A;
         T *c_next = j == J - 1 ? last : A;
         const long next_bs = j == J - 1 ? pyr_bs : nn;
-        FM_LAUNCH(FM_K_STARLET_ROW, k_st_row<T>, dim3(gxr, n, batch), rt, 0, s, c_prev, nn, Bb, n, sp, bnd,
-                  vec_ok ? 1 : 0);
+        T *rj = r_in_last(j) ? last : Bb;
+        const long rj_bs = r_in_last(j) ? pyr_bs : nn;
+        if (!colrow || j == f + 1)
+            FM_LAUNCH(FM_K_STARLET_ROW, k_st_row<T>, dim3(gxr, n, batch), rt, 0, s, c_prev, nn, rj, rj_bs, n, sp, bnd,
+                      vec_ok ? 1 : 0);
+        if (colrow && j < J - 1) {
+            T *rn = r_in_last(j + 1) ? last : Bb;
+            const long rn_bs = r_in_last(j + 1) ? pyr_bs : nn;
+            const unsigned gyc = (unsigned)(sp * ((((n + sp - 1) / sp) + KRC - 1) / KRC));
+#define FM_COLROW(CP)                                                                                               \
+    do {                                                                                                            \
+        auto kc = k_st_colrow<T, KRC, CP>;                                                                          \
+        FM_CUDA_TRY(fm::smem_attr((const void *)kc, rsm));                                                          \
+        FM_LAUNCH(FM_K_STARLET_COLROW, kc, dim3(1, gyc, batch), ct, rsm, s, rj, rj_bs, c_prev, nn, c_next, next_bs,  \
+                  pyr + (long)(j - 1) * nn, pyr_bs, rn, rn_bs, n, sp, bnd);                                         \
+    } while (0)
+            switch (cpt) {
+            case 1: FM_COLROW(1); break;
+            case 2: FM_COLROW(2); break;
+            case 4: FM_COLROW(4); break;
+            default: FM_COLROW(8); break;
+            }
+#undef FM_COLROW
+            continue;
+        }
         const unsigned gy = (unsigned)(sp * ((((n + sp - 1) / sp) + KR - 1) / KR));
         CUtensorMap mr, mp;
         memset(&mr, 0, sizeof(mr));
@@ -1027,7 +1154,7 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
         // only for maps of 4096^2 and up, whose arrays do not stay in L2: there
         // the copies cut 16 x 4096^2 (J = 9) from 11.75 to 11.40 ms, while on
         // the L2-resident chunks of 1024^2 maps they cost 0.835 -> 0.849 ms
-        if (sizeof(T) == 4 && vec_ok && n >= 4096 && n % 512 == 0 && (mask & 24)) {
+        if (sizeof(T) == 4 && vec_ok && n >= 4096 && n % 512 == 0 && (mask & 24) && rj == Bb) {
             // r and c_{j-1} viewed as {256, n/256, sp, n/sp, batch}: a box picks
             // 512 columns of rows r0 + sp (m0 .. m0 + rows - 1)
             const uint64_t dims[5] = {256, (uint64_t)n / 256, (uint64_t)sp, (uint64_t)(n / sp), (uint64_t)batch};
@@ -1038,8 +1165,8 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
         }
         const size_t csm = tma ? 128 + (size_t)(2 * KR + 4) * 512 * sizeof(float) : 0;
         if (tma) FM_CUDA_TRY(fm::smem_attr((const void *)k_st_col<T, KR>, csm));
-        FM_LAUNCH(FM_K_STARLET_COL, (k_st_col<T, KR>), dim3(gx, gy, batch), 128, csm, s, Bb, c_prev, nn, c_next,
-                  next_bs, pyr + (long)(j - 1) * nn, pyr_bs, n, sp, bnd, vec_ok ? 1 : 0, mr, mp, tma);
+        FM_LAUNCH(FM_K_STARLET_COL, (k_st_col<T, KR>), dim3(gx, gy, batch), 128, csm, s, rj, rj_bs, c_prev, nn,
+                  c_next, next_bs, pyr + (long)(j - 1) * nn, pyr_bs, n, sp, bnd, vec_ok ? 1 : 0, mr, mp, tma);
     }
     return FM_OK;
 }

@@ -29,7 +29,7 @@ FM_F32, FM_F64 = 0, 1
 FM_MIRROR, FM_PERIODIC = 0, 1
 FM_FILTER_STARLET, FM_FILTER_S98, FM_FILTER_JBJ04, FM_FILTER_VW98 = 0, 1, 2, 3
 KERNEL_IDS = {"fft_rows_fwd": 1, "fft_cols_ks": 2, "fft_rows_inv": 3, "starlet_tile": 4, "starlet_row": 5,
-              "starlet_col": 6, "map_direct": 7, "noise_final": 8, "noise_accum": 9}
+              "starlet_col": 6, "map_direct": 7, "noise_final": 8, "noise_accum": 9, "starlet_colrow": 10}
 
 
 class fm_config(ctypes.Structure):

@@ -34,7 +34,7 @@ def test_starlet_matches_oracle(n, J, boundary, dtype):
     for fuse in sorted({-1, 1, 2, 3, J - 1}):
         if fuse > J - 1:
             continue
-        for large_path in ((1, 2) if 0 < fuse < J - 1 else (0,)):
+        for large_path in ((0, 1, 2, 3) if 0 < fuse < J - 1 else (0, 3)):
             pyr = fm.fm_starlet_forward(torch.from_numpy(kappa).cuda(), J, boundary=boundary, fuse_depth=fuse,
                                         large_path=large_path)
             errs = band_errs(pyr.cpu().numpy(), ref)
@@ -143,3 +143,26 @@ def test_bulk_copy_halo_equals_thread_loads(n, J, batch):
     assert torch.equal(with_tma, without)
     ref = oracle.starlet(maps[batch - 1].astype(np.float64), J)
     assert max(band_errs(with_tma[batch - 1].cpu().numpy(), ref)) <= 1e-5
+
+
+@pytest.mark.parametrize("n,J,batch,boundary,dtype", [(1024, 7, 4, 0, np.float32), (2048, 8, 1, 0, np.float32),
+                                                      (4096, 9, 1, 0, np.float32), (512, 6, 3, 1, np.float32),
+                                                      (1000, 7, 2, 0, np.float32), (512, 7, 2, 0, np.float64),
+                                                      (8192, 7, 1, 1, np.float32)])
+def test_fused_column_row_pass_is_bit_exact(n, J, batch, boundary, dtype):
+    """The column pass of each large scale fused with the next scale's row
+    pass (large_path 3; automatic on maps up to 256^2) computes the same sums in the same order as the separate row and column
+    kernels (large_path 1): bit-identical pyramids, with the pyramid's
+    smooth-array slot used as scratch and then overwritten."""
+    fm = _fm()
+    kappa = torch.from_numpy(np.stack([synth.grf_kappa(n, seed=7 + b) for b in range(batch)]).astype(dtype)).cuda()
+    ref = fm.fm_starlet_forward(kappa, J, boundary=boundary, large_path=1)
+    for lp in (0, 3):
+        got = fm.fm_starlet_forward(kappa, J, boundary=boundary, large_path=lp)
+        assert torch.equal(got, ref), (lp, (got - ref).abs().max().item())
+    plain = fm.fm_starlet_forward(kappa, J, boundary=boundary, fuse_depth=-1, large_path=3)
+    assert torch.equal(plain, fm.fm_starlet_forward(kappa, J, boundary=boundary, fuse_depth=-1, large_path=1))
+    # the oracle on one sampled map
+    r = oracle.starlet(kappa[-1].double().cpu().numpy(), J, boundary) if n <= 1024 else None
+    if r is not None:
+        assert max(band_errs(ref[-1].cpu().numpy(), r)) <= TOL[dtype]
