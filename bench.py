@@ -313,7 +313,9 @@ def side_legs(fm, torch, n, J, g1, g2):
     # batched noise maps: R realisations of KS + starlet with FP64 accumulation
     R = 1000
     t_noise = cuda_time(torch, lambda: fm.fm_map_noise(s1, s2, J, R, seed=3), 2)
-    out["noise"] = {"R": R, "ms": t_noise, "value": n * n * J * R / (t_noise * 1e-3) / 1e6, "unit": UNIT}
+    t_kahan = cuda_time(torch, lambda: fm.fm_map_noise(s1, s2, J, R, seed=3, accum=1), 2)
+    out["noise"] = {"R": R, "ms": t_noise, "value": n * n * J * R / (t_noise * 1e-3) / 1e6, "unit": UNIT,
+                    "kahan_fp32_sums_ms": t_kahan}
     # the exact expectation of that variance (periodic boundary): one FFT pipeline
     t_exp = cuda_time(torch, lambda: fm.fm_map_noise_expected(s1, s2, J), 5)
     out["noise_expected"] = {"ms": t_exp, "boundary": "periodic",

@@ -72,7 +72,8 @@ extern "C" {
 typedef struct {
     int precision;  /* FM_F32 (0) or FM_F64 (1) */
     int boundary;   /* starlet boundary: FM_MIRROR (0) or FM_PERIODIC (1) */
-    int accum;      /* noise accumulators: 0 = FP64 (the only mode) */
+    int accum;      /* noise running sums: 0 = FP64, 1 = fp32 with Kahan
+                       compensation (FM_F32 maps only); same scratch size */
     int fuse_depth; /* starlet scales done by the fused 2-D tile kernel:
                        0 = automatic (2 for fp32 maps of 1024^2 to 2048^2,
                        else 3; see fm_starlet_fuse_depth), k > 0 = scales

@@ -22,7 +22,8 @@ static int check_cfg(const fm_config &c)
 {
     if (c.precision != FM_F32 && c.precision != FM_F64) return einval("precision must be FM_F32 or FM_F64");
     if (c.boundary != FM_MIRROR && c.boundary != FM_PERIODIC) return einval("boundary must be FM_MIRROR or FM_PERIODIC");
-    if (c.accum != 0) return einval("accum must be 0 (FP64 accumulation)");
+    if (c.accum != 0 && c.accum != 1) return einval("accum must be 0 (FP64 sums) or 1 (Kahan fp32 sums)");
+    if (c.accum == 1 && c.precision != FM_F32) return einval("accum = 1 (Kahan fp32 sums) needs FM_F32 maps");
     if (c.fuse_depth < -1 || c.fuse_depth > 8) return einval("fuse_depth out of range [-1, 8]");
     if (c.large_path < 0 || c.large_path > 3) return einval("large_path must be 0, 1, 2 or 3");
     return FM_OK;

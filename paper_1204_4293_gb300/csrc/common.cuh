@@ -196,9 +196,10 @@ int launch_modulus2(const void *a, long a_bs, const void *b, long b_bs, void *ou
 int launch_unit_shears(void *g1d, void *g2d, long nn, int precision, cudaStream_t s);
 int launch_band_moments(const void *pyr, double *moments, int n, int J, int batch, int precision, void *scratch,
                         cudaStream_t s);
-int launch_noise_accum(const void *pyr, int nb, long pyr_bs, long nn, int bands, double *s1, double *s2,
-                       int precision, cudaStream_t s);
-int launch_noise_finalize(const double *s1, const double *s2, const void *wdata, double *var, void *snr,
-                          long nelem, int R, int precision, cudaStream_t s);
+// acc: FP64 S1, S2 (accum 0) or fp32 Kahan pairs s1, c1, s2, c2 (accum 1), bands * nn elements each
+int launch_noise_accum(const void *pyr, int nb, long pyr_bs, long nn, int bands, void *acc, int precision, int accum,
+                       cudaStream_t s);
+int launch_noise_finalize(const void *acc, const void *wdata, double *var, void *snr, long nelem, int R,
+                          int precision, int accum, cudaStream_t s);
 
 }  // namespace fm

@@ -39,12 +39,59 @@ __global__ void __launch_bounds__(256) k_noise_accum(const T *__restrict__ pyr, 
     }
 }
 
-int launch_noise_accum(const void *pyr, int nb, long pyr_bs, long nn, int bands, double *s1, double *s2,
-                       int precision, cudaStream_t s)
+// accum = 1 (fp32 maps): the running sums are fp32 with Kahan compensation
+// (Kahan 1965): per element a sum s and a compensation c, the true sum being
+// s - c; a batch's partial sum a enters as y = a - c, t = s + y,
+// c = (t - s) - y, s = t.  The arrays are s1, c1, s2, c2, each nb floats.
+__global__ void __launch_bounds__(256) k_noise_accum_kahan(const float *__restrict__ pyr, int nb, long pyr_bs,
+                                                           long nn, int bands, float *__restrict__ acc)
+{
+    pdl_entry();
+    const long ne = bands * nn;
+    const long nq = ne / 4;
+    float4 *s1 = reinterpret_cast<float4 *>(acc), *c1 = s1 + nq, *s2 = c1 + nq, *c2 = s2 + nq;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nq; i += (long)gridDim.x * blockDim.x) {
+        float a[4] = {0.f, 0.f, 0.f, 0.f}, q[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int b = 0; b < nb; ++b) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(pyr + b * pyr_bs) + i);
+            const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] += w[u];
+                q[u] = fmaf(w[u], w[u], q[u]);
+            }
+        }
+        float4 S1 = s1[i], C1 = c1[i], S2 = s2[i], C2 = c2[i];
+        float *ps1 = &S1.x, *pc1 = &C1.x, *ps2 = &S2.x, *pc2 = &C2.x;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float y1 = __fsub_rn(a[u], pc1[u]);
+            const float t1 = __fadd_rn(ps1[u], y1);
+            pc1[u] = __fsub_rn(__fsub_rn(t1, ps1[u]), y1);
+            ps1[u] = t1;
+            const float y2 = __fsub_rn(q[u], pc2[u]);
+            const float t2 = __fadd_rn(ps2[u], y2);
+            pc2[u] = __fsub_rn(__fsub_rn(t2, ps2[u]), y2);
+            ps2[u] = t2;
+        }
+        s1[i] = S1;
+        c1[i] = C1;
+        s2[i] = S2;
+        c2[i] = C2;
+    }
+}
+
+// acc: FP64 s1, s2 (accum 0) or fp32 s1, c1, s2, c2 (accum 1), bands * nn each
+int launch_noise_accum(const void *pyr, int nb, long pyr_bs, long nn, int bands, void *acc, int precision, int accum,
+                       cudaStream_t s)
 {
     long g = (bands * nn / 4 + 255) / 256;
     if (g > 152L * 16) g = 152L * 16;
-    if (precision == FM_F64)
+    double *s1 = static_cast<double *>(acc), *s2 = s1 + (long)bands * nn;
+    if (accum == 1)
+        FM_LAUNCH(FM_K_NOISE_ACCUM, k_noise_accum_kahan, (unsigned)g, 256, 0, s, (const float *)pyr, nb, pyr_bs, nn,
+                  bands, static_cast<float *>(acc));
+    else if (precision == FM_F64)
         FM_LAUNCH(FM_K_NOISE_ACCUM, (k_noise_accum<double, double2>), (unsigned)g, 256, 0, s, (const double *)pyr,
                   nb, pyr_bs, nn, bands, s1, s2);
     else
@@ -53,15 +100,30 @@ int launch_noise_accum(const void *pyr, int nb, long pyr_bs, long nn, int bands,
     return FM_OK;
 }
 
-template <typename T>
-__global__ void k_noise_final(const double *__restrict__ s1, const double *__restrict__ s2,
-                              const T *__restrict__ wdata, double *__restrict__ var, T *__restrict__ snr, long nelem,
-                              int R)
+// S1 and S2 of element i in FP64: the FP64 sums, or s - c of the Kahan pairs
+template <bool KAHAN>
+__device__ __forceinline__ void noise_sums(const void *acc, long nelem, long i, double &a, double &q)
+{
+    if constexpr (KAHAN) {
+        const float *f = static_cast<const float *>(acc);
+        a = (double)f[i] - (double)f[nelem + i];
+        q = (double)f[2 * nelem + i] - (double)f[3 * nelem + i];
+    } else {
+        const double *d = static_cast<const double *>(acc);
+        a = d[i];
+        q = d[nelem + i];
+    }
+}
+
+template <typename T, bool KAHAN>
+__global__ void k_noise_final(const void *__restrict__ acc, const T *__restrict__ wdata, double *__restrict__ var,
+                              T *__restrict__ snr, long nelem, int R)
 {
     pdl_entry();
     const double invR = 1.0 / R, invR1 = 1.0 / (R - 1);
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nelem; i += (long)gridDim.x * blockDim.x) {
-        const double a = s1[i], q = s2[i];
+        double a, q;
+        noise_sums<KAHAN>(acc, nelem, i, a, q);
         double v = (q - a * a * invR) * invR1;
         v = v < 0 ? 0 : v;
         var[i] = v;
@@ -69,17 +131,20 @@ __global__ void k_noise_final(const double *__restrict__ s1, const double *__res
     }
 }
 
-int launch_noise_finalize(const double *s1, const double *s2, const void *wdata, double *var, void *snr, long nelem,
-                          int R, int precision, cudaStream_t s)
+int launch_noise_finalize(const void *acc, const void *wdata, double *var, void *snr, long nelem, int R,
+                          int precision, int accum, cudaStream_t s)
 {
     long g = (nelem + 255) / 256;
     if (g > 152L * 16) g = 152L * 16;
     if (precision == FM_F64)
-        FM_LAUNCH(FM_K_NOISE_FINAL, k_noise_final<double>, (unsigned)g, 256, 0, s, s1, s2, (const double *)wdata, var,
-                  (double *)snr, nelem, R);
+        FM_LAUNCH(FM_K_NOISE_FINAL, (k_noise_final<double, false>), (unsigned)g, 256, 0, s, acc,
+                  (const double *)wdata, var, (double *)snr, nelem, R);
+    else if (accum == 1)
+        FM_LAUNCH(FM_K_NOISE_FINAL, (k_noise_final<float, true>), (unsigned)g, 256, 0, s, acc, (const float *)wdata,
+                  var, (float *)snr, nelem, R);
     else
-        FM_LAUNCH(FM_K_NOISE_FINAL, k_noise_final<float>, (unsigned)g, 256, 0, s, s1, s2, (const float *)wdata, var,
-                  (float *)snr, nelem, R);
+        FM_LAUNCH(FM_K_NOISE_FINAL, (k_noise_final<float, false>), (unsigned)g, 256, 0, s, acc, (const float *)wdata,
+                  var, (float *)snr, nelem, R);
     return FM_OK;
 }
 

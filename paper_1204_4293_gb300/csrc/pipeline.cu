@@ -263,14 +263,13 @@ int noise_submit(const void *g1, const void *g2, double *var_out, void *snr_out,
     const size_t es = cfg.precision == FM_F64 ? 8 : 4;
     const long nn = (long)n * n;
     const long nb = (long)(J - 1) * nn;
-    double *s1 = reinterpret_cast<double *>(scr);
-    double *s2 = s1 + nb;
+    void *acc = scr;  // FP64 S1, S2 or the fp32 Kahan pairs: 16 bytes per band pixel either way
     char *pyr = scr + L.acc_b, *slots = pyr + L.pyr_b;
     const ChunkPlan &p = L.p;
     const bool multi = ds && L.slots > 1;
     const char *c1 = static_cast<const char *>(g1), *c2 = static_cast<const char *>(g2);
     int r;
-    FM_CUDA_TRY(cudaMemsetAsync(s1, 0, (size_t)2 * nb * sizeof(double), s));
+    FM_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)2 * nb * sizeof(double), s));
     for (int r0 = 0; r0 < R; r0 += L.batch) {
         const int b = R - r0 < L.batch ? R - r0 : L.batch;
         if (multi) {  // the batch's pyramid buffer is free once `s` has accumulated the last batch
@@ -290,12 +289,12 @@ int noise_submit(const void *g1, const void *g2, double *var_out, void *snr_out,
                 FM_CUDA_TRY(cudaEventRecord(ds->join[k], ds->s[k]));
                 FM_CUDA_TRY(cudaStreamWaitEvent(s, ds->join[k], 0));
             }
-        if ((r = launch_noise_accum(pyr, b, (long)J * nn, nn, J - 1, s1, s2, cfg.precision, s))) return r;
+        if ((r = launch_noise_accum(pyr, b, (long)J * nn, nn, J - 1, acc, cfg.precision, cfg.accum, s))) return r;
     }
     // S/N needs the unrotated bands; finalize reads them from the first pyramid
     // (every chunk stream has joined `s` after the last batch)
     if (snr_out && (r = run_chunk(c1, c2, pyr, n, J, 0, 1, cfg, p, slots, s))) return r;
-    return launch_noise_finalize(s1, s2, snr_out ? pyr : nullptr, var_out, snr_out, nb, R, cfg.precision, s);
+    return launch_noise_finalize(acc, snr_out ? pyr : nullptr, var_out, snr_out, nb, R, cfg.precision, cfg.accum, s);
 }
 
 struct NoiseKey {

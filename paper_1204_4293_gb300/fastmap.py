@@ -112,9 +112,9 @@ def _prec(t: torch.Tensor) -> int:
     raise TypeError(f"maps must be float32 or float64, got {t.dtype}")
 
 
-def _cfg(precision, boundary=FM_MIRROR, fuse_depth=0, large_path=0):
+def _cfg(precision, boundary=FM_MIRROR, fuse_depth=0, large_path=0, accum=0):
     c = fm_config()
-    c.precision, c.boundary, c.accum, c.fuse_depth, c.large_path = precision, boundary, 0, fuse_depth, large_path
+    c.precision, c.boundary, c.accum, c.fuse_depth, c.large_path = precision, boundary, accum, fuse_depth, large_path
     return c
 
 
@@ -256,14 +256,15 @@ def fm_map_noise_expected(g1, g2, J, out=None, stream=None):
     return var
 
 
-def fm_map_noise(g1, g2, J, R, seed, boundary=FM_MIRROR, with_snr=True, fuse_depth=0, stream=None):
-    """(variance [J-1, n, n] float64, S/N or None) over R rotated realisations."""
+def fm_map_noise(g1, g2, J, R, seed, boundary=FM_MIRROR, with_snr=True, fuse_depth=0, stream=None, accum=0):
+    """(variance [J-1, n, n] float64, S/N or None) over R rotated realisations.
+    accum: 0 = FP64 running sums, 1 = fp32 running sums with Kahan compensation."""
     n, batch = _maps(g1, g2)
     if batch != 1 or g1.dim() != 2:
         raise ValueError("fm_map_noise takes one [n, n] map")
     var = torch.empty((J - 1, n, n), dtype=torch.float64, device=g1.device)
     snr = torch.empty((J - 1, n, n), dtype=g1.dtype, device=g1.device) if with_snr else None
-    c = _cfg(_prec(g1), boundary, fuse_depth)
+    c = _cfg(_prec(g1), boundary, fuse_depth, accum=accum)
     _check(_lib.fm_map_noise(_ptr(g1), _ptr(g2), _ptr(var), _ptr(snr), n, J, int(R),
                              ctypes.c_uint64(int(seed) & (2**64 - 1)), ctypes.byref(c), _stream(stream)),
            "fm_map_noise")

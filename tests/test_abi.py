@@ -70,6 +70,12 @@ def test_validation_before_any_device_work(fm):
     bad = fm._cfg(2)
     assert lib.fm_starlet_forward(None, None, 64, 3, 1, ctypes.byref(bad), None) == fm.FM_EINVAL
     assert b"precision" in lib.fm_last_error()
+    for acc, prec in ((2, 0), (1, 1)):  # accum 2 does not exist; Kahan fp32 sums need fp32 maps
+        bad = fm._cfg(prec, accum=acc)
+        assert lib.fm_map_noise(1, 1, 1, None, 64, 4, 8, 0, ctypes.byref(bad), None) == fm.FM_EINVAL
+        assert b"accum" in lib.fm_last_error()
+    bad = fm._cfg(0, large_path=4)
+    assert lib.fm_starlet_forward(1, 1, 64, 3, 1, ctypes.byref(bad), None) == fm.FM_EINVAL
     h = ctypes.c_void_p()
     assert lib.fm_serve_create(0, 2, ctypes.byref(h)) == fm.FM_EINVAL
     assert lib.fm_serve_poll(None, 1, None) == fm.FM_EINVAL

@@ -48,8 +48,8 @@ def test_noise_paper_size_few_realisations():
 
 def test_noise_graph_replay_matches_eager_launches():
     # fm_map_noise records the whole call into a CUDA graph and replays it;
-    # the replay, a second replay and eager launches must agree (up to the
-    # order of the FP64 atomic additions)
+    # the replay, a second replay and eager launches must agree (the
+    # accumulation order is fixed, so in practice bit for bit)
     fm = _fm()
     n, J, R = 128, 5, 40
     g1, g2 = shear(n, seed=9, dtype=np.float32)
@@ -73,4 +73,35 @@ def test_noise_graph_replay_matches_eager_launches():
     torch.cuda.synchronize()
     for other in (second, var):
         assert torch.allclose(first, other, rtol=1e-12, atol=0)
+    fm.fm_trim()
+
+
+@pytest.mark.parametrize("n,J,R,boundary", [(32, 4, 23, 1), (64, 5, 40, 0), (1024, 7, 3, 0)])
+def test_noise_kahan_fp32_sums_match_oracle(n, J, R, boundary):
+    """accum = 1: fp32 running sums with Kahan compensation instead of FP64;
+    the variance stays within the same 1e-4 of the FP64 oracle."""
+    fm = _fm()
+    g1, g2 = shear(n, seed=11, dtype=np.float32)
+    var, snr = fm.fm_map_noise(torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda(), J, R, seed=77,
+                               boundary=boundary, accum=1)
+    rv, rs = oracle.map_noise(g1.astype(np.float64), g2.astype(np.float64), J, R, 77, boundary)
+    var, snr = var.cpu().numpy(), snr.cpu().numpy()
+    for j in range(J - 1):
+        assert np.abs(var[j] - rv[j]).max() / rv[j].mean() <= 1e-4
+        if R >= 20:  # with 3 realisations some pixels' sigma is near 0 and S/N is ill-conditioned
+            assert np.abs(snr[j] - rs[j]).max() / np.sqrt(np.mean(rs[j] ** 2)) <= 1e-3
+
+
+def test_noise_kahan_and_fp64_sums_agree_over_many_batches():
+    """R = 300 realisations (ten accumulation batches of at most 32): the
+    compensated fp32 sums give the FP64 sums' variance to ~1e-6."""
+    fm = _fm()
+    n, J, R = 256, 5, 300
+    g1, g2 = shear(n, seed=12, dtype=np.float32)
+    t1, t2 = torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda()
+    v64, _ = fm.fm_map_noise(t1, t2, J, R, seed=5, with_snr=False)
+    vk, _ = fm.fm_map_noise(t1, t2, J, R, seed=5, with_snr=False, accum=1)
+    for j in range(J - 1):
+        rel = ((vk[j] - v64[j]).abs().max() / v64[j].mean()).item()
+        assert rel <= 1e-5, (j, rel)
     fm.fm_trim()
