@@ -9,7 +9,9 @@ namespace fm {
 // pyramids ([nb][J][n][n], bands 0..J-2 used).  The batch's partial sums are
 // formed in the element type (at most 32 terms) and added once to the FP64
 // running sums: GB300's FP64 rate is a small fraction of its FP32 rate, so
-// the FP64 work is two additions per band pixel per batch.
+// the FP64 work is two additions per band pixel per batch.  The pyramids are
+// read once with streaming (evict-first) loads, so they do not push the chunk
+// pipeline's intermediates out of L2.
 template <typename T, typename V>
 __global__ void __launch_bounds__(256) k_noise_accum(const T *__restrict__ pyr, int nb, long pyr_bs, long nn,
                                                      int bands, double *__restrict__ s1, double *__restrict__ s2)
@@ -23,7 +25,7 @@ __global__ void __launch_bounds__(256) k_noise_accum(const T *__restrict__ pyr, 
 #pragma unroll
         for (int u = 0; u < VW; ++u) a[u] = q[u] = (T)0;
         for (int b = 0; b < nb; ++b) {
-            const V v = __ldg(reinterpret_cast<const V *>(pyr + b * pyr_bs + e));
+            const V v = __ldcs(reinterpret_cast<const V *>(pyr + b * pyr_bs + e));
             const T *w = reinterpret_cast<const T *>(&v);
 #pragma unroll
             for (int u = 0; u < VW; ++u) {
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(256) k_noise_accum_kahan(const float *__restri
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nq; i += (long)gridDim.x * blockDim.x) {
         float a[4] = {0.f, 0.f, 0.f, 0.f}, q[4] = {0.f, 0.f, 0.f, 0.f};
         for (int b = 0; b < nb; ++b) {
-            const float4 v = __ldg(reinterpret_cast<const float4 *>(pyr + b * pyr_bs) + i);
+            const float4 v = __ldcs(reinterpret_cast<const float4 *>(pyr + b * pyr_bs) + i);
             const float w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {

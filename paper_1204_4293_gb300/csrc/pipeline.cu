@@ -27,6 +27,7 @@ struct DevStreams {
     cudaStream_t cap = nullptr;  // origin stream for graph capture
     cudaStream_t s[kMaxChunkStreams] = {};
     cudaEvent_t fork = nullptr, join[kMaxChunkStreams] = {};
+    cudaEvent_t acc[2] = {};  // noise: accumulation of the batch in pyramid buffer 0 / 1 done
 };
 std::mutex g_ds_mu;  // guards g_ds and serialises multi-stream submission
 std::unordered_map<int, DevStreams> g_ds;
@@ -43,6 +44,7 @@ int dev_streams(DevStreams **out)
             FM_CUDA_TRY(cudaEventCreateWithFlags(&d.join[k], cudaEventDisableTiming));
         }
         FM_CUDA_TRY(cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming));
+        for (auto &e : d.acc) FM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     *out = &d;
     return FM_OK;
@@ -228,8 +230,10 @@ struct NoiseLayout {
     int batch = 1;  // realisations per accumulation pass
     ChunkPlan p;    // KS + starlet of a batch, chunk by chunk
     int slots = 1;  // chunk slots in use: internal streams, or 1 on the caller's stream
+    int pyr_bufs = 1;  // batch pyramid buffers: 2 lets the chunk streams run on during an accumulation
     size_t acc_b = 0, pyr_b = 0, total = 0;
 };
+constexpr int kNoisePyrBufs = 2;
 
 // A batch's pyramids stay within ~1 GiB (at most 32 realisations: the
 // accumulation's partial sums are fp32 over at most 32 terms).
@@ -244,9 +248,10 @@ NoiseLayout noise_layout(int n, int J, int R, const fm_config &cfg, bool multi_s
     L.batch = (int)(batch > R ? R : batch);
     L.p = plan_chunks(n, J, L.batch, cfg);
     L.slots = multi_stream ? L.p.slots : 1;
+    L.pyr_bufs = L.slots > 1 && R > L.batch ? kNoisePyrBufs : 1;
     L.acc_b = up(2 * (size_t)(J - 1) * nn * sizeof(double));
     L.pyr_b = up((size_t)L.batch * J * nn * es);
-    L.total = L.acc_b + L.pyr_b + (size_t)L.slots * L.p.slot_b;
+    L.total = L.acc_b + (size_t)L.pyr_bufs * L.pyr_b + (size_t)L.slots * L.p.slot_b;
     return L;
 }
 
@@ -254,9 +259,10 @@ NoiseLayout noise_layout(int n, int J, int R, const fm_config &cfg, bool multi_s
 // rotated realisations through KS + starlet, chunk by chunk (over the
 // internal streams when `ds` is given, else on `s`), then S1 += w, S2 += w^2
 // over the batch's pyramids on `s`; the unrotated pass for S/N; the finalize
-// kernel.  (A second pyramid buffer, letting the chunk streams run on into the
-// next batch during an accumulation, measured no faster: 36.5 vs 35.6 ms for
-// R = 1000 at 1024^2.)
+// kernel.  With internal streams and more than one batch, two pyramid
+// buffers alternate so that the chunk streams run on into the next batch
+// while `s` accumulates (R = 1000 at 1024^2: 32.2 -> 31.6 ms; the
+// accumulation's pyramid loads are streaming, evict-first: 31.5 ms).
 int noise_submit(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
                  const fm_config &cfg, const NoiseLayout &L, char *scr, cudaStream_t s, DevStreams *ds)
 {
@@ -264,23 +270,29 @@ int noise_submit(const void *g1, const void *g2, double *var_out, void *snr_out,
     const long nn = (long)n * n;
     const long nb = (long)(J - 1) * nn;
     void *acc = scr;  // FP64 S1, S2 or the fp32 Kahan pairs: 16 bytes per band pixel either way
-    char *pyr = scr + L.acc_b, *slots = pyr + L.pyr_b;
+    char *pyr = scr + L.acc_b, *slots = pyr + (size_t)L.pyr_bufs * L.pyr_b;
     const ChunkPlan &p = L.p;
     const bool multi = ds && L.slots > 1;
     const char *c1 = static_cast<const char *>(g1), *c2 = static_cast<const char *>(g2);
     int r;
     FM_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)2 * nb * sizeof(double), s));
-    for (int r0 = 0; r0 < R; r0 += L.batch) {
+    for (int r0 = 0, ib = 0; r0 < R; r0 += L.batch, ++ib) {
         const int b = R - r0 < L.batch ? R - r0 : L.batch;
-        if (multi) {  // the batch's pyramid buffer is free once `s` has accumulated the last batch
+        const int buf = ib % L.pyr_bufs;
+        char *pb = pyr + (size_t)buf * L.pyr_b;
+        if (multi && (L.pyr_bufs == 1 || ib == 0)) {
+            // start after `s` (the zeroed sums; with one buffer, the last accumulation)
             FM_CUDA_TRY(cudaEventRecord(ds->fork, s));
             for (int k = 0; k < L.slots; ++k) FM_CUDA_TRY(cudaStreamWaitEvent(ds->s[k], ds->fork, 0));
+        } else if (multi && ib >= L.pyr_bufs) {
+            // this buffer is free once the accumulation of batch ib - 2 has read it
+            for (int k = 0; k < L.slots; ++k) FM_CUDA_TRY(cudaStreamWaitEvent(ds->s[k], ds->acc[buf], 0));
         }
         int i = 0;
         for (int c0 = 0; c0 < b; c0 += p.C, ++i) {
             const int k = multi ? i % L.slots : 0;
             const int bc = b - c0 < p.C ? b - c0 : p.C;
-            if ((r = run_chunk(c1, c2, pyr + (size_t)c0 * J * nn * es, n, J, 0, bc, cfg, p, slots + k * p.slot_b,
+            if ((r = run_chunk(c1, c2, pb + (size_t)c0 * J * nn * es, n, J, 0, bc, cfg, p, slots + k * p.slot_b,
                                multi ? ds->s[k] : s, true, seed, r0 + c0)))
                 return r;
         }
@@ -289,7 +301,8 @@ int noise_submit(const void *g1, const void *g2, double *var_out, void *snr_out,
                 FM_CUDA_TRY(cudaEventRecord(ds->join[k], ds->s[k]));
                 FM_CUDA_TRY(cudaStreamWaitEvent(s, ds->join[k], 0));
             }
-        if ((r = launch_noise_accum(pyr, b, (long)J * nn, nn, J - 1, acc, cfg.precision, cfg.accum, s))) return r;
+        if ((r = launch_noise_accum(pb, b, (long)J * nn, nn, J - 1, acc, cfg.precision, cfg.accum, s))) return r;
+        if (multi && L.pyr_bufs > 1) FM_CUDA_TRY(cudaEventRecord(ds->acc[buf], s));
     }
     // S/N needs the unrotated bands; finalize reads them from the first pyramid
     // (every chunk stream has joined `s` after the last batch)
