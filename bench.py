@@ -333,9 +333,13 @@ def large_fields_leg(fm, torch, J=9):
         pyr = torch.empty(B, J, n, n, dtype=torch.float32, device="cuda")
         fn = lambda: fm.fm_map_starlet(g1, g2, J, out=pyr)  # noqa: E731
         fn()
+        ms_builtin = cuda_time(torch, fn, 3)
+        plan = fm.fm_autotune(n, J, B)  # autotuned tile form and fusion depth for this shape
+        fn()
         ms = cuda_time(torch, fn, 3)
         out[f"{B}x{n}"] = {"ms": ms, "value": n * n * J * B / (ms * 1e-3) / 1e6, "unit": UNIT, "J": J,
-                           "hbm_algorithmic_gbs": (12 + 4 * (J + 1)) * n * n * B / (ms * 1e-3) / 1e9}
+                           "hbm_algorithmic_gbs": (12 + 4 * (J + 1)) * n * n * B / (ms * 1e-3) / 1e9,
+                           "plan": plan, "ms_builtin_plan": ms_builtin}
         del g1, g2, pyr
         torch.cuda.empty_cache()
     return out
@@ -461,6 +465,7 @@ def main():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--no-side", action="store_true", help="skip the side legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in plan (no autotuning)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -481,6 +486,10 @@ def main():
     g1, g2 = make_inputs(fm, torch, n, B, seed=1000 * (rank + 1), dtype=torch.float32)
     pyr = torch.empty(B, J, n, n, dtype=torch.float32, device="cuda")
     step = lambda: fm.fm_map_starlet(g1, g2, J, out=pyr)  # noqa: E731
+
+    # the library's autotuner picks the plan (fused depth, large-scale path,
+    # tile form, chunk budget) for this shape before anything is timed
+    plan = None if args.no_autotune else fm.fm_autotune(n, J, B)
 
     # warm-up (the first call records the batched call's CUDA graph)
     for _ in range(args.warmup):
@@ -557,7 +566,7 @@ def main():
     if rank == 0:
         peak, peak_src = load_peaks()
         px_step = n * n * B
-        fuse = fm.fm_starlet_fuse_depth(n, J)  # the library's automatic choice for this size
+        fuse = fm.fm_starlet_fuse_depth(n, J)  # the plan's fused depth for this size
         chunks = per_kind["fft_rows_fwd"][1]  # one row-FFT launch per chunk of maps
         bytes_launch = algo_bytes_per_px_launch(dom, fuse) * px_step / chunks
         achieved = bytes_launch * dom_cnt / (dom_ms * 1e-3) / 1e9
@@ -570,6 +579,7 @@ def main():
             "config": {"workload": f"{B} x {n}x{n} fp32 shear maps per GPU per step -> Kaiser-Squires -> "
                                    f"starlet J={J} (theta=2..{2 ** (J - 1)} px + smooth)",
                        "n": n, "J": J, "maps_per_gpu": B, "parallelism": f"replicas x{world} (maps sharded)",
+                       "plan": plan if plan else "built-in rules (--no-autotune)",
                        "l2": f"inputs larger than L2: {2 * B * n * n * 4 / 2**20:.0f} MB shear in + "
                              f"{B * J * n * n * 4 / 2**20:.0f} MB pyramid out per step"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -75,12 +75,14 @@ typedef struct {
     int accum;      /* noise running sums: 0 = FP64, 1 = fp32 with Kahan
                        compensation (FM_F32 maps only); same scratch size */
     int fuse_depth; /* starlet scales done by the fused 2-D tile kernel:
-                       0 = automatic (2 for fp32 maps of 1024^2 to 2048^2,
-                       else 3; see fm_starlet_fuse_depth), k > 0 = scales
+                       0 = automatic (the autotuned plan, else 2 for fp32
+                       maps of 1024^2 to 2048^2 and 3 otherwise; see
+                       fm_starlet_fuse_depth, fm_autotune), k > 0 = scales
                        1..k (at most 4 in fp32, 3 in fp64, J - 1), -1 = none
                        (the plain one-scale-per-pass form) */
-    int large_path; /* scales after the fused ones: 0 = automatic (3 after
-                       fused small scales on maps up to 256^2, else 1),
+    int large_path; /* scales after the fused ones: 0 = automatic (the
+                       autotuned plan, else 3 after fused small scales on
+                       maps up to 256^2 and 1 otherwise),
                        1 = one row pass + one column pass per scale, 2 = all
                        large scales in one row kernel + one column-strip
                        kernel, 3 = the column pass of each scale fused with
@@ -271,7 +273,8 @@ int fm_device_error(void);
  *                        up); default 31
  *   FM_TUNE_TILE         fp32 kernel of the fused small starlet scales:
  *                        0 = row-filtered shared buffer, 1 = register
- *                        window (default) */
+ *                        window; default: the autotuned plan's, else 1
+ * FM_TUNE_CHUNK_BYTES set this way also overrides autotuned budgets. */
 #define FM_TUNE_CHUNK_BYTES 1
 #define FM_TUNE_GRAPHS 2
 #define FM_TUNE_CHUNK_STREAMS 3
@@ -279,6 +282,42 @@ int fm_device_error(void);
 #define FM_TUNE_TILE 5
 #define FM_TUNE_TMA 6
 int fm_tune(int knob, int64_t value);
+
+/* ---- autotuner ----------------------------------------------------------------
+ * fm_autotune times fm_map_starlet on `batch` synthetic n x n maps (J scales,
+ * cfg->precision and cfg->boundary; cfg's fuse_depth and large_path are
+ * ignored) for candidate plans, by coordinate descent from the built-in rules
+ * over: fused depth 1..4 (fp64 1..3, at most J - 1), large-scale path 1 or 3,
+ * fp32 tile kernel form (1 = register window, 0 = shared buffer) and chunk
+ * budget 40 / 60 / 80 / 120 MiB; a candidate replaces the best so far only
+ * when 1 % faster.  The winner goes into a process-wide table keyed by
+ * (n, J, precision), which the automatic fields (fuse_depth = 0,
+ * large_path = 0) and the default tile form and chunk budget then follow
+ * (knobs set by fm_tune keep precedence).  fm_autotune allocates its own
+ * buffers, synchronises with the device and drops the cached graphs; do not
+ * run it concurrently with other calls.  `best` (may be NULL) receives the
+ * plan, its time and the built-in plan's time.
+ * fm_autotune_get: FM_ENOTFOUND if the table has no entry.  fm_autotune_set
+ * enters a plan by hand (validated).  fm_autotune_save writes the table as
+ * JSON ({"fastmap_autotune": 1, "entries": [{"n", "J", "precision",
+ * "fuse_depth", "large_path", "tile", "chunk_mb", "ms", "default_ms"}]});
+ * fm_autotune_load merges such a file (nothing changes if it is malformed:
+ * FM_EINVAL); fm_autotune_clear empties the table.  Host only except
+ * fm_autotune. */
+typedef struct {
+    int fuse_depth; /* scales of the fused tile kernel */
+    int large_path; /* 1 or 3 (see fm_config) */
+    int tile;       /* fp32 tile kernel: 1 = register window, 0 = shared buffer */
+    int chunk_mb;   /* chunk budget of batched calls, MiB (0 = the default) */
+    double ms;         /* fm_map_starlet with this plan, per call (tuning batch) */
+    double default_ms; /* the same with the built-in rules */
+} fm_plan;
+int fm_autotune(int n, int J, int batch, const fm_config *cfg, fm_plan *best);
+int fm_autotune_get(int n, int J, int precision, fm_plan *plan);
+int fm_autotune_set(int n, int J, int precision, const fm_plan *plan);
+int fm_autotune_save(const char *path);
+int fm_autotune_load(const char *path);
+int fm_autotune_clear(void);
 
 /* Batched fm_map_starlet calls (when chunked) and fm_map_noise calls are
  * recorded once into CUDA graphs that keep their scratch (a few per kind,

@@ -38,7 +38,8 @@ void prof_after(int kid, cudaStream_t s);
 // finished (a no-op when launched without the attribute) and then lets the
 // next kernel's CTAs be scheduled into SMs this grid leaves idle in its tail.
 extern std::atomic<int> g_pdl;
-// fp32 fused-scale tile kernel: 0 = shared row-filtered buffer, 1 = register window
+// fp32 fused-scale tile kernel: 0 = shared row-filtered buffer, 1 = register
+// window, -1 = automatic (the autotuned plan, else the register window)
 extern std::atomic<int> g_tile_variant;
 // bulk tensor copies (mask): 1 = starlet tile halo, 2 = row FFT input rows,
 // 4 = row IFFT input rows, 8 = large-scale column window rows, 16 = its
@@ -179,6 +180,18 @@ int launch_fft32(const float *in1, const float *in2, long in_bs, float *out1, fl
                  int batch, int op, const float2 *filt, float out_scale, uint64_t seed, int r0, bool rotate,
                  const float2 *tw, cudaStream_t s);
 size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg);
+// ---- autotuned plans (tune.cu) ----------------------------------------------------
+// A plan for maps of n^2, J scales, one precision: fused depth, large-scale
+// path (1 or 3), fp32 tile kernel form (1 = register window, 0 = shared
+// buffer), chunk budget in MiB of batched calls (0 = the default).
+struct TunedPlan {
+    int fuse = 0, large_path = 0, tile = 1, chunk_mb = 0;
+    double ms = 0, default_ms = 0;
+};
+bool tune_lookup(int n, int J, int precision, TunedPlan *out);  // false if no entry
+int starlet_builtin_fuse(int n, int J, const fm_config &cfg);  // automatic depth without a table entry
+int starlet_builtin_large_path(int n, int J, int fuse);
+int64_t chunk_budget_default();
 int starlet_fuse_depth(int n, int J, const fm_config &cfg);  // scales of the fused tile kernel
 int launch_map_direct(const void *g1, const void *g2, const void *weight, long w_bs, void *map, void *coverage, int n,
                       int batch, int filter, double theta, int ell, double cut, int precision, cudaStream_t s);

@@ -59,8 +59,15 @@ struct ChunkPlan {
 // replay 0.89 ms per batch, unchunked 1.05 ms, 40 MB 1.06 ms, 100 MB 0.97 ms
 constexpr int64_t kDefaultChunkBytes = 80ll << 20;
 std::atomic<int64_t> g_chunk_bytes{kDefaultChunkBytes};
+std::atomic<int> g_chunk_bytes_set{0};  // set by fm_tune: overrides the autotuned budget
 std::atomic<int> g_chunk_streams{2};
 std::atomic<int> g_use_graphs{1};
+
+}  // namespace
+
+int64_t chunk_budget_default() { return kDefaultChunkBytes; }
+
+namespace {
 
 // intermediates of one slot kept near the chunk budget (two slots in flight)
 ChunkPlan plan_chunks(int n, int J, int batch, const fm_config &cfg)
@@ -69,7 +76,10 @@ ChunkPlan plan_chunks(int n, int J, int batch, const fm_config &cfg)
     const size_t nn = (size_t)n * n;
     const size_t per_map = nn * 3 * es + starlet_scratch_elems(n, J, 1, cfg) * es;
     ChunkPlan p;
-    const int64_t budget = g_chunk_bytes.load();
+    int64_t budget = g_chunk_bytes.load();
+    TunedPlan tp;
+    if (!g_chunk_bytes_set.load() && tune_lookup(n, J, cfg.precision, &tp) && tp.chunk_mb > 0)
+        budget = (int64_t)tp.chunk_mb << 20;
     p.C = budget <= 0 ? batch : (int)(budget / (int64_t)per_map);
     if (p.C < 1) p.C = 1;
     if (p.C > batch) p.C = batch;
@@ -176,7 +186,7 @@ static int map_starlet_dev(const void *g1, const void *g2, void *pyramid, int n,
         return run_chunks(g1, g2, pyramid, n, J, batch, cfg, p, (char *)sc.p, s, *ds);
     }
     GraphKey key{g1, g2, pyramid, n, J, batch, 0, cfg, p.C, p.slots,
-                 g_pdl.load() | (g_tile_variant.load() << 1) | (g_use_tma.load() << 3)};
+                 g_pdl.load() | ((g_tile_variant.load() + 1) << 1) | (g_use_tma.load() << 3)};
     FM_CUDA_TRY(cudaGetDevice(&key.dev));
     GraphEntry *hit = nullptr;
     for (auto &e : g_graphs)
@@ -363,7 +373,7 @@ int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out
     DevStreams *ds = nullptr;
     if ((st = dev_streams(&ds))) return st;
     NoiseKey key{g1, g2, var_out, snr_out, n, J, R, 0, seed, cfg, L.p.C, L.slots,
-                 g_pdl.load() | (g_tile_variant.load() << 1) | (g_use_tma.load() << 3)};
+                 g_pdl.load() | ((g_tile_variant.load() + 1) << 1) | (g_use_tma.load() << 3)};
     FM_CUDA_TRY(cudaGetDevice(&key.dev));
     NoiseGraph *hit = nullptr;
     for (auto &e : g_noise_graphs)
@@ -485,7 +495,10 @@ int fm_trim(void)
 int fm_tune(int knob, int64_t value)
 {
     switch (knob) {
-    case FM_TUNE_CHUNK_BYTES: g_chunk_bytes.store(value < 0 ? kDefaultChunkBytes : value); return FM_OK;
+    case FM_TUNE_CHUNK_BYTES:
+        g_chunk_bytes.store(value < 0 ? kDefaultChunkBytes : value);
+        g_chunk_bytes_set.store(value >= 0);
+        return FM_OK;
     case FM_TUNE_GRAPHS: g_use_graphs.store(value < 0 ? 1 : (value != 0)); return FM_OK;
     case FM_TUNE_CHUNK_STREAMS:
         g_chunk_streams.store(value < 0 ? 2 : (int)(value < 1 ? 1 : value > kMaxChunkStreams ? kMaxChunkStreams : value));
@@ -497,7 +510,7 @@ int fm_tune(int knob, int64_t value)
         return FM_OK;
     case FM_TUNE_TILE:
         if (value > 1) return einval("FM_TUNE_TILE takes 0 or 1");
-        g_tile_variant.store(value < 0 ? 1 : (int)value);
+        g_tile_variant.store(value < 0 ? -1 : (int)value);
         return FM_OK;
     }
     return einval("unknown tuning knob");

@@ -40,7 +40,7 @@ int einval(const std::string &msg)
 // ---- launch accounting and profiling ------------------------------------------
 std::atomic<int64_t> g_launches{0};
 std::atomic<int> g_pdl{1};
-std::atomic<int> g_tile_variant{1};
+std::atomic<int> g_tile_variant{-1};
 std::atomic<int> g_use_tma{kDefaultTma};
 
 namespace {

@@ -927,14 +927,44 @@ __global__ void __launch_bounds__(512) k_st_cols_multi(const T *__restrict__ c_a
 // 2.216 / 2.051 / 2.151:
 // two scales for 1024^2 and 2048^2 maps, whose chunked large-scale passes
 // run from L2, else three.
-static int auto_fuse(int n, int J, const fm_config &cfg)
+// An autotuned plan for (n, J, precision) overrides this rule.
+static int clamp_fuse(int f, int J, const fm_config &cfg)
 {
-    if (cfg.fuse_depth < 0) return 0;
-    int f = cfg.fuse_depth != 0 ? cfg.fuse_depth : (cfg.precision == FM_F32 && n >= 1024 && n <= 2048 ? 2 : 3);
     const int fmax = cfg.precision == FM_F64 ? 3 : 4;  // tile + halo must fit shared memory
     if (f > fmax) f = fmax;
     if (f > J - 1) f = J - 1;
     return f;
+}
+
+int starlet_builtin_fuse(int n, int J, const fm_config &cfg)
+{
+    if (cfg.fuse_depth < 0) return 0;
+    const int f = cfg.fuse_depth != 0 ? cfg.fuse_depth : (cfg.precision == FM_F32 && n >= 1024 && n <= 2048 ? 2 : 3);
+    return clamp_fuse(f, J, cfg);
+}
+
+static int auto_fuse(int n, int J, const fm_config &cfg)
+{
+    TunedPlan tp;
+    if (cfg.fuse_depth == 0 && tune_lookup(n, J, cfg.precision, &tp)) return clamp_fuse(tp.fuse, J, cfg);
+    return starlet_builtin_fuse(n, J, cfg);
+}
+
+// Large-scale path when cfg.large_path = 0: the autotuned plan's, else the
+// column pass fused with the next row pass on maps up to 256^2 after fused
+// small scales (measured below), else one row and one column pass per scale.
+int starlet_builtin_large_path(int n, int J, int fuse)
+{
+    (void)J;
+    return fuse >= 1 && n <= 256 ? 3 : 1;
+}
+
+static int resolve_large_path(int n, int J, int f, const fm_config &cfg)
+{
+    if (cfg.large_path != 0) return cfg.large_path;
+    TunedPlan tp;
+    if (tune_lookup(n, J, cfg.precision, &tp)) return tp.large_path;
+    return starlet_builtin_large_path(n, J, f);
 }
 
 // Strip width of the column-strip kernel: 2 n W elements must fit 128 KB.
@@ -954,7 +984,9 @@ int starlet_fuse_depth(int n, int J, const fm_config &cfg) { return auto_fuse(n,
 size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg)
 {
     const int f = auto_fuse(n, J, cfg);
-    if (f >= J - 1) return 0;
+    // an automatic depth may follow a table entry that changes before the
+    // launch: it gets the two maps of the large-scale passes whenever J > 2
+    if (f >= J - 1 && (cfg.fuse_depth != 0 || J == 2)) return 0;
     const size_t es = cfg.precision == FM_F64 ? 8 : 4;
     const size_t per = (size_t)batch * n * n;
     if (f >= 1 && cfg.large_path == 2 && cols_multi_width(n, es)) return (size_t)(J - f) * per;  // c_f + u's
@@ -982,7 +1014,7 @@ int starlet_wait_error(bool clear) { return wait_error_flag(clear); }
 
 template <int F>
 static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, float *c_out, long c_bs, int n,
-                         int boundary, int batch, bool vec_ok, cudaStream_t s)
+                         int boundary, int batch, bool vec_ok, int variant, cudaStream_t s)
 {
     constexpr int TS = 64;
     constexpr int H = (1 << (F + 1)) - 2;
@@ -991,7 +1023,6 @@ static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, fl
     const size_t smem = 2ull * P * P * sizeof(float);
     const int tiles_x = (n + TS - 1) / TS;
     const int tiles_per_map = tiles_x * tiles_x;
-    const int variant = g_tile_variant.load(std::memory_order_relaxed);
     if (variant == 1) {
         auto k = k_st_tile32v2<F>;
         const size_t smem2 = tile2_smem<F>();
@@ -1016,17 +1047,17 @@ static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, fl
 
 template <typename T>
 static int tile_dispatch(int f, const T *in, T *w_out, long w_bs, long w_ss, T *c_out, long c_bs, int n,
-                         int boundary, int batch, bool vec_ok, cudaStream_t s)
+                         int boundary, int batch, bool vec_ok, int variant, cudaStream_t s)
 {
     constexpr int TS = sizeof(T) == 4 ? 64 : 32;
     if constexpr (sizeof(T) == 4) {
         const float *fi = (const float *)in;
         float *fw = (float *)w_out, *fc = (float *)c_out;
         switch (f) {
-        case 1: return tile32_launch<1>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, vec_ok, s);
-        case 2: return tile32_launch<2>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, vec_ok, s);
-        case 3: return tile32_launch<3>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, vec_ok, s);
-        case 4: return tile32_launch<4>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, vec_ok, s);
+        case 1: return tile32_launch<1>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, vec_ok, variant, s);
+        case 2: return tile32_launch<2>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, vec_ok, variant, s);
+        case 3: return tile32_launch<3>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, vec_ok, variant, s);
+        case 4: return tile32_launch<4>(fi, fw, w_bs, w_ss, fc, c_bs, n, boundary, batch, vec_ok, variant, s);
         }
         return FM_EINVAL;
     }
@@ -1057,12 +1088,18 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
     if (f >= 1) {
         T *c_out = f == J - 1 ? last : A;
         const long c_bs = f == J - 1 ? pyr_bs : nn;
-        int st = tile_dispatch<T>(f, kappa, pyr, pyr_bs, nn, c_out, c_bs, n, bnd, batch, vec_ok, s);
+        int tvar = g_tile_variant.load(std::memory_order_relaxed);
+        if (tvar < 0) {
+            TunedPlan tp;
+            tvar = tune_lookup(n, J, cfg.precision, &tp) ? tp.tile : 1;
+        }
+        int st = tile_dispatch<T>(f, kappa, pyr, pyr_bs, nn, c_out, c_bs, n, bnd, batch, vec_ok, tvar, s);
         if (st != FM_OK) return st;
     }
     const int K = J - 1 - f;  // large scales left after the tile kernel
     const int Wc = cols_multi_width(n, sizeof(T));
-    if (K >= 1 && f >= 1 && Wc && vec_ok && cfg.large_path == 2) {
+    const int lpath = resolve_large_path(n, J, f, cfg);
+    if (K >= 1 && f >= 1 && Wc && vec_ok && lpath == 2) {
         T *U = A + (long)batch * nn;  // u_{f+1} .. u_{f+K}, each batch * nn
         const size_t rsm = 2ull * n * sizeof(T);
         FM_CUDA_TRY(fm::smem_attr((const void *)k_st_rows_multi<T>, rsm));
@@ -1109,8 +1146,7 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
     const int ct = std::min(256, n / VW);
     const int cpt = ct > 0 && (n / VW) % ct == 0 ? (n / VW) / ct : 0;
     const size_t rsm = (size_t)KRC * n * sizeof(T);
-    const bool colrow = vec_ok && (cpt == 1 || cpt == 2 || cpt == 4 || cpt == 8) && rsm <= 64 * 1024 &&
-                        (cfg.large_path == 3 || (cfg.large_path == 0 && f >= 1 && n <= 256));
+    const bool colrow = vec_ok && (cpt == 1 || cpt == 2 || cpt == 4 || cpt == 8) && rsm <= 64 * 1024 && lpath == 3;
     // r_j lives in Bb; with the fused kernel the row-filtered maps alternate
     // between Bb and the pyramid's smooth-array slot (unused until the last
     // column pass writes c_{J-1} there), placed so that r_{J-1} is in Bb.

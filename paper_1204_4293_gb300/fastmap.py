@@ -48,6 +48,11 @@ class fm_result(ctypes.Structure):
                 ("t_done_ns", ctypes.c_int64)]
 
 
+class fm_plan(ctypes.Structure):
+    _fields_ = [("fuse_depth", ctypes.c_int), ("large_path", ctypes.c_int), ("tile", ctypes.c_int),
+                ("chunk_mb", ctypes.c_int), ("ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+
+
 _P, _I, _D, _U64, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_size_t
 _CFG = ctypes.POINTER(fm_config)
 _SIGS = {
@@ -76,6 +81,12 @@ _SIGS = {
     "fm_profile_select": (_I, [_I]),
     "fm_tune": (_I, [_I, ctypes.c_int64]),
     "fm_trim": (_I, []),
+    "fm_autotune": (_I, [_I, _I, _I, _CFG, ctypes.POINTER(fm_plan)]),
+    "fm_autotune_get": (_I, [_I, _I, _I, ctypes.POINTER(fm_plan)]),
+    "fm_autotune_set": (_I, [_I, _I, _I, ctypes.POINTER(fm_plan)]),
+    "fm_autotune_save": (_I, [ctypes.c_char_p]),
+    "fm_autotune_load": (_I, [ctypes.c_char_p]),
+    "fm_autotune_clear": (_I, []),
     "fm_profile_read": (_I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -291,6 +302,47 @@ def fm_band_moments(pyramid, stream=None):
     _check(_lib.fm_band_moments(_ptr(pyramid), _ptr(out), n, J, batch, ctypes.byref(c), _stream(stream)),
            "fm_band_moments")
     return out
+
+
+def _plan_dict(p: fm_plan) -> dict:
+    return {"fuse_depth": p.fuse_depth, "large_path": p.large_path, "tile": p.tile, "chunk_mb": p.chunk_mb,
+            "ms": p.ms, "default_ms": p.default_ms}
+
+
+def fm_autotune(n, J, batch, precision=FM_F32, boundary=FM_MIRROR) -> dict:
+    """Time candidate plans of fm_map_starlet for `batch` n x n maps and keep
+    the fastest for (n, J, precision) in the library's table."""
+    c = _cfg(precision, boundary)
+    p = fm_plan()
+    _check(_lib.fm_autotune(int(n), int(J), int(batch), ctypes.byref(c), ctypes.byref(p)), "fm_autotune")
+    return _plan_dict(p)
+
+
+def fm_autotune_get(n, J, precision=FM_F32):
+    """The table's plan for (n, J, precision), or None."""
+    p = fm_plan()
+    st = _lib.fm_autotune_get(int(n), int(J), int(precision), ctypes.byref(p))
+    if st == FM_ENOTFOUND:
+        return None
+    _check(st, "fm_autotune_get")
+    return _plan_dict(p)
+
+
+def fm_autotune_set(n, J, precision=FM_F32, fuse_depth=3, large_path=1, tile=1, chunk_mb=0) -> None:
+    p = fm_plan(fuse_depth=fuse_depth, large_path=large_path, tile=tile, chunk_mb=chunk_mb)
+    _check(_lib.fm_autotune_set(int(n), int(J), int(precision), ctypes.byref(p)), "fm_autotune_set")
+
+
+def fm_autotune_save(path) -> None:
+    _check(_lib.fm_autotune_save(os.fsencode(path)), "fm_autotune_save")
+
+
+def fm_autotune_load(path) -> None:
+    _check(_lib.fm_autotune_load(os.fsencode(path)), "fm_autotune_load")
+
+
+def fm_autotune_clear() -> None:
+    _check(_lib.fm_autotune_clear(), "fm_autotune_clear")
 
 
 def fm_trim() -> None:

@@ -104,3 +104,51 @@ def test_fuse_depth_rule(fm):
         d(16, 5)  # n < 2^J
     with pytest.raises(fm.FastmapError):
         d(1024, 7, fuse_depth=9)
+
+
+def test_autotune_table_roundtrip(fm, tmp_path):
+    """The autotuner's table (host only): a plan entered for (n, J,
+    precision) drives the automatic fused depth; it saves to JSON, loads
+    back, rejects malformed files and invalid plans, and clears."""
+    import json
+    fm.fm_autotune_clear()
+    try:
+        assert fm.fm_autotune_get(1024, 7) is None
+        assert fm.fm_starlet_fuse_depth(1024, 7) == 2  # built-in rule
+        fm.fm_autotune_set(1024, 7, fuse_depth=4, large_path=3, tile=0, chunk_mb=60)
+        fm.fm_autotune_set(512, 6, precision=fm.FM_F64, fuse_depth=1, large_path=1, tile=1, chunk_mb=0)
+        got = fm.fm_autotune_get(1024, 7)
+        assert (got["fuse_depth"], got["large_path"], got["tile"], got["chunk_mb"]) == (4, 3, 0, 60)
+        assert fm.fm_starlet_fuse_depth(1024, 7) == 4
+        assert fm.fm_starlet_fuse_depth(1024, 7, fuse_depth=3) == 3  # an explicit depth wins
+        assert fm.fm_starlet_fuse_depth(1024, 7, precision=fm.FM_F64) == 3  # other precision: built-in
+        assert fm.fm_starlet_fuse_depth(512, 6, precision=fm.FM_F64) == 1
+        path = tmp_path / "plans.json"
+        fm.fm_autotune_save(path)
+        doc = json.loads(path.read_text())
+        assert doc["fastmap_autotune"] == 1 and len(doc["entries"]) == 2
+        fm.fm_autotune_clear()
+        assert fm.fm_autotune_get(1024, 7) is None and fm.fm_starlet_fuse_depth(1024, 7) == 2
+        fm.fm_autotune_load(path)
+        assert fm.fm_autotune_get(1024, 7)["chunk_mb"] == 60
+        assert fm.fm_autotune_get(512, 6, fm.FM_F64)["fuse_depth"] == 1
+        bad = tmp_path / "bad.json"
+        bad.write_text('{"fastmap_autotune": 1, "entries": [{"n": 1024, "J": 7, "precision": 0, "fuse_depth": 9, '
+                       '"large_path": 1, "tile": 1, "chunk_mb": 80}]}')
+        with pytest.raises(fm.FastmapError):
+            fm.fm_autotune_load(bad)
+        assert fm.fm_autotune_get(1024, 7)["fuse_depth"] == 4  # unchanged
+        bad.write_text('{"entries": []}')
+        with pytest.raises(fm.FastmapError):
+            fm.fm_autotune_load(bad)
+        for kw in ({"fuse_depth": 5}, {"large_path": 2}, {"tile": 2}, {"chunk_mb": -1}):
+            args = dict(fuse_depth=3, large_path=1, tile=1, chunk_mb=0)
+            args.update(kw)
+            with pytest.raises(fm.FastmapError):
+                fm.fm_autotune_set(256, 5, **args)
+        with pytest.raises(fm.FastmapError):
+            fm.fm_autotune_set(256, 5, precision=fm.FM_F64, fuse_depth=4)
+        with pytest.raises(fm.FastmapError):
+            fm.fm_autotune(48, 4, 1)  # not a power of two: refused before any device work
+    finally:
+        fm.fm_autotune_clear()
