@@ -323,6 +323,37 @@ def side_legs(fm, torch, n, J, g1, g2):
     return out
 
 
+def per_kernel_hbm(fm, fn, px, fuse, reps=3):
+    """Per kernel kind: device time per call (CUDA events around each launch,
+    chunks on one stream), launches, algorithmic bytes per launch and the
+    fraction of the measured HBM copy bandwidth that they reach."""
+    peak, src = load_peaks()
+    fm.fm_tune(fm.FM_TUNE_CHUNK_STREAMS, 1)
+    kinds = ["fft_rows_fwd", "fft_cols_ks", "fft_rows_inv", "starlet_tile", "starlet_row", "starlet_col",
+             "starlet_colrow"]
+    res = {}
+    try:
+        for k in kinds:
+            fm.fm_profile_select(k)
+            for _ in range(reps):
+                fn()
+            ms, cnt = fm.fm_profile_read()
+            if cnt:
+                res[k] = [ms / reps, cnt / reps]
+    finally:
+        fm.fm_profile_select(0)
+        fm.fm_tune(fm.FM_TUNE_CHUNK_STREAMS, -1)
+    chunks = res["fft_rows_fwd"][1]
+    out = {}
+    for k, (ms, cnt) in res.items():
+        b = algo_bytes_per_px_launch(k, fuse) * px / chunks
+        gbs = b * cnt / (ms * 1e-3) / 1e9
+        out[k] = {"ms_per_call": ms, "launches": cnt, "algorithmic_bytes_per_launch": b, "gbs": gbs,
+                  "frac_hbm": gbs / peak}
+    out["peak_gbs"] = f"{peak} ({src})"
+    return out
+
+
 def large_fields_leg(fm, torch, J=9):
     """Large fields, batched: 16 x 4096^2 and 1 x 8192^2 fp32 maps, P(k) ~
     k^-2.5, starlet J = 9 (two distinct GRFs per size, repeated, plus shape
@@ -340,6 +371,8 @@ def large_fields_leg(fm, torch, J=9):
         out[f"{B}x{n}"] = {"ms": ms, "value": n * n * J * B / (ms * 1e-3) / 1e6, "unit": UNIT, "J": J,
                            "hbm_algorithmic_gbs": (12 + 4 * (J + 1)) * n * n * B / (ms * 1e-3) / 1e9,
                            "plan": plan, "ms_builtin_plan": ms_builtin}
+        if B > 1:  # maps far larger than L2: each kernel's HBM roofline fraction
+            out[f"{B}x{n}"]["per_kernel"] = per_kernel_hbm(fm, fn, n * n * B, plan["fuse_depth"])
         del g1, g2, pyr
         torch.cuda.empty_cache()
     return out
