@@ -222,22 +222,42 @@ __global__ void __launch_bounds__(256, 2) k_rows_inv32(const float2 *__restrict_
     }
 }
 
+// With use_tma (mw: the work buffer as floats {2n, n, batch}, box {2W,
+// min(n, 256), 1}), the CTA's strip of W columns arrives by n / min(n, 256)
+// bulk tensor copies into the exchange buffer, densely as [n][W] float2,
+// instead of 32 strided loads per thread.
 template <int LOGN>
 __global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, const float2 *__restrict__ tw,
-                                                   int op, const float2 *__restrict__ filt)
+                                                   int op, const float2 *__restrict__ filt,
+                                                   const __grid_constant__ CUtensorMap mw, int use_tma)
 {
     pdl_entry();
     using P = Plan32<LOGN>;
     constexpr int W = P::W, N = P::N;
     constexpr int STRIPS = N / W;
-    extern __shared__ __align__(16) float2 sm32[];
+    extern __shared__ __align__(16) unsigned char smem_col[];
+    float2 *sm32 = align128<float2>(smem_col);
     const long b = blockIdx.x / STRIPS;
     const int x0 = (blockIdx.x % STRIPS) * W;
     const int c = threadIdx.x % W, j = threadIdx.x / W;
     float2 *base = work + b * (long)N * N + x0 + c;
     float2 v[32];
+    if (use_tma) {
+        __shared__ uint64_t bar;
+        constexpr int BR = N < 256 ? N : 256;  // rows per copy
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&bar, (uint32_t)(N * W * sizeof(float2)));
+            for (int k = 0; k < N / BR; ++k) tma_load_3d(sm32 + k * BR * W, &mw, 2 * x0, k * BR, (int)b, &bar);
+        }
+        if (!tma_wait_all(&bar, 0)) return;  // the copies never completed (flagged)
 #pragma unroll
-    for (int r = 0; r < 32; ++r) v[r] = base[(long)(j + r * P::TV) * N];
+        for (int r = 0; r < 32; ++r) v[r] = sm32[(j + r * P::TV) * W + c];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = base[(long)(j + r * P::TV) * N];
+    }
     fft_vec<LOGN, W, false>(v, sm32, c, j, tw);
     if (op == FFT_OP_SPECTRUM) {  // the 2-D spectrum [ky][kx] is the result
 #pragma unroll
@@ -304,7 +324,8 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
     // array or RPC n float2 <= RPC (n + n/32) float2) + 128 bytes of alignment
     const size_t row_smem = P::NPASS > 1 ? (size_t)RPC * (P::N + P::N / 32) * sizeof(float2) + 128 : 0;
     const int col_threads = P::W * P::TV;
-    const size_t col_smem = P::NPASS > 1 ? (size_t)(P::N * P::W + P::N * P::W / 32 + 1) * sizeof(float2) : 0;
+    // exchange buffer (also the TMA strip: n W float2) + 128 bytes of alignment
+    const size_t col_smem = P::NPASS > 1 ? (size_t)(P::N * P::W + P::N * P::W / 32 + 1) * sizeof(float2) + 128 : 0;
     const unsigned col_grid = (unsigned)((long)batch * (P::N / P::W));
     FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_fwd32<LOGN>, row_smem));
     FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_inv32<LOGN>, row_smem));
@@ -334,9 +355,25 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
         const uint32_t wbox[3] = {e0, (uint32_t)(2 * P::N / e0), (uint32_t)RPC};
         tma_out = (tma_mode & 4) && encode_map3d_f32(&mw, work, wdims, wstrides, wbox);
     }
+    // column strips by bulk tensor copies: the work buffer as floats
+    // {2n, n, batch}, a box of 2W floats (16 B at n = 8192) x min(n, 256) rows.
+    // Measured (KS + starlet, mask 31 -> 63): 32 x 1024^2 0.822 -> 0.815 ms,
+    // 16 x 2048^2 2.055 -> 2.020, 16 x 4096^2 11.32 -> 10.93, 1 x 8192^2
+    // 3.41 -> 3.17; 64 x 512^2 no change (the plain KS 0.177 -> 0.182), so
+    // from n = 1024 up.
+    CUtensorMap mc;
+    memset(&mc, 0, sizeof(mc));
+    int tma_col = 0;
+    if (P::NPASS > 1 && P::N >= 1024 && (tma_mode & 32)) {
+        const uint64_t cdims[3] = {(uint64_t)2 * P::N, (uint64_t)P::N, (uint64_t)batch};
+        const uint64_t cstrides[2] = {(uint64_t)P::N * 8, (uint64_t)P::N * P::N * 8};
+        const uint32_t cbox[3] = {(uint32_t)(2 * P::W), (uint32_t)(P::N < 256 ? P::N : 256), 1};
+        tma_col = encode_map3d_f32(&mc, work, cdims, cstrides, cbox) ? 1 : 0;
+    }
     FM_LAUNCH(FM_K_FFT_ROWS_FWD, k_rows_fwd32<LOGN>, row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs, work,
               total_rows, tw, seed, r0, rotate ? 1 : 0, m1, m2, tma_in);
-    FM_LAUNCH(FM_K_FFT_COLS_KS, k_cols_ks32<LOGN>, col_grid, col_threads, col_smem, s, work, tw, op, filt);
+    FM_LAUNCH(FM_K_FFT_COLS_KS, k_cols_ks32<LOGN>, col_grid, col_threads, col_smem, s, work, tw, op, filt, mc,
+              tma_col);
     if (op == FFT_OP_SPECTRUM) return FM_OK;
     const float scale = out_scale / ((float)P::N * (float)P::N);
     FM_LAUNCH(FM_K_FFT_ROWS_INV, k_rows_inv32<LOGN>, row_grid, RPC * P::TV, row_smem, s, work, out1, out2,

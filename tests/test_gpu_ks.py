@@ -56,16 +56,17 @@ def test_ks_8192_sampled_rows():
     assert kB.abs().max().item() / rms < 1e-5
 
 
-@pytest.mark.parametrize("n,batch", [(64, 3), (1024, 2), (4096, 1)])
+@pytest.mark.parametrize("n,batch", [(64, 3), (256, 2), (1024, 2), (2048, 1), (4096, 1), (8192, 1)])
 def test_bulk_copy_rows_equal_thread_loads(n, batch):
-    # the row FFT kernels take their rows by bulk tensor copies (default) or
-    # by per-thread loads: identical results, also for the rotated noise rows
-    # (one broadcast input map), and no wait ran out
+    # the FFT kernels take their rows (row passes) and column strips (column
+    # pass) by bulk tensor copies or by per-thread loads: identical results,
+    # also for the rotated noise rows (one broadcast input map), and no wait
+    # ran out
     fm = _fm()
     g1 = torch.empty((batch, n, n), device="cuda").normal_(0, 0.1)
     g2 = torch.empty_like(g1).normal_(0, 0.1)
     outs = {}
-    for tma in (1, 0):
+    for tma in (63, 0):
         fm.fm_tune(fm.FM_TUNE_TMA, tma)
         try:
             kE, kB = fm.fm_ks_invert(g1, g2, with_b=True)
@@ -75,5 +76,5 @@ def test_bulk_copy_rows_equal_thread_loads(n, batch):
             fm.fm_tune(fm.FM_TUNE_TMA, -1)
     torch.cuda.synchronize()
     assert fm.fm_device_error() == 0
-    for a, b in zip(outs[1], outs[0]):
+    for a, b in zip(outs[63], outs[0]):
         assert torch.equal(a, b)

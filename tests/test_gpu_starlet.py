@@ -131,7 +131,7 @@ def test_bulk_copy_halo_equals_thread_loads(n, J, batch):
     fm = _fm()
     maps = np.stack([synth.grf_kappa(n, seed=7 + b) for b in range(batch)]).astype(np.float32)
     kap = torch.from_numpy(maps).cuda()
-    fm.fm_tune(fm.FM_TUNE_TMA, 31)
+    fm.fm_tune(fm.FM_TUNE_TMA, 63)
     with_tma = fm.fm_starlet_forward(kap, J)
     fm.fm_tune(fm.FM_TUNE_TMA, 0)
     try:
