@@ -271,7 +271,8 @@ int fm_device_error(void);
  *                        8 / 16 = the window rows / the c_{j-1} rows of the
  *                        large-scale column pass (fp32 maps of 4096^2 and
  *                        up), 32 = the column strips of the column FFT
- *                        (n >= 1024); default 63
+ *                        (n >= 1024), 64 = their stores (n = 8192);
+ *                        default 127
  *   FM_TUNE_TILE         fp32 kernel of the fused small starlet scales:
  *                        0 = row-filtered shared buffer, 1 = register
  *                        window; default: the autotuned plan's, else 1

@@ -44,8 +44,8 @@ extern std::atomic<int> g_tile_variant;
 // bulk tensor copies (mask): 1 = starlet tile halo, 2 = row FFT input rows,
 // 4 = row IFFT input rows, 8 = large-scale column window rows, 16 = its
 // c_{j-1} rows (the last two on maps of 4096^2 and up), 32 = the column
-// FFT's strips (n >= 1024)
-constexpr int kDefaultTma = 63;
+// FFT's strips (n >= 1024), 64 = their stores (n = 8192)
+constexpr int kDefaultTma = 127;
 extern std::atomic<int> g_use_tma;
 extern std::atomic<int> g_prof_kid;  // kernel id whose launches are being timed (0: none)
 // 1 if a kernel of that file gave up waiting on a bulk copy (see fm_device_error)

@@ -222,10 +222,11 @@ __global__ void __launch_bounds__(256, 2) k_rows_inv32(const float2 *__restrict_
     }
 }
 
-// With use_tma (mw: the work buffer as floats {2n, n, batch}, box {2W,
-// min(n, 256), 1}), the CTA's strip of W columns arrives by n / min(n, 256)
-// bulk tensor copies into the exchange buffer, densely as [n][W] float2,
-// instead of 32 strided loads per thread.
+// With use_tma bit 0 (mw: the work buffer as floats {2n, n, batch}, box
+// {2W, min(n, 256), 1}), the CTA's strip of W columns arrives by
+// n / min(n, 256) bulk tensor copies into the exchange buffer, densely as
+// [n][W] float2, instead of 32 strided loads per thread; with bit 1 the
+// result leaves the same way (the spectrum-only mode stores per thread).
 template <int LOGN>
 __global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, const float2 *__restrict__ tw,
                                                    int op, const float2 *__restrict__ filt,
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, co
     const int c = threadIdx.x % W, j = threadIdx.x / W;
     float2 *base = work + b * (long)N * N + x0 + c;
     float2 v[32];
-    if (use_tma) {
+    if (use_tma & 1) {
         __shared__ uint64_t bar;
         constexpr int BR = N < 256 ? N : 256;  // rows per copy
         if (threadIdx.x == 0) mbar_init(&bar, 1);
@@ -304,6 +305,24 @@ __global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, co
         for (int r = 0; r < 32; ++r) v[r] = sm32[pad32((j + r * P::TV) * W + c)];
     }
     fft_vec<LOGN, W, true>(v, sm32, c, j, tw);
+    if (use_tma & 2) {
+        // the strip back through shared memory, dense [n][W], and out by bulk
+        // tensor stores of the same boxes
+        constexpr int BR = N < 256 ? N : 256;
+        __syncthreads();  // the last pass may still read the exchange buffer
+#pragma unroll
+        for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+            for (int r = 0; r < P::RL; ++r) sm32[(j + m * P::TV + r * P::NSL) * W + c] = v[m * P::RL + r];
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < N / BR; ++k) tma_store_3d(&mw, 2 * x0, k * BR, (int)b, sm32 + k * BR * W);
+            bulk_commit();
+            bulk_wait_all();
+        }
+        return;
+    }
 #pragma unroll
     for (int m = 0; m < P::ML; ++m)
 #pragma unroll
@@ -368,7 +387,11 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
         const uint64_t cdims[3] = {(uint64_t)2 * P::N, (uint64_t)P::N, (uint64_t)batch};
         const uint64_t cstrides[2] = {(uint64_t)P::N * 8, (uint64_t)P::N * P::N * 8};
         const uint32_t cbox[3] = {(uint32_t)(2 * P::W), (uint32_t)(P::N < 256 ? P::N : 256), 1};
-        tma_col = encode_map3d_f32(&mc, work, cdims, cstrides, cbox) ? 1 : 0;
+        // stores the same way only at n = 8192 (KS + starlet: 1 x 8192^2 3.18 ->
+        // 3.15 ms; 32 x 1024^2 0.813 -> 0.828, 16 x 4096^2 10.95 -> 11.00)
+        tma_col = encode_map3d_f32(&mc, work, cdims, cstrides, cbox)
+                      ? (1 | ((tma_mode & 64) && P::N >= 8192 ? 2 : 0))
+                      : 0;
     }
     FM_LAUNCH(FM_K_FFT_ROWS_FWD, k_rows_fwd32<LOGN>, row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs, work,
               total_rows, tw, seed, r0, rotate ? 1 : 0, m1, m2, tma_in);

@@ -505,7 +505,7 @@ int fm_tune(int knob, int64_t value)
         return FM_OK;
     case FM_TUNE_PDL: g_pdl.store(value < 0 ? 1 : (value != 0)); return FM_OK;
     case FM_TUNE_TMA:
-        if (value > 63) return einval("FM_TUNE_TMA is a mask of 1, 2, 4, 8, 16 and 32");
+        if (value > 127) return einval("FM_TUNE_TMA is a mask of 1, 2, 4, 8, 16, 32 and 64");
         g_use_tma.store(value < 0 ? kDefaultTma : (int)value);
         return FM_OK;
     case FM_TUNE_TILE:

@@ -66,6 +66,23 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
         : "memory");
 }
+// box of shared memory (128-byte aligned, written by this CTA's threads and
+// made visible to the async proxy with fence_async_smem) to a 3-D tensor map
+// at (x, y, z) >= 0; completion tracked by the issuing thread's bulk group
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int x, int y, int z, const void *src)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the issuing thread waits until its committed bulk stores are complete
+// (their shared-memory sources read and their writes performed); the CTA
+// must not exit before the sources have been read
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 // every thread polls phase `parity` of bar; false (for the whole CTA) when
 // the bound ran out, after flagging it.  Every thread of the CTA must call it.
 __device__ __forceinline__ bool tma_wait_all(uint64_t *bar, uint32_t parity)

@@ -66,7 +66,7 @@ def test_bulk_copy_rows_equal_thread_loads(n, batch):
     g1 = torch.empty((batch, n, n), device="cuda").normal_(0, 0.1)
     g2 = torch.empty_like(g1).normal_(0, 0.1)
     outs = {}
-    for tma in (63, 0):
+    for tma in (127, 0):
         fm.fm_tune(fm.FM_TUNE_TMA, tma)
         try:
             kE, kB = fm.fm_ks_invert(g1, g2, with_b=True)
@@ -76,5 +76,5 @@ def test_bulk_copy_rows_equal_thread_loads(n, batch):
             fm.fm_tune(fm.FM_TUNE_TMA, -1)
     torch.cuda.synchronize()
     assert fm.fm_device_error() == 0
-    for a, b in zip(outs[63], outs[0]):
+    for a, b in zip(outs[127], outs[0]):
         assert torch.equal(a, b)
