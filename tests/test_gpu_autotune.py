@@ -42,3 +42,35 @@ def test_autotuned_plan_is_used_and_matches_oracle(fm, n, J, batch, dtype):
     kappa = oracle.ks_invert(g1b[-1].astype(np.float64), g2b[-1].astype(np.float64))[0]
     ref = oracle.starlet(kappa, J)
     assert max(band_errs(auto[-1].cpu().numpy(), ref)) <= TOL[dtype]
+
+
+def test_hand_set_plan_drives_every_automatic_choice(fm):
+    """A plan entered by hand (shared-buffer tile form, fused column/row
+    path, 40 MiB chunks, one fused scale) is what the automatic
+    configuration runs: bit-identical to the same choices made explicitly,
+    within tolerance of the oracle, and for the noise maps too."""
+    n, J, batch = 512, 6, 6
+    g1, g2 = shear(n, seed=5, dtype=np.float32)
+    t1 = torch.from_numpy(np.stack([np.roll(g1, 11 * b, axis=1) for b in range(batch)])).cuda()
+    t2 = torch.from_numpy(np.stack([np.roll(g2, 11 * b, axis=1) for b in range(batch)])).cuda()
+    fm.fm_autotune_set(n, J, fuse_depth=1, large_path=3, tile=0, chunk_mb=40)
+    auto = fm.fm_map_starlet(t1, t2, J)
+    fm.fm_autotune_clear()
+    fm.fm_tune(fm.FM_TUNE_TILE, 0)
+    fm.fm_tune(fm.FM_TUNE_CHUNK_BYTES, 40 << 20)
+    try:
+        explicit = fm.fm_map_starlet(t1, t2, J, fuse_depth=1, large_path=3)
+    finally:
+        fm.fm_tune(fm.FM_TUNE_TILE, -1)
+        fm.fm_tune(fm.FM_TUNE_CHUNK_BYTES, -1)
+    assert torch.equal(auto, explicit)
+    kappa = oracle.ks_invert(np.roll(g1, 11 * (batch - 1), axis=1).astype(np.float64),
+                             np.roll(g2, 11 * (batch - 1), axis=1).astype(np.float64))[0]
+    assert max(band_errs(auto[-1].cpu().numpy(), oracle.starlet(kappa, J))) <= TOL[np.float32]
+    # noise maps follow the plan as well and stay within the variance bound
+    fm.fm_autotune_set(n, J, fuse_depth=1, large_path=3, tile=0, chunk_mb=40)
+    var, _ = fm.fm_map_noise(t1[0], t2[0], J, 5, seed=8, with_snr=False)
+    rv, _ = oracle.map_noise(g1.astype(np.float64), g2.astype(np.float64), J, 5, 8, with_snr=False)
+    var = var.cpu().numpy()
+    for j in range(J - 1):
+        assert np.abs(var[j] - rv[j]).max() / rv[j].mean() <= 1e-4
