@@ -35,6 +35,15 @@ METRIC = "starlet Map Mpix*scales/s, batched FP32 vs plain FP64 (<=1e-5 err); %H
 UNIT = "Mpix*scales/s"
 L2_BYTES = 129 * 2 ** 20
 
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # unit counts x maximum SM clock
+
+
+def disc_taps(R):
+    """Lattice offsets d with 0 < |d| <= R: the taps of the direct sum."""
+    Ri = int(np.floor(R))
+    return sum(2 * int(np.floor(np.sqrt(R * R - dy * dy))) + 1 for dy in range(-Ri, Ri + 1)) - 1
+
+
 def algo_bytes_per_px_launch(kernel, fuse):
     """Algorithmic bytes per map pixel that one launch of `kernel` moves
     (fp32): what the kernel must read and write once.  FFT passes move
@@ -283,10 +292,17 @@ def side_legs(fm, torch, n, J, g1, g2):
         reps = 3 if theta >= 32 else 5
         t_s98 = cuda_time(torch, lambda: fm.fm_map_direct(s1, s2, fm.FM_FILTER_S98, theta), reps)
         t_stq = cuda_time(torch, lambda: fm.fm_map_direct(s1, s2, fm.FM_FILTER_STARLET, theta), reps)
+        # the direct sum is FP32-FMA bound: 4 flops per tap (A gamma1 + B gamma2)
+        tf_s98 = 4.0 * disc_taps(theta) * n * n / (t_s98 * 1e-3) / 1e12
+        tf_stq = 4.0 * disc_taps(2 * theta) * n * n / (t_stq * 1e-3) / 1e12
         rows.append({"theta_px": theta, "J": Jj, "starlet_ms": t_st, "ks_starlet_ms": t_ks,
                      "map_s98_cut_theta_ms": t_s98, "map_starletQ_cut_2theta_ms": t_stq,
-                     "speedup_vs_s98": t_s98 / t_st, "speedup_ks_starlet_vs_s98": t_s98 / t_ks})
+                     "speedup_vs_s98": t_s98 / t_st, "speedup_ks_starlet_vs_s98": t_s98 / t_ks,
+                     "s98_tflops": tf_s98, "starletQ_tflops": tf_stq,
+                     "s98_alu_frac": tf_s98 / FP32_PEAK_TFLOPS, "starletQ_alu_frac": tf_stq / FP32_PEAK_TFLOPS})
     out["direct_map"] = rows
+    out["direct_map_alu_peak"] = {"tflops": FP32_PEAK_TFLOPS, "source": "derived: 152 SMs x 128 FP32 lanes x 2 flops "
+                                  "(FMA) x 2.07 GHz maximum SM clock"}
     # weighted direct M_ap on a field with 15 % masked (stars + a bad column)
     from paper_1204_4293_gb300 import synth
     wmask = torch.from_numpy(synth.star_mask(n, frac=0.15, seed=7).astype(np.float32)).cuda()
