@@ -162,8 +162,9 @@ cudaError_t smem_attr(const void *kernel, size_t bytes);
 // ---- internal launchers (defined per .cu file) ------------------------------------
 int launch_ks(const void *in1, const void *in2, long in_bstride, void *out1, void *out2, void *work, int n, int batch,
               int precision, bool forward, uint64_t rot_seed, int rot_r0, bool rotate, cudaStream_t s);
+// bands_only: the smooth array c_{J-1} is not written (noise realisations)
 int launch_starlet(const void *kappa, void *pyr, long pyr_bstride, int n, int J, int batch, const fm_config &cfg,
-                   void *scratch, cudaStream_t s);
+                   void *scratch, cudaStream_t s, bool bands_only = false);
 int launch_ks32(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int n,
                 int batch, bool forward, uint64_t seed, int r0, bool rotate, const float2 *tw, cudaStream_t s);
 // Spectral operation of the column pass of the 2-D FFT pipeline

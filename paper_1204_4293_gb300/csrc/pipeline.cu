@@ -105,7 +105,8 @@ int run_chunk(const char *g1, const char *g2, char *pyr, int n, int J, int b0, i
     int r = launch_ks(g1 + in_off, g2 + in_off, rotate ? 0 : (long)nn, kap, nullptr, work, n, bc, cfg.precision, false,
                       seed, r0, rotate, s);
     if (r != FM_OK) return r;
-    return launch_starlet(kap, pyr + (size_t)b0 * J * nn * es, (long)J * nn, n, J, bc, cfg, st, s);
+    // a noise realisation needs its bands only (the smooth array is not accumulated)
+    return launch_starlet(kap, pyr + (size_t)b0 * J * nn * es, (long)J * nn, n, J, bc, cfg, st, s, rotate);
 }
 
 // All chunks, forked from `origin` onto the internal streams (round robin

@@ -1074,7 +1074,7 @@ static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 template <typename T>
 static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int batch, const fm_config &cfg,
-                        T *scratch, cudaStream_t s)
+                        T *scratch, cudaStream_t s, bool bands_only)
 {
     constexpr int VW = 16 / sizeof(T);
     constexpr int KR = 8;
@@ -1086,7 +1086,7 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
     T *last = pyr + (long)(J - 1) * nn;  // slot of the smooth array
     const bool vec_ok = n % VW == 0 && aligned16(kappa) && aligned16(pyr) && (!scratch || aligned16(scratch));
     if (f >= 1) {
-        T *c_out = f == J - 1 ? last : A;
+        T *c_out = f == J - 1 ? (bands_only ? nullptr : last) : A;
         const long c_bs = f == J - 1 ? pyr_bs : nn;
         int tvar = g_tile_variant.load(std::memory_order_relaxed);
         if (tvar < 0) {
@@ -1154,7 +1154,7 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
     for (int j = f + 1; j <= J - 1; ++j) {
         const int sp = 1 << (j - 1);
         const T *c_prev = j == 1 ? kappa : A;
-        T *c_next = j == J - 1 ? last : A;
+        T *c_next = j == J - 1 ? (bands_only ? nullptr : last) : A;
         const long next_bs = j == J - 1 ? pyr_bs : nn;
         T *rj = r_in_last(j) ? last : Bb;
         const long rj_bs = r_in_last(j) ? pyr_bs : nn;
@@ -1208,13 +1208,13 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
 }
 
 int launch_starlet(const void *kappa, void *pyr, long pyr_bstride, int n, int J, int batch, const fm_config &cfg,
-                   void *scratch, cudaStream_t s)
+                   void *scratch, cudaStream_t s, bool bands_only)
 {
     if (cfg.precision == FM_F64)
         return starlet_impl<double>((const double *)kappa, (double *)pyr, pyr_bstride, n, J, batch, cfg,
-                                    (double *)scratch, s);
+                                    (double *)scratch, s, bands_only);
     return starlet_impl<float>((const float *)kappa, (float *)pyr, pyr_bstride, n, J, batch, cfg, (float *)scratch,
-                               s);
+                               s, bands_only);
 }
 
 }  // namespace fm
