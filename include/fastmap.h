@@ -276,6 +276,12 @@ int fm_device_error(void);
  *   FM_TUNE_TILE         fp32 kernel of the fused small starlet scales:
  *                        0 = row-filtered shared buffer, 1 = register
  *                        window; default: the autotuned plan's, else 1
+ *   FM_TUNE_WAIT_TEST    test hook of the bounded-wait path: 1 = the fused
+ *                        tile kernel's halo copy announces 16 bytes more than
+ *                        it delivers, so every interior tile's wait runs out
+ *                        (within about 0.1 s), the tile leaves its outputs
+ *                        unwritten and fm_device_error reports 1; 0 = off
+ *                        (default)
  * FM_TUNE_CHUNK_BYTES set this way also overrides autotuned budgets. */
 #define FM_TUNE_CHUNK_BYTES 1
 #define FM_TUNE_GRAPHS 2
@@ -283,6 +289,7 @@ int fm_device_error(void);
 #define FM_TUNE_PDL 4
 #define FM_TUNE_TILE 5
 #define FM_TUNE_TMA 6
+#define FM_TUNE_WAIT_TEST 7
 int fm_tune(int knob, int64_t value);
 
 /* ---- autotuner ----------------------------------------------------------------

@@ -48,6 +48,9 @@ extern std::atomic<int> g_tile_variant;
 constexpr int kDefaultTma = 127;
 extern std::atomic<int> g_use_tma;
 extern std::atomic<int> g_prof_kid;  // kernel id whose launches are being timed (0: none)
+// test hook (FM_TUNE_WAIT_TEST): the fused tile kernel's bulk copy waits for
+// more bytes than arrive, so its bounded wait runs out and is flagged
+extern std::atomic<int> g_wait_test;
 // 1 if a kernel of that file gave up waiting on a bulk copy (see fm_device_error)
 int starlet_wait_error(bool clear);
 int fft_wait_error(bool clear);

@@ -187,7 +187,7 @@ static int map_starlet_dev(const void *g1, const void *g2, void *pyramid, int n,
         return run_chunks(g1, g2, pyramid, n, J, batch, cfg, p, (char *)sc.p, s, *ds);
     }
     GraphKey key{g1, g2, pyramid, n, J, batch, 0, cfg, p.C, p.slots,
-                 g_pdl.load() | ((g_tile_variant.load() + 1) << 1) | (g_use_tma.load() << 3)};
+                 g_pdl.load() | ((g_tile_variant.load() + 1) << 1) | (g_use_tma.load() << 3) | (g_wait_test.load() << 10)};
     FM_CUDA_TRY(cudaGetDevice(&key.dev));
     GraphEntry *hit = nullptr;
     for (auto &e : g_graphs)
@@ -379,7 +379,7 @@ int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out
     DevStreams *ds = nullptr;
     if ((st = dev_streams(&ds))) return st;
     NoiseKey key{g1, g2, var_out, snr_out, n, J, R, 0, seed, cfg, L.p.C, L.slots,
-                 g_pdl.load() | ((g_tile_variant.load() + 1) << 1) | (g_use_tma.load() << 3)};
+                 g_pdl.load() | ((g_tile_variant.load() + 1) << 1) | (g_use_tma.load() << 3) | (g_wait_test.load() << 10)};
     FM_CUDA_TRY(cudaGetDevice(&key.dev));
     NoiseGraph *hit = nullptr;
     for (auto &e : g_noise_graphs)
@@ -514,6 +514,7 @@ int fm_tune(int knob, int64_t value)
         if (value > 127) return einval("FM_TUNE_TMA is a mask of 1, 2, 4, 8, 16, 32 and 64");
         g_use_tma.store(value < 0 ? kDefaultTma : (int)value);
         return FM_OK;
+    case FM_TUNE_WAIT_TEST: g_wait_test.store(value > 0 ? 1 : 0); return FM_OK;
     case FM_TUNE_TILE:
         if (value > 1) return einval("FM_TUNE_TILE takes 0 or 1");
         g_tile_variant.store(value < 0 ? -1 : (int)value);

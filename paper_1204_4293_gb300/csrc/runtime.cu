@@ -42,6 +42,7 @@ std::atomic<int64_t> g_launches{0};
 std::atomic<int> g_pdl{1};
 std::atomic<int> g_tile_variant{-1};
 std::atomic<int> g_use_tma{kDefaultTma};
+std::atomic<int> g_wait_test{0};
 
 namespace {
 struct Prof {

@@ -482,12 +482,14 @@ __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3)
     const bool vok = vec_ok != 0;
 
     const bool interior = vok && ty0 >= HP && tx0 >= HP && ty0 + TS + HP <= n && tx0 + TS + HP <= n;
-    if (interior && use_tma) {
+    if (interior && (use_tma & 1)) {
         // one bulk tensor copy of the P x P halo box, completion on the mbarrier
+        // (use_tma bit 1, a test hook: 16 bytes more are announced than the
+        // copy delivers, so the bounded wait runs out and is flagged)
         if (threadIdx.x == 0) mbar_init(bar, 1);
         __syncthreads();
         if (threadIdx.x == 0) {
-            mbar_expect_tx(bar, (uint32_t)(P * P * sizeof(float)));
+            mbar_expect_tx(bar, (uint32_t)(P * P * sizeof(float)) + ((use_tma & 2) ? 16u : 0u));
             tma_load_3d(b0, &tmap, tx0 - HP, ty0 - HP, (int)b, bar);
         }
         if (!tma_wait_all(bar, 0)) return;  // the copy never completed (flagged)
@@ -1031,8 +1033,9 @@ static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, fl
         const uint64_t dims[3] = {(uint64_t)n, (uint64_t)n, (uint64_t)batch};
         const uint64_t strides[2] = {(uint64_t)n * 4, (uint64_t)n * n * 4};
         const uint32_t box[3] = {(uint32_t)P, (uint32_t)P, 1};
-        const int use_tma = (g_use_tma.load(std::memory_order_relaxed) & 1) && vec_ok && n >= 2 * TS + 2 * HP &&
-                            encode_map3d_f32(&map, in, dims, strides, box);
+        int use_tma = (g_use_tma.load(std::memory_order_relaxed) & 1) && vec_ok && n >= 2 * TS + 2 * HP &&
+                      encode_map3d_f32(&map, in, dims, strides, box);
+        if (use_tma && g_wait_test.load(std::memory_order_relaxed)) use_tma |= 2;
         if (!use_tma) memset(&map, 0, sizeof(map));
         FM_LAUNCH(FM_K_STARLET_TILE, k, (unsigned)(tiles_per_map * (long)batch), 256, smem2, s, in, (long)n * n,
                   w_out, w_bs, w_ss, c_out, c_bs, n, boundary, tiles_x, tiles_per_map, vec_ok ? 1 : 0, map,

@@ -83,12 +83,30 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 // must not exit before the sources have been read
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // every thread polls phase `parity` of bar; false (for the whole CTA) when
 // the bound ran out, after flagging it.  Every thread of the CTA must call it.
+// A few blocking polls (try_wait may suspend the thread for a system-defined
+// time) and then non-blocking polls 64 ns apart, so that a wait that runs out
+// ends after about 2^20 x 64 ns = 0.07 s whatever that suspend time is.
 __device__ __forceinline__ bool tma_wait_all(uint64_t *bar, uint32_t parity)
 {
     bool done = false;
-    for (int it = 0; it < kMaxWaitIters && !done; ++it) done = mbar_try_wait(bar, parity);
+    for (int it = 0; it < 8 && !done; ++it) done = mbar_try_wait(bar, parity);
+    for (int it = 0; it < kMaxWaitIters && !done; ++it) {
+        __nanosleep(64);
+        done = mbar_test_wait(bar, parity);
+    }
     if (__syncthreads_or(!done)) {
         if (threadIdx.x == 0) atomicExch(&g_wait_error, 1);
         return false;

@@ -283,6 +283,7 @@ def fm_map_noise(g1, g2, J, R, seed, boundary=FM_MIRROR, with_snr=True, fuse_dep
 
 
 FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS, FM_TUNE_CHUNK_STREAMS, FM_TUNE_PDL, FM_TUNE_TILE, FM_TUNE_TMA = 1, 2, 3, 4, 5, 6
+FM_TUNE_WAIT_TEST = 7
 
 
 def fm_tune(knob: int, value: int) -> None:

@@ -136,3 +136,35 @@ def test_noise_graph_cache_eviction():
             v, snr = fm.fm_map_noise(g1, g2, J, R, seed=s)
             assert torch.equal(v, v_ref) and torch.equal(snr, snr_ref)
     fm.fm_trim()
+
+
+def test_bounded_wait_runs_out_and_is_reported():
+    """Failure detection without a GPU fault: the FM_TUNE_WAIT_TEST hook makes
+    the fused tile kernel's halo copy announce more bytes than it delivers,
+    so every interior tile's bounded wait runs out.  The call still returns
+    FM_OK, the device stays usable, fm_device_error reports the timeout once,
+    and the next call is exact again."""
+    import time
+
+    import numpy as np
+
+    from paper_1204_4293_gb300 import synth
+    fm = _fm()
+    kap = torch.from_numpy(synth.grf_kappa(512, seed=3).astype(np.float32)).cuda()
+    ref = fm.fm_starlet_forward(kap, 5)
+    torch.cuda.synchronize()
+    assert fm.fm_device_error() == 0
+    fm.fm_tune(fm.FM_TUNE_WAIT_TEST, 1)
+    try:
+        t0 = time.time()
+        fm.fm_starlet_forward(kap, 5)
+        torch.cuda.synchronize()
+        dt = time.time() - t0
+    finally:
+        fm.fm_tune(fm.FM_TUNE_WAIT_TEST, 0)
+    assert fm.fm_device_error() == 1
+    assert fm.fm_device_error() == 0  # reading cleared it
+    assert dt < 30.0
+    again = fm.fm_starlet_forward(kap, 5)
+    torch.cuda.synchronize()
+    assert torch.equal(again, ref) and fm.fm_device_error() == 0
