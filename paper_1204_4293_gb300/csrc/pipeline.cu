@@ -245,14 +245,14 @@ struct NoiseLayout {
     size_t acc_b = 0, pyr_b = 0, total = 0;
 };
 constexpr int kNoisePyrBufs = 2;
-constexpr long kNoisePyrBatchBytes = 4L << 30;  // pyramids of one accumulation batch
+constexpr long kNoisePyrBatchBytes = 8L << 30;  // pyramids of one accumulation batch
 
-// A batch's pyramids stay within 4 GiB (at most 32 realisations: the
+// A batch's pyramids stay within 8 GiB (at most 32 realisations: the
 // accumulation's partial sums are fp32 over at most 32 terms).  Each batch
 // re-reads and re-writes the FP64 sums (32 bytes per band pixel), so large
 // maps need several realisations per batch: with 1 GiB a 4096^2 J = 10 map
-// had one, and R = 100 took 273 ms; with 4 GiB (six) 116 ms, and the
-// serving trace's throughput doubled (3.9 -> 8.0 requests/s).
+// had one, and R = 100 took 273 ms; with 4 GiB (six) 116 ms, with 8 GiB
+// (twelve) 102 ms; the serving trace went 3.9 -> 8.0 -> 9.0 requests/s.
 NoiseLayout noise_layout(int n, int J, int R, const fm_config &cfg, bool multi_stream)
 {
     const size_t es = cfg.precision == FM_F64 ? 8 : 4;
