@@ -231,7 +231,7 @@ def cpu_oracle_baseline(n, J, budget_s=12.0):
     with oracle_pool(n, J, procs) as pool:
         oracle_round(pool, procs)  # warm-up (workers load the oracle)
         rounds, dt = 0, 0.0
-        while dt < budget_s and rounds < 20:
+        while dt < budget_s and rounds < 200:
             dt += oracle_round(pool, procs)
             rounds += 1
     maps = rounds * procs
