@@ -27,6 +27,13 @@ namespace fm {
 
 __device__ __forceinline__ int pad32(int a) { return a + (a >> 5); }
 
+// threads of a row-pass CTA (RPC rows of TV threads; one row when TV is
+// larger): 128-thread CTAs overlap better with the other chunk stream's
+// kernels than 256-thread ones (KS + starlet, 256 -> 128: 32 x 1024^2
+// 0.813 -> 0.805 ms, 16 x 2048^2 2.025 -> 1.988, 16 x 4096^2 10.95 -> 10.83,
+// noise R = 1000 at 1024^2 31.1 -> 30.7)
+constexpr int kRowThreads = 128;
+
 template <int LOGN> struct Plan32 {
     static constexpr int N = 1 << LOGN;
     static constexpr int TV = N / 32;                     // threads per vector
@@ -105,7 +112,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__
 {
     pdl_entry();
     using P = Plan32<LOGN>;
-    constexpr int RPC = P::TV >= 256 ? 1 : 256 / P::TV;
+    constexpr int RPC = P::TV >= kRowThreads ? 1 : kRowThreads / P::TV;
     extern __shared__ __align__(16) float2 sm32[];
     __shared__ uint64_t bar;
     float2 *smb = align128<float2>(sm32);
@@ -179,7 +186,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_inv32(const float2 *__restrict_
 {
     pdl_entry();
     using P = Plan32<LOGN>;
-    constexpr int RPC = P::TV >= 256 ? 1 : 256 / P::TV;
+    constexpr int RPC = P::TV >= kRowThreads ? 1 : kRowThreads / P::TV;
     extern __shared__ __align__(16) float2 sm32[];
     __shared__ uint64_t bar;
     float2 *smb = align128<float2>(sm32);
@@ -336,7 +343,7 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
                      const float2 *tw, cudaStream_t s)
 {
     using P = Plan32<LOGN>;
-    constexpr int RPC = P::TV >= 256 ? 1 : 256 / P::TV;
+    constexpr int RPC = P::TV >= kRowThreads ? 1 : kRowThreads / P::TV;
     const long total_rows = (long)batch * P::N;
     const unsigned row_grid = (unsigned)((total_rows + RPC - 1) / RPC);
     // exchange buffer (which also stages the TMA rows: RPC n floats per input
