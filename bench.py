@@ -267,8 +267,9 @@ def run_reference(args):
     return 0
 
 
-def side_legs(fm, torch, n, J, g1, g2):
-    """Plain FP64 form, direct M_ap per radius, batched noise maps."""
+def side_legs(fm, torch, n, J, g1, g2, pyr):
+    """Plain FP64 form (and the batched FP32 step's error against it),
+    direct M_ap per radius, batched noise maps."""
     out = {}
     # plain form: one map per launch, FP64, one scale per pass (no fusion)
     p1 = g1[0].double().contiguous()
@@ -277,8 +278,13 @@ def side_legs(fm, torch, n, J, g1, g2):
     fn = lambda: fm.fm_map_starlet(p1, p2, J, fuse_depth=-1, out=pyr64)  # noqa: E731
     fn()
     ms = cuda_time(torch, fn, 5)
+    # error of the batched FP32 step's first map against the plain FP64 form, per band:
+    # max |w_fp32 - w_fp64| / RMS(w_fp64)
+    fn()
+    errs = [float((pyr[0, j].double() - pyr64[j]).abs().max() / pyr64[j].pow(2).mean().sqrt()) for j in range(J)]
     out["plain_fp64"] = {"value": n * n * J / (ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_map": ms,
-                         "form": "one map per call, FP64, unfused (one starlet scale per pass)"}
+                         "form": "one map per call, FP64, unfused (one starlet scale per pass)",
+                         "fp32_err_per_band": errs, "fp32_max_err": max(errs)}
     # direct M_ap vs starlet per aperture radius (Fig. 4 analogue), fp32, one map
     s1, s2 = g1[0].contiguous(), g2[0].contiguous()
     kap, _ = fm.fm_ks_invert(s1.unsqueeze(0), s2.unsqueeze(0))
@@ -608,7 +614,7 @@ def main():
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_side:
-        extras = side_legs(fm, torch, n, J, g1, g2)
+        extras = side_legs(fm, torch, n, J, g1, g2, pyr)
     if sampler:
         sampler.stop()
 
@@ -648,6 +654,7 @@ def main():
         line.update(extras)
         if "plain_fp64" in extras:
             line["batched_fp32_over_plain_fp64"] = value / extras["plain_fp64"]["value"]
+            line["fp32_max_err_vs_plain_fp64"] = extras["plain_fp64"]["fp32_max_err"]
         if not args.no_cpu and world == 1:
             line["cpu_baseline"] = cpu_oracle_baseline(n, J)
             if not args.no_side:
