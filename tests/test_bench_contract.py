@@ -31,3 +31,19 @@ def test_reference_arm_non_zero_rank_is_silent():
                          env=env)
     assert out.returncode == 0, out.stderr[-2000:]
     assert not [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_direct_map_tap_count_and_alu_peak():
+    """The direct M_ap roofline counts the lattice offsets 0 < |d| <= R
+    (brute force here) and derives the FP32 FMA peak from unit counts."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    for R in (1.0, 2.0, 3.5, 16.0, 64.0):
+        Ri = int(np.floor(R))
+        d = np.arange(-Ri, Ri + 1)
+        r2 = d[:, None] ** 2 + d[None, :] ** 2
+        assert bench.disc_taps(R) == int(((r2 > 0) & (r2 <= R * R)).sum())
+    assert abs(bench.FP32_PEAK_TFLOPS - 152 * 128 * 2 * 2.07) < 1e-6
+    assert bench.algo_bytes_per_px_launch("starlet_tile", 2) == 16
+    assert bench.algo_bytes_per_px_launch("starlet_col", 2) == 16 and bench.algo_bytes_per_px_launch("starlet_row", 3) == 8
