@@ -44,6 +44,6 @@ def test_direct_map_tap_count_and_alu_peak():
         d = np.arange(-Ri, Ri + 1)
         r2 = d[:, None] ** 2 + d[None, :] ** 2
         assert bench.disc_taps(R) == int(((r2 > 0) & (r2 <= R * R)).sum())
-    assert abs(bench.FP32_PEAK_TFLOPS - 152 * 128 * 2 * 2.07) < 1e-6
+    assert abs(bench.FP32_PEAK_TFLOPS - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
     assert bench.algo_bytes_per_px_launch("starlet_tile", 2) == 16
     assert bench.algo_bytes_per_px_launch("starlet_col", 2) == 16 and bench.algo_bytes_per_px_launch("starlet_row", 3) == 8
