@@ -167,13 +167,15 @@ int fm_map_direct_masked(const void *g1, const void *g2, const void *weight, lon
  * the unbiased variance of each band over the R realisations (R >= 2);
  * snr_out (element type, same shape, or NULL) receives w_j(data)/sigma_j.
  * One map; n a power of two.  Realisations run in batches of up to 32 (the
- * batch's pyramids within 1 GiB); each batch goes through KS and the starlet
- * in L2-sized chunks alternating over the library's streams, then one pass
- * adds its bands to the FP64 sums.  The whole call is recorded once into a
+ * batch's pyramids within 8 GiB); each batch goes through KS and the starlet
+ * (bands only) in L2-sized chunks alternating over the library's streams,
+ * then one pass adds its bands to the FP64 sums (or, with cfg->accum = 1,
+ * to fp32 sums with Kahan compensation) while the chunks run on into the
+ * next batch (two pyramid buffers).  The whole call is recorded once into a
  * CUDA graph (keyed by pointers, sizes, R, seed, config and chunk plan) and
- * replayed as one launch.  Scratch: 16 (J-1) bytes per pixel of FP64 sums,
- * the batch's pyramids and the chunks' intermediates, kept with the graph
- * until fm_trim or eviction. */
+ * replayed as one launch.  Scratch: 16 (J-1) bytes per pixel of sums, the
+ * batches' pyramids and the chunks' intermediates, kept with the graph until
+ * fm_trim or eviction. */
 int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
                  const fm_config *cfg, void *stream);
 
