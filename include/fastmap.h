@@ -179,6 +179,22 @@ int fm_map_direct_masked(const void *g1, const void *g2, const void *weight, lon
 int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
                  const fm_config *cfg, void *stream);
 
+/* Noise maps in parts, for checkpoint / resume or realisations split over
+ * GPUs.  fm_map_noise_accumulate adds realisations r0 .. r0 + R - 1 (the
+ * generator of fm_map_noise) to `sums` = [2][J-1][n][n] doubles (S1 = sum w,
+ * then S2 = sum w^2; zero them before the first part): sums from disjoint
+ * ranges add, on one device or after copying between devices.  Runs on the
+ * caller's stream with stream-ordered scratch; cfg->accum must be 0.
+ * fm_noise_finalize turns sums of R_total >= 2 realisations into the
+ * variance var_out [(J-1)][n][n] (double) and, when snr_out is given, S/N =
+ * w_j(data) / sigma_j from the data's pyramid [J][n][n] (fm_map_starlet of the
+ * same map, element type).  The variance equals fm_map_noise's up to the
+ * grouping of the fp32 partial sums (~1e-7 relative). */
+int fm_map_noise_accumulate(const void *g1, const void *g2, double *sums, int n, int J, int r0, int R, uint64_t seed,
+                            const fm_config *cfg, void *stream);
+int fm_noise_finalize(const double *sums, const void *pyramid, double *var_out, void *snr_out, int n, int J,
+                      int R_total, const fm_config *cfg, void *stream);
+
 /* ---- exact expected noise variance (Sec. 1) -----------------------------------
  * The expectation of fm_map_noise's variance over the random rotation: with a
  * uniform phase per pixel, Var[w_j(x)] = 1/2 sum_y |K_j(x - y)|^2 |gamma(y)|^2,

@@ -197,6 +197,38 @@ int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out,
     return map_noise_run(g1, g2, var_out, snr_out, n, J, R, seed, cfg, (cudaStream_t)stream, true);
 }
 
+// Noise maps in parts (checkpoint and resume, or realisations split over
+// GPUs): realisations r0 .. r0 + R - 1 added to the caller's FP64 sums, and
+// the variance (and S/N) from sums of R_total realisations.
+int fm_map_noise_accumulate(const void *g1, const void *g2, double *sums, int n, int J, int r0, int R, uint64_t seed,
+                            const fm_config *cfgp, void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if (cfg.accum != 0) return einval("fm_map_noise_accumulate keeps FP64 sums (accum = 0)");
+    if ((st = check_fft_n(n))) return st;
+    if ((st = check_J(n, J))) return st;
+    if (R < 1 || r0 < 0 || (long)r0 + R > 2147483647L) return einval("need R >= 1, r0 >= 0, r0 + R < 2^31");
+    if (!g1 || !g2 || !sums) return einval("null pointer");
+    return map_noise_accumulate_run(g1, g2, sums, n, J, r0, R, seed, cfg, (cudaStream_t)stream);
+}
+
+int fm_noise_finalize(const double *sums, const void *pyramid, double *var_out, void *snr_out, int n, int J,
+                      int R_total, const fm_config *cfgp, void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_cfg(cfg);
+    if (st) return st;
+    if (cfg.accum != 0) return einval("fm_noise_finalize reads FP64 sums (accum = 0)");
+    if (n < 1 || (st = check_J(n, J))) return st ? st : einval("n must be >= 1");
+    if (R_total < 2) return einval("R_total must be >= 2");
+    if (!sums || !var_out) return einval("null pointer");
+    if (snr_out && !pyramid) return einval("S/N needs the data's pyramid");
+    return launch_noise_finalize(sums, snr_out ? pyramid : nullptr, var_out, snr_out, (long)(J - 1) * n * n,
+                                 R_total, cfg.precision, 0, (cudaStream_t)stream);
+}
+
 // Exact expected noise variance (Sec. 1), periodic boundary:
 // Var_j = 1/2 |K_j|^2 (*) |gamma|^2 (circular convolution).  K_j is the
 // pipeline's response to unit shears at pixel 0 (Re K_j from gamma1, -Im K_j

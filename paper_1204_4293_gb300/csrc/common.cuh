@@ -209,6 +209,8 @@ size_t noise_scratch_bytes(int n, int J, int R, const fm_config &cfg, bool with_
 size_t map_starlet_scratch_bytes(int n, int J, int batch, const fm_config &cfg);
 int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
                   const fm_config &cfg, cudaStream_t s, bool allow_graph);
+int map_noise_accumulate_run(const void *g1, const void *g2, double *sums, int n, int J, int r0, int R, uint64_t seed,
+                             const fm_config &cfg, cudaStream_t s);
 int launch_modulus2(const void *a, long a_bs, const void *b, long b_bs, void *out, long nn, int count, int precision,
                     cudaStream_t s);
 int launch_unit_shears(void *g1d, void *g2d, long nn, int precision, cudaStream_t s);

@@ -279,19 +279,24 @@ NoiseLayout noise_layout(int n, int J, int R, const fm_config &cfg, bool multi_s
 // buffers alternate so that the chunk streams run on into the next batch
 // while `s` accumulates (R = 1000 at 1024^2: 32.2 -> 31.6 ms; the
 // accumulation's pyramid loads are streaming, evict-first: 31.5 ms).
+// ext_sums (partial accumulation): the caller's FP64 sums, added to without
+// zeroing and without the S/N pass and finalize; realisations rbase ..
+// rbase + R - 1.
 int noise_submit(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
-                 const fm_config &cfg, const NoiseLayout &L, char *scr, cudaStream_t s, DevStreams *ds)
+                 const fm_config &cfg, const NoiseLayout &L, char *scr, cudaStream_t s, DevStreams *ds,
+                 double *ext_sums = nullptr, int rbase = 0)
 {
     const size_t es = cfg.precision == FM_F64 ? 8 : 4;
     const long nn = (long)n * n;
     const long nb = (long)(J - 1) * nn;
-    void *acc = scr;  // FP64 S1, S2 or the fp32 Kahan pairs: 16 bytes per band pixel either way
+    void *acc = ext_sums ? static_cast<void *>(ext_sums) : static_cast<void *>(scr);  // FP64 S1, S2 or the fp32
+                                                                                       // Kahan pairs: 16 B / band px
     char *pyr = scr + L.acc_b, *slots = pyr + (size_t)L.pyr_bufs * L.pyr_b;
     const ChunkPlan &p = L.p;
     const bool multi = ds && L.slots > 1;
     const char *c1 = static_cast<const char *>(g1), *c2 = static_cast<const char *>(g2);
     int r;
-    FM_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)2 * nb * sizeof(double), s));
+    if (!ext_sums) FM_CUDA_TRY(cudaMemsetAsync(acc, 0, (size_t)2 * nb * sizeof(double), s));
     for (int r0 = 0, ib = 0; r0 < R; r0 += L.batch, ++ib) {
         const int b = R - r0 < L.batch ? R - r0 : L.batch;
         const int buf = ib % L.pyr_bufs;
@@ -309,7 +314,7 @@ int noise_submit(const void *g1, const void *g2, double *var_out, void *snr_out,
             const int k = multi ? i % L.slots : 0;
             const int bc = b - c0 < p.C ? b - c0 : p.C;
             if ((r = run_chunk(c1, c2, pb + (size_t)c0 * J * nn * es, n, J, 0, bc, cfg, p, slots + k * p.slot_b,
-                               multi ? ds->s[k] : s, true, seed, r0 + c0)))
+                               multi ? ds->s[k] : s, true, seed, rbase + r0 + c0)))
                 return r;
         }
         if (multi)
@@ -320,6 +325,7 @@ int noise_submit(const void *g1, const void *g2, double *var_out, void *snr_out,
         if ((r = launch_noise_accum(pb, b, (long)J * nn, nn, J - 1, acc, cfg.precision, cfg.accum, s))) return r;
         if (multi && L.pyr_bufs > 1) FM_CUDA_TRY(cudaEventRecord(ds->acc[buf], s));
     }
+    if (ext_sums) return FM_OK;
     // S/N needs the unrotated bands; finalize reads them from the first pyramid
     // (every chunk stream has joined `s` after the last batch)
     if (snr_out && (r = run_chunk(c1, c2, pyr, n, J, 0, 1, cfg, p, slots, s))) return r;
@@ -424,6 +430,19 @@ int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out
     FM_CUDA_TRY(cudaGraphLaunch(hit->exec, s));
     g_launches.fetch_add(hit->kernels);
     return FM_OK;
+}
+
+// Realisations r0 .. r0 + R - 1 added to the caller's FP64 sums, on `s`
+// (one stream, stream-ordered scratch).
+int map_noise_accumulate_run(const void *g1, const void *g2, double *sums, int n, int J, int r0, int R, uint64_t seed,
+                             const fm_config &cfg, cudaStream_t s)
+{
+    int st = FM_OK;
+    if (!twiddles(n, cfg.precision, s, &st)) return st;
+    const NoiseLayout L = noise_layout(n, J, R, cfg, false);
+    Scratch sc;
+    if ((st = scratch_alloc(sc, L.total, s))) return st;
+    return noise_submit(g1, g2, nullptr, nullptr, n, J, R, seed, cfg, L, (char *)sc.p, s, nullptr, sums, r0);
 }
 
 // scratch of a noise call on the caller's stream (the serving path)

@@ -67,6 +67,8 @@ _SIGS = {
     "fm_map_direct_masked": (_I, [_P, _P, _P, ctypes.c_long, _P, _P, _I, _I, _I, _D, _I, _D, _CFG, _P]),
     "fm_map_noise": (_I, [_P, _P, _P, _P, _I, _I, _I, _U64, _CFG, _P]),
     "fm_map_noise_expected": (_I, [_P, _P, _P, _I, _I, _CFG, _P]),
+    "fm_map_noise_accumulate": (_I, [_P, _P, _P, _I, _I, _I, _I, _U64, _CFG, _P]),
+    "fm_noise_finalize": (_I, [_P, _P, _P, _P, _I, _I, _I, _CFG, _P]),
     "fm_band_moments": (_I, [_P, _P, _I, _I, _I, _CFG, _P]),
     "fm_serve_create": (_I, [_SZ, _I, ctypes.POINTER(ctypes.c_void_p)]),
     "fm_serve_submit": (_I, [_P, ctypes.POINTER(fm_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -279,6 +281,42 @@ def fm_map_noise(g1, g2, J, R, seed, boundary=FM_MIRROR, with_snr=True, fuse_dep
     _check(_lib.fm_map_noise(_ptr(g1), _ptr(g2), _ptr(var), _ptr(snr), n, J, int(R),
                              ctypes.c_uint64(int(seed) & (2**64 - 1)), ctypes.byref(c), _stream(stream)),
            "fm_map_noise")
+    return var, snr
+
+
+def fm_map_noise_accumulate(g1, g2, J, r0, R, seed, sums=None, boundary=FM_MIRROR, stream=None):
+    """Add realisations r0 .. r0 + R - 1 to `sums` ([2, J-1, n, n] float64,
+    zeros when None) and return it."""
+    n, batch = _maps(g1, g2)
+    if batch != 1 or g1.dim() != 2:
+        raise ValueError("fm_map_noise_accumulate takes one [n, n] map")
+    if sums is None:
+        sums = torch.zeros((2, J - 1, n, n), dtype=torch.float64, device=g1.device)
+    if sums.shape != (2, J - 1, n, n) or sums.dtype != torch.float64 or not sums.is_contiguous():
+        raise ValueError("sums must be a contiguous [2, J-1, n, n] float64 tensor")
+    c = _cfg(_prec(g1), boundary)
+    _check(_lib.fm_map_noise_accumulate(_ptr(g1), _ptr(g2), _ptr(sums), n, J, int(r0), int(R),
+                                        ctypes.c_uint64(int(seed) & (2**64 - 1)), ctypes.byref(c), _stream(stream)),
+           "fm_map_noise_accumulate")
+    return sums
+
+
+def fm_noise_finalize(sums, R_total, pyramid=None, dtype=torch.float32, stream=None):
+    """(variance [J-1, n, n] float64, S/N or None) from sums of R_total
+    realisations; S/N when the data's pyramid [J, n, n] is given."""
+    if sums.dim() != 4 or sums.shape[0] != 2 or sums.dtype != torch.float64 or not sums.is_contiguous():
+        raise ValueError("sums must be a contiguous [2, J-1, n, n] float64 tensor")
+    J, n = sums.shape[1] + 1, sums.shape[2]
+    var = torch.empty((J - 1, n, n), dtype=torch.float64, device=sums.device)
+    snr = None
+    prec = _prec(pyramid) if pyramid is not None else (FM_F64 if dtype == torch.float64 else FM_F32)
+    if pyramid is not None:
+        if pyramid.shape != (J, n, n) or not pyramid.is_contiguous():
+            raise ValueError("pyramid must be a contiguous [J, n, n] tensor")
+        snr = torch.empty((J - 1, n, n), dtype=pyramid.dtype, device=sums.device)
+    c = _cfg(prec)
+    _check(_lib.fm_noise_finalize(_ptr(sums), _ptr(pyramid), _ptr(var), _ptr(snr), n, J, int(R_total),
+                                  ctypes.byref(c), _stream(stream)), "fm_noise_finalize")
     return var, snr
 
 

@@ -74,6 +74,13 @@ def test_validation_before_any_device_work(fm):
         bad = fm._cfg(prec, accum=acc)
         assert lib.fm_map_noise(1, 1, 1, None, 64, 4, 8, 0, ctypes.byref(bad), None) == fm.FM_EINVAL
         assert b"accum" in lib.fm_last_error()
+    assert lib.fm_map_noise_accumulate(1, 1, None, 64, 4, 0, 3, 0, cfg, None) == fm.FM_EINVAL  # null sums
+    assert lib.fm_map_noise_accumulate(1, 1, 1, 64, 4, -1, 3, 0, cfg, None) == fm.FM_EINVAL  # r0 < 0
+    assert lib.fm_map_noise_accumulate(1, 1, 1, 64, 4, 0, 0, 0, cfg, None) == fm.FM_EINVAL  # R < 1
+    assert lib.fm_noise_finalize(1, None, 1, 1, 64, 4, 10, cfg, None) == fm.FM_EINVAL  # S/N without pyramid
+    assert lib.fm_noise_finalize(1, None, 1, None, 64, 4, 1, cfg, None) == fm.FM_EINVAL  # R_total < 2
+    kahan = fm._cfg(0, accum=1)
+    assert lib.fm_map_noise_accumulate(1, 1, 1, 64, 4, 0, 3, 0, ctypes.byref(kahan), None) == fm.FM_EINVAL
     bad = fm._cfg(0, large_path=4)
     assert lib.fm_starlet_forward(1, 1, 64, 3, 1, ctypes.byref(bad), None) == fm.FM_EINVAL
     h = ctypes.c_void_p()

@@ -105,3 +105,27 @@ def test_noise_kahan_and_fp64_sums_agree_over_many_batches():
         rel = ((vk[j] - v64[j]).abs().max() / v64[j].mean()).item()
         assert rel <= 1e-5, (j, rel)
     fm.fm_trim()
+
+
+def test_noise_in_parts_equals_one_call():
+    """Realisations accumulated in parts (checkpoint / resume, or ranges
+    split over GPUs: the sums of disjoint ranges add) give fm_map_noise's
+    variance and S/N up to the grouping of the fp32 partial sums."""
+    fm = _fm()
+    n, J, R = 128, 5, 40
+    g1, g2 = shear(n, seed=13, dtype=np.float32)
+    t1, t2 = torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda()
+    var, snr = fm.fm_map_noise(t1, t2, J, R, seed=21)
+    sums = fm.fm_map_noise_accumulate(t1, t2, J, 0, 15, seed=21)  # resume after 15 realisations
+    sums = fm.fm_map_noise_accumulate(t1, t2, J, 15, R - 15, seed=21, sums=sums)
+    pyr = fm.fm_map_starlet(t1, t2, J)
+    v2, s2 = fm.fm_noise_finalize(sums, R, pyramid=pyr)
+    a = fm.fm_map_noise_accumulate(t1, t2, J, 0, 20, seed=21)  # two "ranks"
+    b = fm.fm_map_noise_accumulate(t1, t2, J, 20, 20, seed=21)
+    v3, _ = fm.fm_noise_finalize(a + b, R)
+    for j in range(J - 1):
+        ref = var[j].mean().item()
+        assert (v2[j] - var[j]).abs().max().item() / ref <= 1e-5
+        assert (v3[j] - var[j]).abs().max().item() / ref <= 1e-5
+        assert (s2[j] - snr[j]).abs().max().item() / snr[j].pow(2).mean().sqrt().item() <= 1e-4
+    fm.fm_trim()
