@@ -2,7 +2,10 @@
 process per GPU (the maps shard across ranks; no data crosses ranks).
 
 Only two things cross ranks: a barrier around the timed region and one
-scalar all-reduce (max) of the measured time.
+scalar all-reduce (max) of the measured time.  Noise maps can also split
+their realisations: each rank adds its range (noise_range) to partial sums
+with fm_map_noise_accumulate, merge_noise_sums adds the ranks' sums, and one
+rank finalizes them.
 """
 from __future__ import annotations
 
@@ -42,3 +45,18 @@ def max_over_ranks(value: float, device=None) -> float:
 def weak_scaling_value(units_per_rank: float, world: int, seconds: float) -> float:
     """Whole-job throughput: all ranks' units over the slowest rank's time."""
     return units_per_rank * world / seconds
+
+
+def noise_range(total_realisations: int, world: int, rank: int) -> range:
+    """The realisations (generator indices) that `rank` accumulates."""
+    return shard_maps(total_realisations, world, rank)
+
+
+def merge_noise_sums(sums):
+    """Sum of every rank's partial noise sums, in place (one all-reduce of
+    the [2, J-1, n, n] tensor; a no-op on one process)."""
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(sums, op=dist.ReduceOp.SUM)
+    return sums
