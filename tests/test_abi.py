@@ -159,3 +159,26 @@ def test_autotune_table_roundtrip(fm, tmp_path):
             fm.fm_autotune(48, 4, 1)  # not a power of two: refused before any device work
     finally:
         fm.fm_autotune_clear()
+
+
+def test_autotune_json_is_tolerant_of_layout(fm, tmp_path):
+    """The plan table loads JSON written by other tools: any whitespace and key
+    order, numbers in exponent form, the timing fields optional."""
+    fm.fm_autotune_clear()
+    try:
+        path = tmp_path / "hand.json"
+        path.write_text('{\n "entries": [ { "J" : 6, "n": 512, "precision": 0,\n "chunk_mb": 4e1, "tile": 1,'
+                        ' "large_path": 3, "fuse_depth": 2 } ],\n "fastmap_autotune": 1 }\n')
+        fm.fm_autotune_load(path)
+        got = fm.fm_autotune_get(512, 6)
+        assert (got["fuse_depth"], got["large_path"], got["tile"], got["chunk_mb"]) == (2, 3, 1, 40)
+        assert got["ms"] == 0.0 and got["default_ms"] == 0.0
+        assert fm.fm_starlet_fuse_depth(512, 6) == 2
+        path.write_text('{"fastmap_autotune": 1, "entries": []}')
+        fm.fm_autotune_load(path)  # an empty table file merges nothing
+        assert fm.fm_autotune_get(512, 6)["fuse_depth"] == 2
+        missing = tmp_path / "missing.json"
+        with pytest.raises(fm.FastmapError):
+            fm.fm_autotune_load(missing)
+    finally:
+        fm.fm_autotune_clear()
