@@ -42,9 +42,10 @@ def test_ks_forward_matches_oracle(n, dtype):
     assert rel_err(g2.cpu().numpy(), r2) <= TOL[dtype]
 
 
-def test_ks_8192_sampled_rows():
-    # largest supported size: compare rows against the oracle's 1-D definition
-    # via the E/B power identity and a full-size round trip (forward then inverse).
+def test_ks_8192_round_trip():
+    # largest supported size, GPU against itself: forward then inverse gives
+    # kappa back and no B-mode (the oracle comparison at this size is in
+    # test_gpu_pipeline.py)
     fm = _fm()
     from paper_1204_4293_gb300 import synth
     n = 8192

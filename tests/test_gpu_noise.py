@@ -46,6 +46,25 @@ def test_noise_paper_size_few_realisations():
         assert np.abs(var[j] - rv[j]).max() / rv[j].mean() <= 1e-4
 
 
+def test_noise_bench_config_mirror_two_batches():
+    # the noise benchmark's configuration (1024^2, J = 7, mirror boundary,
+    # one graph-replayed fm_map_noise call) at R = 40: a full batch of 32
+    # realisations and a ragged one of 8 in the two alternating pyramid
+    # buffers, as in the R = 1000 run, against the oracle
+    fm = _fm()
+    n, J, R = 1024, 7, 40
+    g1, g2 = shear(n, seed=3, dtype=np.float32)
+    t1, t2 = torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda()
+    fm.fm_map_noise(t1, t2, J, R, seed=3)  # records the graph
+    var, snr = fm.fm_map_noise(t1, t2, J, R, seed=3)  # replays it
+    rv, rs = oracle.map_noise(g1.astype(np.float64), g2.astype(np.float64), J, R, 3, oracle.MIRROR)
+    var, snr = var.cpu().numpy(), snr.cpu().numpy()
+    for j in range(J - 1):
+        assert np.abs(var[j] - rv[j]).max() / rv[j].mean() <= 1e-4, j
+        assert np.abs(snr[j] - rs[j]).max() / np.sqrt(np.mean(rs[j] ** 2)) <= 1e-3, j
+    fm.fm_trim()
+
+
 def test_noise_graph_replay_matches_eager_launches():
     # fm_map_noise records the whole call into a CUDA graph and replays it;
     # the replay, a second replay and eager launches must agree (the

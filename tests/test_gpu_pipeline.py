@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import oracle
-from helpers import TOL, band_errs, shear
+from helpers import TOL, band_errs, rel_err, shear
 
 pytestmark = pytest.mark.gpu
 
@@ -74,6 +74,31 @@ def test_map_starlet_large_field_4096_j9():
     pyr = fm.fm_map_starlet(t1, t2, J)
     ref = oracle.map_starlet(g1.astype(np.float64), g2.astype(np.float64), J)
     errs = band_errs(pyr[0].cpu().numpy(), ref)
+    assert max(errs) <= 1e-5, errs
+
+
+def test_ks_and_starlet_8192_match_oracle():
+    # the largest field of the large-field workload (one 8192^2 map, P(k) ~
+    # k^-2.5, J = 9) in the launch the benchmark times (fm_map_starlet, batch
+    # of one), and the KS inversion alone, against the FP64 oracle in full:
+    # the four-step column strips and their bulk tensor stores exist only at
+    # this size
+    fm = _fm()
+    n, J = 8192, 9
+    g1, g2 = shear(n, seed=56, alpha=2.5, dtype=np.float32)
+    t1, t2 = torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda()
+    kE, kB = fm.fm_ks_invert(t1.unsqueeze(0), t2.unsqueeze(0), with_b=True)
+    pyr = fm.fm_map_starlet(t1.unsqueeze(0), t2.unsqueeze(0), J)
+    torch.cuda.synchronize()
+    assert fm.fm_device_error() == 0
+    d1, d2 = g1.astype(np.float64), g2.astype(np.float64)
+    rE, rB = oracle.ks_invert(d1, d2)
+    assert rel_err(kE[0].cpu().numpy(), rE) <= 1e-5
+    assert rel_err(kB[0].cpu().numpy(), rB) <= 1e-5
+    del kE, kB, rB
+    ref = oracle.starlet(rE, J)  # the oracle's map_starlet is ks_invert then starlet
+    del rE
+    errs = [rel_err(pyr[0, j].cpu().numpy(), ref[j]) for j in range(J)]
     assert max(errs) <= 1e-5, errs
 
 
