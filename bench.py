@@ -74,9 +74,10 @@ def load_peaks():
 
 
 def ncu_traffic(kernel):
-    """DRAM bytes per algorithmic byte of `kernel` from the committed ncu
-    summary (dram__bytes_read + dram__bytes_write over the launch's algorithmic
-    bytes), valid only while the kernel source is unchanged (sha at capture)."""
+    """DRAM bytes (read + write) per map pixel of one launch of `kernel`, from
+    the committed ncu summary (a warm capture of that kernel alone on a small
+    case), valid only while the kernel source is unchanged (sha at capture);
+    None otherwise."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -88,13 +89,81 @@ def ncu_traffic(kernel):
         parts = dict(kv.split("=", 1) for kv in line.split())
         if parts.get("kernel") == kernel:
             rec = parts
-    if not rec:
+    if not rec or "dram_bytes_per_px" not in rec:
         return None
     src = os.path.join(ROOT, "paper_1204_4293_gb300", "csrc", rec["source"])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if sha != rec.get("sha"):
         return None
-    return float(rec["dram_per_algo"])
+    return float(rec["dram_bytes_per_px"])
+
+
+# Method bytes per map pixel of the fast path (fp32), the algorithmic traffic
+# of the steps: Kaiser-Squires reads gamma1, gamma2 and writes kappa (12 B);
+# the starlet reads kappa and writes J arrays (4 (J + 1) B); one unfused large
+# scale reads c_{j-1} and writes c_j and w_j (12 B); the fused tile of F
+# scales reads kappa and writes F bands and c_F (8 + 4 F B).  The floor is
+# what must cross HBM at all: the shear in, the J arrays out (8 + 4 J B).
+def method_groups(J, fuse):
+    """Kernel groups of one KS + starlet step: (kernel kinds, method bytes per
+    pixel per unit of work, units per map)."""
+    return {
+        "ks": (["fft_rows_fwd", "fft_cols_ks", "fft_rows_inv"], 12.0, 1),
+        "starlet_tile": (["starlet_tile"], 8.0 + 4.0 * fuse, 1),
+        "starlet_large_scale": (["starlet_row", "starlet_col", "starlet_colrow"], 12.0, J - 1 - fuse),
+    }
+
+
+def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src):
+    """The roofline of the dominant kernel group on the method bytes above,
+    each group's fraction, and the whole step's.  per_kind: kind -> (device
+    ms per step, launches per step), from CUDA events around each launch."""
+    chunks = per_kind["fft_rows_fwd"][1]  # one row-FFT launch per chunk of maps
+    groups = {}
+    for name, (kinds, bpp, units) in method_groups(J, fuse).items():
+        ks = [k for k in kinds if k in per_kind]
+        if not ks:
+            continue
+        ms = sum(per_kind[k][0] for k in ks)
+        # a unit launch: one chunk's pass of the group over one unit of work
+        # (all of the group's kernels; a large scale is its row and column pass)
+        launches = chunks * units
+        bytes_step = bpp * px_step * units
+        bytes_launch = bytes_step / launches
+        avg_ms = ms / launches
+        achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
+        # the kernels' own reads and writes per unit launch (a large scale's
+        # row pass 8 B/px and column pass 16 B/px through L2 or HBM)
+        kern_bytes = sum(algo_bytes_per_px_launch(k, fuse) for k in ks) * px_step / chunks
+        trf = [ncu_traffic(k) for k in ks]
+        groups[name] = {"kernels": ks, "method_bytes_per_px": bpp * units, "ms_per_step": ms,
+                        "launches_per_step": launches, "avg_launch_ms": avg_ms,
+                        "method_bytes_per_launch": bytes_launch, "achieved_gbs": achieved, "frac": achieved / peak,
+                        "traffic_per_launch": (sum(trf) * px_step / chunks) if all(
+                            t is not None for t in trf) else None,
+                        "kernel_bytes_per_launch": kern_bytes}
+    dom = max(groups, key=lambda g: groups[g]["ms_per_step"])
+    d = groups[dom]
+    bpp_step = 12.0 + 4.0 * (J + 1)
+    floor_bpp = 8.0 + 4.0 * J
+    step_gbs = bpp_step * px_step / (ms_step * 1e-3) / 1e9
+    return {
+        "bound": "hbm", "kernel": f"{dom} ({' + '.join(d['kernels'])})", "achieved": d["achieved_gbs"],
+        "peak": peak, "unit": "GB/s", "frac": d["frac"], "traffic": d["traffic_per_launch"],
+        "peak_source": f"hbm_gbs ({peak_src})",
+        "algorithmic_bytes_per_launch": d["method_bytes_per_launch"], "avg_launch_ms": d["avg_launch_ms"],
+        "launches_per_step": d["launches_per_step"], "kernel_bytes_per_launch": d["kernel_bytes_per_launch"],
+        "bytes_basis": "method bytes per pixel: KS 12, fused tile of F scales 8 + 4F, each unfused large scale 12 "
+                      "(read c_{j-1}, write c_j and w_j), credited to the group's launches together",
+        "fused_scales": fuse,
+        "groups": groups,
+        "step": {"method_bytes_per_px": bpp_step, "achieved": step_gbs, "frac": step_gbs / peak,
+                 "floor_bytes_per_px": floor_bpp, "floor_frac": floor_bpp * px_step / (ms_step * 1e-3) / 1e9 / peak,
+                 "floor_ms": floor_bpp * px_step / (peak * 1e9) * 1e3},
+        "timing": "CUDA events around every launch of the group's kernels on their launch stream; the same steps "
+                  "launched eagerly with the chunks on one stream (graph bypassed, no kernel overlap); the step's "
+                  "figures use the timed graph-replayed steps",
+    }
 
 
 class ClockSampler:
@@ -237,7 +306,24 @@ def cpu_oracle_baseline(n, J, budget_s=12.0):
     maps = rounds * procs
     return {"value": n * n * J * maps / dt / 1e6, "unit": UNIT, "cores": procs, "kind": "oracle",
             "sample": f"{maps} map(s) of {n}x{n}, J={J}, KS + starlet in FP64, {procs} processes (one map each "
-                      f"per round), {dt:.1f} s"}
+                      f"per round), {dt:.1f} s",
+            "single_core": cpu_oracle_single_core(n, J)}
+
+
+def cpu_oracle_single_core(n, J, budget_s=6.0):
+    """The same oracle in this process on one core: maps one after another
+    for ~budget_s of wall time."""
+    import oracle
+    from paper_1204_4293_gb300 import synth
+    g1, g2 = oracle.ks_forward(synth.grf_kappa(n, seed=2))
+    oracle.map_starlet(g1, g2, J)  # warm-up
+    maps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s or maps == 0:
+        oracle.map_starlet(g1, g2, J)
+        maps += 1
+    dt = time.perf_counter() - t0
+    return {"value": n * n * J * maps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{maps} map(s) of {n}x{n}, J={J}, KS + starlet in FP64, one thread, {dt:.1f} s"}
 
 
 # ---------------------------------------------------------------------------
@@ -301,11 +387,20 @@ def side_legs(fm, torch, n, J, g1, g2, pyr):
         # the direct sum is FP32-FMA bound: 4 flops per tap (A gamma1 + B gamma2)
         tf_s98 = 4.0 * disc_taps(theta) * n * n / (t_s98 * 1e-3) / 1e12
         tf_stq = 4.0 * disc_taps(2 * theta) * n * n / (t_stq * 1e-3) / 1e12
+        # the Gaussian filter (JBJ04, b = 1/2) needs a cut well beyond theta
+        # (Sec. 4.3): 5 theta; the paper expects it to cost about ten times
+        # the polynomial filter cut at theta (Sec. 5.1)
+        t_g = cuda_time(torch, lambda: fm.fm_map_direct(s1, s2, fm.FM_FILTER_JBJ04, theta, cut_over_theta=5.0),
+                        2 if theta >= 32 else reps)
+        tf_g = 4.0 * disc_taps(5 * theta) * n * n / (t_g * 1e-3) / 1e12
         rows.append({"theta_px": theta, "J": Jj, "starlet_ms": t_st, "ks_starlet_ms": t_ks,
                      "map_s98_cut_theta_ms": t_s98, "map_starletQ_cut_2theta_ms": t_stq,
+                     "map_jbj04_cut_5theta_ms": t_g, "jbj04_over_s98": t_g / t_s98,
                      "speedup_vs_s98": t_s98 / t_st, "speedup_ks_starlet_vs_s98": t_s98 / t_ks,
-                     "s98_tflops": tf_s98, "starletQ_tflops": tf_stq,
-                     "s98_alu_frac": tf_s98 / FP32_PEAK_TFLOPS, "starletQ_alu_frac": tf_stq / FP32_PEAK_TFLOPS})
+                     "speedup_vs_jbj04": t_g / t_st,
+                     "s98_tflops": tf_s98, "starletQ_tflops": tf_stq, "jbj04_tflops": tf_g,
+                     "s98_alu_frac": tf_s98 / FP32_PEAK_TFLOPS, "starletQ_alu_frac": tf_stq / FP32_PEAK_TFLOPS,
+                     "jbj04_alu_frac": tf_g / FP32_PEAK_TFLOPS})
     out["direct_map"] = rows
     out["direct_map_alu_peak"] = {"tflops": FP32_PEAK_TFLOPS, "source": "derived: 152 SMs x 128 FP32 lanes x 2 flops "
                                   "(FMA) x 2.07 GHz maximum SM clock"}
@@ -589,8 +684,6 @@ def main():
             per_kind[k] = (ms / prof_steps, cnt / prof_steps)
     fm.fm_profile_select(0)
     fm.fm_tune(fm.FM_TUNE_CHUNK_STREAMS, -1)
-    dom = max(per_kind, key=lambda k: per_kind[k][0])
-    dom_ms, dom_cnt = per_kind[dom]
 
     t = torch.tensor([ms_step], device="cuda")
     if world > 1:
@@ -622,11 +715,6 @@ def main():
         peak, peak_src = load_peaks()
         px_step = n * n * B
         fuse = fm.fm_starlet_fuse_depth(n, J)  # the plan's fused depth for this size
-        chunks = per_kind["fft_rows_fwd"][1]  # one row-FFT launch per chunk of maps
-        bytes_launch = algo_bytes_per_px_launch(dom, fuse) * px_step / chunks
-        achieved = bytes_launch * dom_cnt / (dom_ms * 1e-3) / 1e9
-        dom_avg_ms = dom_ms / max(dom_cnt, 1)
-        trf = ncu_traffic(dom)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -637,13 +725,7 @@ def main():
                        "plan": plan if plan else "built-in rules (--no-autotune)",
                        "l2": f"inputs larger than L2: {2 * B * n * n * 4 / 2**20:.0f} MB shear in + "
                              f"{B * J * n * n * 4 / 2**20:.0f} MB pyramid out per step"},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": f"hbm_gbs ({peak_src})",
-                         "traffic": trf * bytes_launch if trf else None,
-                         "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": dom_avg_ms,
-                         "launches_per_step": dom_cnt, "fused_scales": fuse, "timing": "CUDA events around every launch of the "
-                         "kernel on its launch stream; the same steps launched eagerly with the chunks on "
-                         "one stream (graph bypassed, no kernel overlap)"},
+            "roofline": step_roofline(per_kind, px_step, J, fuse, ms_max, peak, peak_src),
             "kernel_breakdown_ms_per_step": {k: v[0] for k, v in per_kind.items()},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * B * n * n * 4,
                     "d2h_bytes_per_step": B * J * n * n * 4, "ms_per_step": float(te.item()),

@@ -184,12 +184,17 @@ int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out,
  * generator of fm_map_noise) to `sums` = [2][J-1][n][n] doubles (S1 = sum w,
  * then S2 = sum w^2; zero them before the first part): sums from disjoint
  * ranges add, on one device or after copying between devices.  Runs on the
- * caller's stream with stream-ordered scratch; cfg->accum must be 0.
+ * caller's stream with stream-ordered scratch (the batches' pyramids and the
+ * chunks' intermediates; none for the sums, which are the caller's);
+ * cfg->accum must be 0.
  * fm_noise_finalize turns sums of R_total >= 2 realisations into the
  * variance var_out [(J-1)][n][n] (double) and, when snr_out is given, S/N =
  * w_j(data) / sigma_j from the data's pyramid [J][n][n] (fm_map_starlet of the
- * same map, element type).  The variance equals fm_map_noise's up to the
- * grouping of the fp32 partial sums (~1e-7 relative). */
+ * same map, element type).  `sums` must be exactly the [2][J-1][n][n]
+ * doubles that fm_map_noise_accumulate wrote for the same n and J (n a power
+ * of two in [4, 8192], FM_EINVAL otherwise: the C ABI cannot check the
+ * buffer's length).  The variance equals fm_map_noise's up to the grouping
+ * of the fp32 partial sums (~1e-7 relative). */
 int fm_map_noise_accumulate(const void *g1, const void *g2, double *sums, int n, int J, int r0, int R, uint64_t seed,
                             const fm_config *cfg, void *stream);
 int fm_noise_finalize(const double *sums, const void *pyramid, double *var_out, void *snr_out, int n, int J,
@@ -212,18 +217,22 @@ int fm_map_noise_expected(const void *g1, const void *g2, void *var_out, int n, 
  * callers that cannot allocate device memory where they run the inversion
  * (their device memory is reserved up front by another framework's pool, or
  * the code path must never enter the allocator).  Same arguments, layout and
- * results as fm_ks_invert, FM_F32 only (cfg NULL or precision FM_F32), n a
- * power of two in [32, 8192], batch * n^2 <= 4194304.  The FFT work buffer
- * and twiddle tables are file-scope device arrays (32 MiB + 128 KiB) that
- * every GPU loading the library holds until the process exits; this entry
- * point calls no cudaMalloc, cudaFree or other allocating routine.  Larger
- * sizes return FM_EINVAL.  The first call on each device sets up (looks up
- * the arrays' device addresses and copies the twiddle tables synchronously)
- * with that device current; make that first call before any stream capture.
- * All calls share the one work buffer, which keeps the last call's contents
- * (every call overwrites all of the part it uses, so nothing needs clearing);
- * calls whose work overlaps on the GPU race on it and must be ordered by the
- * caller, e.g. by issuing them on one stream. */
+ * results as fm_ks_invert, FM_F32 only (cfg NULL or a valid config with
+ * precision FM_F32), n a power of two in [32, 2048], batch * n^2 <= 4194304
+ * (so a batch of one 2048^2 map, four of 1024^2, ...).  The FFT work buffer
+ * and twiddle tables are file-scope device arrays (32 MiB + 32 KiB per
+ * device); this entry point calls no cudaMalloc, cudaFree or other
+ * allocating routine.  The driver allocates the arrays when it loads their
+ * module on a device: with CUDA's default lazy module loading that is the
+ * first call on that device, so make the first call before another pool
+ * reserves the device's memory (and before any stream capture); the arrays
+ * stay allocated until the process exits.  Larger sizes return FM_EINVAL.
+ * The first call on each device also sets up (looks up the arrays' device
+ * addresses and copies the twiddle tables synchronously) with that device
+ * current.  All calls share the one work buffer, which keeps the last
+ * call's contents (every call overwrites all of the part it uses, so nothing
+ * needs clearing); calls whose work overlaps on the GPU race on it and must
+ * be ordered by the caller, e.g. by issuing them on one stream. */
 int fm_ks_invert_noalloc(const void *g1, const void *g2, void *kappa_E, void *kappa_B, int n, int batch,
                          const fm_config *cfg, void *stream);
 
@@ -266,6 +275,11 @@ size_t fm_request_scratch_bytes(const fm_request *req);
 const char *fm_status_string(int status);
 const char *fm_last_error(void);   /* message of the calling thread's last error */
 int64_t fm_launch_count(void);     /* kernels launched by this library so far */
+/* Device allocations this library has made (stream-ordered scratch, graph
+ * scratch, twiddle tables, the autotuner's buffers) since the last reset:
+ * their number and the largest one in bytes; reset != 0 zeroes both after
+ * reading.  Either pointer may be NULL. */
+int fm_alloc_stats(int64_t *count, int64_t *max_bytes, int reset);
 /* 1 if a kernel on the current device gave up waiting for a bulk tensor copy
  * (an iteration-bounded wait that ran out; its outputs are then missing),
  * else 0; clears the flag.  Synchronises with the device.  FM_EINVAL if no

@@ -18,7 +18,7 @@ static fm_config cfg_or_default(const fm_config *c)
     return d;
 }
 
-static int check_cfg(const fm_config &c)
+int check_config(const fm_config &c)
 {
     if (c.precision != FM_F32 && c.precision != FM_F64) return einval("precision must be FM_F32 or FM_F64");
     if (c.boundary != FM_MIRROR && c.boundary != FM_PERIODIC) return einval("boundary must be FM_MIRROR or FM_PERIODIC");
@@ -61,7 +61,7 @@ int fm_ks_invert(const void *g1, const void *g2, void *kappa_E, void *kappa_B, i
                  void *stream)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if ((st = check_fft_n(n))) return st;
     if (batch < 1) return einval("batch must be >= 1");
@@ -76,7 +76,7 @@ int fm_ks_invert(const void *g1, const void *g2, void *kappa_E, void *kappa_B, i
 int fm_ks_forward(const void *kappa, void *g1, void *g2, int n, int batch, const fm_config *cfgp, void *stream)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if ((st = check_fft_n(n))) return st;
     if (batch < 1) return einval("batch must be >= 1");
@@ -90,7 +90,7 @@ int fm_ks_forward(const void *kappa, void *g1, void *g2, int n, int batch, const
 int fm_starlet_forward(const void *kappa, void *pyramid, int n, int J, int batch, const fm_config *cfgp, void *stream)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if (n < 1) return einval("n must be >= 1");
     if ((st = check_J(n, J))) return st;
@@ -105,7 +105,7 @@ int fm_starlet_forward(const void *kappa, void *pyramid, int n, int J, int batch
 int fm_starlet_fuse_depth(int n, int J, const fm_config *cfgp)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if (n < 1) return einval("n must be >= 1");
     if ((st = check_J(n, J))) return st;
@@ -116,7 +116,7 @@ int fm_map_starlet(const void *g1, const void *g2, void *pyramid, int n, int J, 
                    void *stream)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if ((st = check_fft_n(n))) return st;
     if ((st = check_J(n, J))) return st;
@@ -129,7 +129,7 @@ int fm_map_starlet_host(const void *g1_host, const void *g2_host, void *pyramid_
                         const fm_config *cfgp, void *stream)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if ((st = check_fft_n(n))) return st;
     if ((st = check_J(n, J))) return st;
@@ -143,7 +143,7 @@ int fm_map_direct(const void *g1, const void *g2, void *map, int n, int filter, 
                   double cut_over_theta, const fm_config *cfgp, void *stream)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if (n < 1 || n > 65536) return einval("n must be in [1, 65536]");
     if (filter < FM_FILTER_STARLET || filter > FM_FILTER_VW98) return einval("unknown filter");
@@ -163,7 +163,7 @@ int fm_map_direct_masked(const void *g1, const void *g2, const void *weight, lon
                          double cut_over_theta, const fm_config *cfgp, void *stream)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if (n < 1 || n > 65536) return einval("n must be in [1, 65536]");
     if (batch < 1 || batch > 65535) return einval("batch must be in [1, 65535]");
@@ -188,7 +188,7 @@ int fm_map_noise(const void *g1, const void *g2, double *var_out, void *snr_out,
                  const fm_config *cfgp, void *stream)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if ((st = check_fft_n(n))) return st;
     if ((st = check_J(n, J))) return st;
@@ -204,7 +204,7 @@ int fm_map_noise_accumulate(const void *g1, const void *g2, double *sums, int n,
                             const fm_config *cfgp, void *stream)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if (cfg.accum != 0) return einval("fm_map_noise_accumulate keeps FP64 sums (accum = 0)");
     if ((st = check_fft_n(n))) return st;
@@ -218,10 +218,11 @@ int fm_noise_finalize(const double *sums, const void *pyramid, double *var_out, 
                       int R_total, const fm_config *cfgp, void *stream)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if (cfg.accum != 0) return einval("fm_noise_finalize reads FP64 sums (accum = 0)");
-    if (n < 1 || (st = check_J(n, J))) return st ? st : einval("n must be >= 1");
+    if ((st = check_fft_n(n))) return st;  // the sizes fm_map_noise_accumulate produces sums for
+    if ((st = check_J(n, J))) return st;
     if (R_total < 2) return einval("R_total must be >= 2");
     if (!sums || !var_out) return einval("null pointer");
     if (snr_out && !pyramid) return einval("S/N needs the data's pyramid");
@@ -239,7 +240,7 @@ int fm_map_noise_expected(const void *g1, const void *g2, void *var_out, int n, 
                           void *stream)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if ((st = check_fft_n(n))) return st;
     if ((st = check_J(n, J))) return st;
@@ -275,7 +276,7 @@ int fm_band_moments(const void *pyramid, double *moments, int n, int J, int batc
                     void *stream)
 {
     fm_config cfg = cfg_or_default(cfgp);
-    int st = check_cfg(cfg);
+    int st = check_config(cfg);
     if (st) return st;
     if (n < 1 || n > 65536) return einval("n must be in [1, 65536]");
     if (J < 1 || J > 20) return einval("J must be in [1, 20]");

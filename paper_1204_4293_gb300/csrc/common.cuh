@@ -157,6 +157,10 @@ struct Scratch {
     }
 };
 int scratch_alloc(Scratch &sc, size_t bytes, cudaStream_t s);
+// cudaMalloc, counted by fm_alloc_stats (graph scratch, tables, tuner buffers)
+cudaError_t dev_malloc(void **p, size_t bytes);
+// the checks every entry point applies to its fm_config (api.cu)
+int check_config(const fm_config &c);
 
 // Raise a kernel's dynamic shared-memory limit once per (device, kernel,
 // size); later calls with no larger size make no driver call.

@@ -6,8 +6,11 @@
 // memory is reserved up front by another framework's pool, so that a fresh
 // allocation would fail, or a latency-critical loop that must never enter the
 // allocator.  fm_ks_invert_noalloc serves them: its work buffer and FFT
-// twiddle tables live in file-scope device arrays that every GPU loading the
-// library holds until the process exits (32 MiB + 128 KiB per GPU).
+// twiddle tables live in file-scope device arrays (32 MiB + 32 KiB per
+// device).  The driver allocates them when it loads this file's module on a
+// device: under CUDA's default lazy module loading that happens at the first
+// call on that device (the set-up below), with eager loading when the
+// library's context starts; either way they are held until the process exits.
 #include <math.h>
 
 #include <mutex>
@@ -20,8 +23,9 @@ namespace fm {
 namespace {
 
 constexpr long kNoallocWorkElems = 4l << 20;  // float2 elements: 32 MiB
-constexpr int kTwMinN = 32, kTwMaxN = 8192;
-constexpr int kTwElems = 2 * kTwMaxN - kTwMinN;  // tables n = 32, 64, ..., 8192 back to back
+// batch * n^2 <= 4194304 caps n at 2048 (a batch of one)
+constexpr int kTwMinN = 32, kTwMaxN = 2048;
+constexpr int kTwElems = 2 * kTwMaxN - kTwMinN;  // tables n = 32, 64, ..., 2048 back to back
 
 static __device__ __align__(256) float2 g_noalloc_work[kNoallocWorkElems];
 static __device__ __align__(256) float2 g_noalloc_tw[kTwElems];
@@ -67,12 +71,16 @@ using namespace fm;
 extern "C" int fm_ks_invert_noalloc(const void *g1, const void *g2, void *kappa_E, void *kappa_B, int n, int batch,
                                     const fm_config *cfg, void *stream)
 {
-    if (cfg && cfg->precision != FM_F32) {
-        set_error("fm_ks_invert_noalloc: only FM_F32 is supported");
-        return FM_EINVAL;
+    if (cfg) {
+        const int c = check_config(*cfg);  // the same configs fm_ks_invert accepts
+        if (c != FM_OK) return c;
+        if (cfg->precision != FM_F32) {
+            set_error("fm_ks_invert_noalloc: only FM_F32 is supported");
+            return FM_EINVAL;
+        }
     }
     if (n < kTwMinN || n > kTwMaxN || !is_pow2(n)) {
-        set_error("fm_ks_invert_noalloc: n must be a power of two in [32, 8192]");
+        set_error("fm_ks_invert_noalloc: n must be a power of two in [32, 2048]");
         return FM_EINVAL;
     }
     if (batch < 1 || (long)batch * n * n > kNoallocWorkElems) {

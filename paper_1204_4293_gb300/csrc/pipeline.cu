@@ -201,7 +201,7 @@ static int map_starlet_dev(const void *g1, const void *g2, void *pyramid, int n,
         }
         GraphEntry e;
         e.key = key;
-        cudaError_t ce = cudaMalloc(&e.scratch, p.slot_b * p.slots);
+        cudaError_t ce = dev_malloc(&e.scratch, p.slot_b * p.slots);
         if (ce != cudaSuccess) return cuda_fail(ce, "cudaMalloc (graph scratch)");
         cudaGraph_t graph = nullptr;
         ce = cudaStreamBeginCapture(ds->cap, cudaStreamCaptureModeRelaxed);
@@ -253,7 +253,9 @@ constexpr long kNoisePyrBatchBytes = 8L << 30;  // pyramids of one accumulation 
 // maps need several realisations per batch: with 1 GiB a 4096^2 J = 10 map
 // had one, and R = 100 took 273 ms; with 4 GiB (six) 116 ms, with 8 GiB
 // (twelve) 102 ms; the serving trace went 3.9 -> 8.0 -> 9.0 requests/s.
-NoiseLayout noise_layout(int n, int J, int R, const fm_config &cfg, bool multi_stream)
+// ext_sums: the running sums are the caller's (partial accumulation), so the
+// layout holds no space for them.
+NoiseLayout noise_layout(int n, int J, int R, const fm_config &cfg, bool multi_stream, bool ext_sums = false)
 {
     const size_t es = cfg.precision == FM_F64 ? 8 : 4;
     const size_t nn = (size_t)n * n;
@@ -265,7 +267,7 @@ NoiseLayout noise_layout(int n, int J, int R, const fm_config &cfg, bool multi_s
     L.p = plan_chunks(n, J, L.batch, cfg);
     L.slots = multi_stream ? L.p.slots : 1;
     L.pyr_bufs = L.slots > 1 && R > L.batch ? kNoisePyrBufs : 1;
-    L.acc_b = up(2 * (size_t)(J - 1) * nn * sizeof(double));
+    L.acc_b = ext_sums ? 0 : up(2 * (size_t)(J - 1) * nn * sizeof(double));
     L.pyr_b = up((size_t)L.batch * J * nn * es);
     L.total = L.acc_b + (size_t)L.pyr_bufs * L.pyr_b + (size_t)L.slots * L.p.slot_b;
     return L;
@@ -399,7 +401,7 @@ int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out
         }
         NoiseGraph e;
         e.key = key;
-        cudaError_t ce = cudaMalloc(&e.scratch, L.total);
+        cudaError_t ce = dev_malloc(&e.scratch, L.total);
         if (ce != cudaSuccess) return cuda_fail(ce, "cudaMalloc (noise graph scratch)");
         cudaGraph_t graph = nullptr;
         ce = cudaStreamBeginCapture(ds->cap, cudaStreamCaptureModeRelaxed);
@@ -439,7 +441,7 @@ int map_noise_accumulate_run(const void *g1, const void *g2, double *sums, int n
 {
     int st = FM_OK;
     if (!twiddles(n, cfg.precision, s, &st)) return st;
-    const NoiseLayout L = noise_layout(n, J, R, cfg, false);
+    const NoiseLayout L = noise_layout(n, J, R, cfg, false, true);
     Scratch sc;
     if ((st = scratch_alloc(sc, L.total, s))) return st;
     return noise_submit(g1, g2, nullptr, nullptr, n, J, R, seed, cfg, L, (char *)sc.p, s, nullptr, sums, r0);

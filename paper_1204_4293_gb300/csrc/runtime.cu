@@ -119,7 +119,7 @@ const void *twiddles(int n, int precision, cudaStream_t s, int *status)
         }
     }
     void *d = nullptr;
-    e = cudaMalloc(&d, host.size());
+    e = dev_malloc(&d, host.size());
     if (e == cudaSuccess) e = cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         if (d) cudaFree(d);
@@ -151,11 +151,31 @@ cudaError_t smem_attr(const void *kernel, size_t bytes)
     return e;
 }
 
+// ---- device allocations ---------------------------------------------------------
+// Every device allocation the library makes (stream-ordered scratch, graph
+// scratch, tables, the autotuner's buffers) is counted here: fm_alloc_stats.
+std::atomic<int64_t> g_alloc_count{0}, g_alloc_max{0};
+
+void note_alloc(size_t bytes)
+{
+    g_alloc_count.fetch_add(1);
+    int64_t cur = g_alloc_max.load();
+    while ((int64_t)bytes > cur && !g_alloc_max.compare_exchange_weak(cur, (int64_t)bytes)) {
+    }
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    note_alloc(bytes);
+    return cudaMalloc(p, bytes);
+}
+
 // ---- scratch -------------------------------------------------------------------
 int scratch_alloc(Scratch &sc, size_t bytes, cudaStream_t s)
 {
     sc.s = s;
     if (bytes == 0) return FM_OK;
+    note_alloc(bytes);
     static std::once_flag pool_once;
     std::call_once(pool_once, [] {
         // keep freed stream-ordered memory in the pool instead of returning it
@@ -247,6 +267,17 @@ const char *fm_status_string(int status)
 const char *fm_last_error(void) { return t_last_error.c_str(); }
 
 int64_t fm_launch_count(void) { return g_launches.load(); }
+
+int fm_alloc_stats(int64_t *count, int64_t *max_bytes, int reset)
+{
+    if (count) *count = g_alloc_count.load();
+    if (max_bytes) *max_bytes = g_alloc_max.load();
+    if (reset) {
+        g_alloc_count.store(0);
+        g_alloc_max.store(0);
+    }
+    return FM_OK;
+}
 
 int fm_profile_select(int kid)
 {

@@ -128,9 +128,9 @@ int fm_autotune(int n, int J, int batch, const fm_config *cfgp, fm_plan *best)
     const size_t es = cfg.precision == FM_F64 ? 8 : 4;
     const long nn = (long)n * n;
     DevBuf g1, g2, pyr;
-    FM_CUDA_TRY(cudaMalloc(&g1.p, (size_t)batch * nn * es));
-    FM_CUDA_TRY(cudaMalloc(&g2.p, (size_t)batch * nn * es));
-    FM_CUDA_TRY(cudaMalloc(&pyr.p, (size_t)batch * J * nn * es));
+    FM_CUDA_TRY(dev_malloc(&g1.p, (size_t)batch * nn * es));
+    FM_CUDA_TRY(dev_malloc(&g2.p, (size_t)batch * nn * es));
+    FM_CUDA_TRY(dev_malloc(&pyr.p, (size_t)batch * J * nn * es));
     Stream st;
     FM_CUDA_TRY(cudaStreamCreateWithFlags(&st.s, cudaStreamNonBlocking));
     FM_CUDA_TRY(cudaEventCreate(&st.e0));

@@ -79,6 +79,7 @@ _SIGS = {
     "fm_status_string": (ctypes.c_char_p, [_I]),
     "fm_last_error": (ctypes.c_char_p, []),
     "fm_launch_count": (ctypes.c_int64, []),
+    "fm_alloc_stats": (_I, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _I]),
     "fm_device_error": (_I, []),
     "fm_profile_select": (_I, [_I]),
     "fm_tune": (_I, [_I, ctypes.c_int64]),
@@ -391,6 +392,14 @@ def fm_trim() -> None:
 
 def fm_launch_count() -> int:
     return int(_lib.fm_launch_count())
+
+
+def fm_alloc_stats(reset: bool = False):
+    """(count, largest bytes) of the device allocations the library made
+    since the last reset; reset=True zeroes them after reading."""
+    c, m = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(_lib.fm_alloc_stats(ctypes.byref(c), ctypes.byref(m), 1 if reset else 0), "fm_alloc_stats")
+    return int(c.value), int(m.value)
 
 
 def fm_device_error() -> int:

@@ -79,13 +79,26 @@ def test_validation_before_any_device_work(fm):
     assert lib.fm_map_noise_accumulate(1, 1, 1, 64, 4, 0, 0, 0, cfg, None) == fm.FM_EINVAL  # R < 1
     assert lib.fm_noise_finalize(1, None, 1, 1, 64, 4, 10, cfg, None) == fm.FM_EINVAL  # S/N without pyramid
     assert lib.fm_noise_finalize(1, None, 1, None, 64, 4, 1, cfg, None) == fm.FM_EINVAL  # R_total < 2
+    assert lib.fm_noise_finalize(1, None, 1, None, 48, 4, 10, cfg, None) == fm.FM_EINVAL  # no sums exist for n = 48
     kahan = fm._cfg(0, accum=1)
     assert lib.fm_map_noise_accumulate(1, 1, 1, 64, 4, 0, 3, 0, ctypes.byref(kahan), None) == fm.FM_EINVAL
+    # the allocation-free KS takes the configs fm_ks_invert takes, and n up to
+    # 2048 (a batch of one fills its static buffer)
+    for bad in (fm._cfg(0, large_path=4), fm._cfg(0, boundary=5), fm._cfg(1)):
+        assert lib.fm_ks_invert_noalloc(1, 1, 1, None, 256, 1, ctypes.byref(bad), None) == fm.FM_EINVAL
+    assert lib.fm_ks_invert_noalloc(1, 1, 1, None, 4096, 1, cfg, None) == fm.FM_EINVAL
+    assert b"[32, 2048]" in lib.fm_last_error()
     bad = fm._cfg(0, large_path=4)
     assert lib.fm_starlet_forward(1, 1, 64, 3, 1, ctypes.byref(bad), None) == fm.FM_EINVAL
     h = ctypes.c_void_p()
     assert lib.fm_serve_create(0, 2, ctypes.byref(h)) == fm.FM_EINVAL
     assert lib.fm_serve_poll(None, 1, None) == fm.FM_EINVAL
+
+
+def test_alloc_stats_read_and_reset(fm):
+    count, largest = fm.fm_alloc_stats(reset=True)
+    assert count >= 0 and largest >= 0
+    assert fm.fm_alloc_stats() == (0, 0)
 
 
 def test_request_scratch_bytes_is_monotone(fm):

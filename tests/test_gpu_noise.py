@@ -148,3 +148,26 @@ def test_noise_in_parts_equals_one_call():
         assert (v3[j] - var[j]).abs().max().item() / ref <= 1e-5
         assert (s2[j] - snr[j]).abs().max().item() / snr[j].pow(2).mean().sqrt().item() <= 1e-4
     fm.fm_trim()
+
+
+def test_noise_accumulate_scratch_excludes_the_sums():
+    """A partial accumulation adds to the caller's sums, so its scratch is the
+    eager fm_map_noise call's minus the FP64 sums (2 (J-1) n^2 doubles)."""
+    fm = _fm()
+    n, J, R = 256, 6, 4
+    g1, g2 = shear(n, seed=14, dtype=np.float32)
+    t1, t2 = torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda()
+    fm.fm_tune(fm.FM_TUNE_GRAPHS, 0)  # the eager call takes one stream-ordered scratch block
+    try:
+        fm.fm_alloc_stats(reset=True)
+        fm.fm_map_noise(t1, t2, J, R, seed=1)
+        _, whole = fm.fm_alloc_stats(reset=True)
+    finally:
+        fm.fm_tune(fm.FM_TUNE_GRAPHS, -1)
+    sums = torch.zeros(2, J - 1, n, n, dtype=torch.float64, device="cuda")
+    fm.fm_alloc_stats(reset=True)
+    fm.fm_map_noise_accumulate(t1, t2, J, 0, R, seed=1, sums=sums)
+    count, part = fm.fm_alloc_stats()
+    torch.cuda.synchronize()
+    assert count == 1
+    assert whole - part == 2 * (J - 1) * n * n * 8

@@ -2,14 +2,16 @@
 allocate device memory where they run it (their memory is reserved up front
 by another pool, or the code path must never enter the allocator).  Its work
 buffer is a static device array; this checks it through the C ABI against the
-allocating fm_ks_invert on two calls in a row, since the shared buffer keeps
-the previous call's contents.  Kept last in collection order."""
+FP64 oracle and against the allocating fm_ks_invert on two calls in a row
+(the shared buffer keeps the previous call's contents), and that a call makes
+no device allocation.  Kept last in collection order."""
 import ctypes
 
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from helpers import TOL, rel_err, shear
 
 pytestmark = pytest.mark.gpu
@@ -23,8 +25,8 @@ def _noalloc(fm, g1, g2, kE, kB, n, batch):
     assert st == fm.FM_OK, fm.lib.fm_last_error()
 
 
-@pytest.mark.parametrize("n,batch", [(1024, 2), (256, 3)])
-def test_noalloc_matches_allocating_entry_point_twice(n, batch):
+@pytest.mark.parametrize("n,batch", [(1024, 2), (256, 3), (2048, 1)])
+def test_noalloc_matches_oracle_and_allocating_entry_point_twice(n, batch):
     from paper_1204_4293_gb300 import fastmap as fm
     for call, seed in enumerate((41, 42)):  # second call sees the first call's buffer contents
         maps = [shear(n, seed=seed + 10 * b, dtype=np.float32) for b in range(batch)]
@@ -38,6 +40,30 @@ def test_noalloc_matches_allocating_entry_point_twice(n, batch):
         for b in range(batch):
             assert rel_err(kE[b].cpu().numpy(), rE[b].cpu().numpy()) <= TOL[np.float32], call
             assert rel_err(kB[b].cpu().numpy(), rB[b].cpu().numpy()) <= TOL[np.float32], call
+            oE, oB = oracle.ks_invert(maps[b][0].astype(np.float64), maps[b][1].astype(np.float64))
+            assert rel_err(kE[b].cpu().numpy(), oE) <= TOL[np.float32], call
+            assert rel_err(kB[b].cpu().numpy(), oB) <= TOL[np.float32], call
+
+
+def test_noalloc_makes_no_device_allocation():
+    from paper_1204_4293_gb300 import fastmap as fm
+    n, batch = 512, 4
+    g1 = torch.empty((batch, n, n), device="cuda").normal_(0, 0.1)
+    g2 = torch.empty_like(g1).normal_(0, 0.1)
+    kE, kB = torch.empty_like(g1), torch.empty_like(g1)
+    _noalloc(fm, g1, g2, kE, kB, n, batch)  # the device's first call loads the static arrays
+    torch.cuda.synchronize()
+    fm.fm_alloc_stats(reset=True)
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        _noalloc(fm, g1, g2, kE, kB, n, batch)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert fm.fm_alloc_stats() == (0, 0)  # the library allocated nothing
+    assert free1 == free0  # and neither did anything else on the device
+    fm.fm_ks_invert(g1, g2)  # the allocating entry point, for contrast
+    torch.cuda.synchronize()
+    assert fm.fm_alloc_stats()[0] >= 1
 
 
 def test_noalloc_rejects_sizes_beyond_its_buffer():
