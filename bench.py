@@ -375,6 +375,7 @@ def side_legs(fm, torch, n, J, g1, g2, pyr):
     s1, s2 = g1[0].contiguous(), g2[0].contiguous()
     kap, _ = fm.fm_ks_invert(s1.unsqueeze(0), s2.unsqueeze(0))
     kap = kap[0].contiguous()
+    gb1, gb2 = g1[:8].contiguous(), g2[:8].contiguous()
     rows = []
     for j in range(1, J):
         theta = float(2 ** j)
@@ -393,6 +394,9 @@ def side_legs(fm, torch, n, J, g1, g2, pyr):
         t_g = cuda_time(torch, lambda: fm.fm_map_direct(s1, s2, fm.FM_FILTER_JBJ04, theta, cut_over_theta=5.0),
                         2 if theta >= 32 else reps)
         tf_g = 4.0 * disc_taps(5 * theta) * n * n / (t_g * 1e-3) / 1e12
+        # the same S98 sum over 8 maps in one launch (fm_map_direct_batch)
+        t_b8 = cuda_time(torch, lambda: fm.fm_map_direct(gb1, gb2, fm.FM_FILTER_S98, theta), 2) / 8
+        tf_b8 = 4.0 * disc_taps(theta) * n * n / (t_b8 * 1e-3) / 1e12
         rows.append({"theta_px": theta, "J": Jj, "starlet_ms": t_st, "ks_starlet_ms": t_ks,
                      "map_s98_cut_theta_ms": t_s98, "map_starletQ_cut_2theta_ms": t_stq,
                      "map_jbj04_cut_5theta_ms": t_g, "jbj04_over_s98": t_g / t_s98,
@@ -400,7 +404,8 @@ def side_legs(fm, torch, n, J, g1, g2, pyr):
                      "speedup_vs_jbj04": t_g / t_st,
                      "s98_tflops": tf_s98, "starletQ_tflops": tf_stq, "jbj04_tflops": tf_g,
                      "s98_alu_frac": tf_s98 / FP32_PEAK_TFLOPS, "starletQ_alu_frac": tf_stq / FP32_PEAK_TFLOPS,
-                     "jbj04_alu_frac": tf_g / FP32_PEAK_TFLOPS})
+                     "jbj04_alu_frac": tf_g / FP32_PEAK_TFLOPS,
+                     "s98_batch8_ms_per_map": t_b8, "s98_batch8_alu_frac": tf_b8 / FP32_PEAK_TFLOPS})
     out["direct_map"] = rows
     out["direct_map_alu_peak"] = {"tflops": FP32_PEAK_TFLOPS, "source": "derived: 152 SMs x 128 FP32 lanes x 2 flops "
                                   "(FMA) x 2.07 GHz maximum SM clock"}

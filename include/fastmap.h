@@ -141,6 +141,12 @@ int fm_map_starlet_host(const void *g1_host, const void *g2_host, void *pyramid_
 int fm_map_direct(const void *g1, const void *g2, void *map, int n, int filter, double theta_px, int ell,
                   double cut_over_theta, const fm_config *cfg, void *stream);
 
+/* The same for a batch of maps [batch][n][n] in one launch (the maps share
+ * the filter's weight table; small radii no longer leave most of the GPU
+ * idle in the grid's last wave). */
+int fm_map_direct_batch(const void *g1, const void *g2, void *map, int n, int batch, int filter, double theta_px,
+                        int ell, double cut_over_theta, const fm_config *cfg, void *stream);
+
 /* ---- direct M_ap with missing data (Sec. 4.3, Sec. 4.5) -----------------------
  * The paper notes that masks (bright stars, bad pixels) and field edges
  * leave pixels without data and that the brute-force aperture sum suffers
@@ -314,6 +320,13 @@ int fm_device_error(void);
  *                        (within about 0.1 s), the tile leaves its outputs
  *                        unwritten and fm_device_error reports 1; 0 = off
  *                        (default)
+ *   FM_TUNE_DIRECT       kernel of the fp32 direct M_ap without weights:
+ *                        0 = scalar FMAs with synchronous row staging,
+ *                        1 = packed two-lane FMAs with asynchronous row
+ *                        staging, 4 rows x 8 columns per lane, 4 warps;
+ *                        2, 3, 4 = the same with 2 x 8 per lane and 4 warps,
+ *                        4 x 8 and 2 warps, 2 x 8 and 8 warps; default: 2
+ *                        below a 48-pixel cut radius, else 3
  * FM_TUNE_CHUNK_BYTES set this way also overrides autotuned budgets. */
 #define FM_TUNE_CHUNK_BYTES 1
 #define FM_TUNE_GRAPHS 2
@@ -322,6 +335,7 @@ int fm_device_error(void);
 #define FM_TUNE_TILE 5
 #define FM_TUNE_TMA 6
 #define FM_TUNE_WAIT_TEST 7
+#define FM_TUNE_DIRECT 8
 int fm_tune(int knob, int64_t value);
 
 /* ---- autotuner ----------------------------------------------------------------

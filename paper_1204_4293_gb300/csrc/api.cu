@@ -158,6 +158,26 @@ int fm_map_direct(const void *g1, const void *g2, void *map, int n, int filter, 
                              (cudaStream_t)stream);
 }
 
+int fm_map_direct_batch(const void *g1, const void *g2, void *map, int n, int batch, int filter, double theta_px,
+                        int ell, double cut_over_theta, const fm_config *cfgp, void *stream)
+{
+    fm_config cfg = cfg_or_default(cfgp);
+    int st = check_config(cfg);
+    if (st) return st;
+    if (n < 1 || n > 65536) return einval("n must be in [1, 65536]");
+    if (batch < 1 || batch > 65535) return einval("batch must be in [1, 65535]");
+    if (filter < FM_FILTER_STARLET || filter > FM_FILTER_VW98) return einval("unknown filter");
+    if (!(theta_px > 0) || theta_px > 4096) return einval("theta_px must be in (0, 4096]");
+    if (filter == FM_FILTER_S98 && (ell < 0 || ell > 64)) return einval("ell must be in [0, 64]");
+    const double cut = cut_over_theta > 0 ? cut_over_theta : 0.0;
+    const double R = (cut > 0 ? cut : (filter == FM_FILTER_STARLET ? 2.0 : filter == FM_FILTER_S98 ? 1.0 : 5.0)) *
+                     theta_px;
+    if (R > 2048) return einval("cut radius above 2048 px");
+    if (!g1 || !g2 || !map) return einval("null pointer");
+    return launch_map_direct(g1, g2, nullptr, 0, map, nullptr, n, batch, filter, theta_px, ell, cut, cfg.precision,
+                             (cudaStream_t)stream);
+}
+
 int fm_map_direct_masked(const void *g1, const void *g2, const void *weight, long weight_bstride, void *map,
                          void *coverage, int n, int batch, int filter, double theta_px, int ell,
                          double cut_over_theta, const fm_config *cfgp, void *stream)

@@ -51,6 +51,8 @@ extern std::atomic<int> g_prof_kid;  // kernel id whose launches are being timed
 // test hook (FM_TUNE_WAIT_TEST): the fused tile kernel's bulk copy waits for
 // more bytes than arrive, so its bounded wait runs out and is flagged
 extern std::atomic<int> g_wait_test;
+// kernel form of the unmasked fp32 direct M_ap (FM_TUNE_DIRECT)
+extern std::atomic<int> g_direct_form;
 // 1 if a kernel of that file gave up waiting on a bulk copy (see fm_device_error)
 int starlet_wait_error(bool clear);
 int fft_wait_error(bool clear);

@@ -27,6 +27,7 @@
 // aperture's pixel count.
 #include <math.h>
 
+#include <atomic>
 #include <vector>
 
 #include "common.cuh"
@@ -74,6 +75,7 @@ static double default_cut(int filter) { return filter == FM_FILTER_STARLET ? 2.0
 
 // ---- kernel -------------------------------------------------------------------
 __device__ __forceinline__ int padc(int c) { return c + (c >> 3); }
+__device__ __forceinline__ uint32_t smem_u32_md(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 template <typename T, int CX, int RY, int NW, bool MASK>
 __global__ void __launch_bounds__(NW * 32) k_map_direct(const T *__restrict__ g1, const T *__restrict__ g2,
@@ -216,6 +218,210 @@ __global__ void __launch_bounds__(NW * 32) k_map_direct(const T *__restrict__ g1
     }
 }
 
+// ---- fp32 form without weights ------------------------------------------------
+// The same walk over input rows with two changes: the next input row arrives
+// by asynchronous 4-byte copies (cp.async, zero-filled outside the field)
+// into the other buffer while the CTA works on the current one, so the
+// global-memory latency of the staging is hidden; and the two components are
+// staged interleaved, (gamma1, gamma2) per column, so that one packed
+// two-lane FMA (fma.rn.f32x2) per tap adds A gamma1 into lane x and
+// B gamma2 into lane y of a partial sum; the lanes are added when the input
+// row is done.  Half the FMA instructions of the scalar form.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32_md(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+//
+// With P > 1 the input rows a tile needs (TY + 2R of them) are split into P
+// consecutive parts, one CTA each (blockIdx.z = b P + p), so that a single
+// map with a large radius still gives the GPU several waves of CTAs; part p
+// writes its sums to part_out[p][b] and k_sum_parts adds the parts in order
+// (the same order whatever the batch, so a map's result does not depend on
+// the maps beside it).
+template <int CX, int RY, int NW>
+__global__ void __launch_bounds__(NW * 32) k_map_direct_f2(const float *__restrict__ g1, const float *__restrict__ g2,
+                                                           const float2 *__restrict__ taps, int tw,
+                                                           const int *__restrict__ dxmax, float *__restrict__ out,
+                                                           int n, int Ri, int P, int batch)
+{
+    pdl_entry();
+    constexpr int TX = 32 * CX, TY = NW * RY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int width = TX + 2 * Ri + 8;
+    const int pw = padc(width) + 1;
+    float2 *s2 = reinterpret_cast<float2 *>(smem_raw);  // [2 buffers][pw] of (gamma1, gamma2)
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const long nn = (long)n * n;
+    const long b = blockIdx.z / P;
+    const int p = blockIdx.z % P;
+    g1 += b * nn;
+    g2 += b * nn;
+    out += ((long)p * batch + b) * nn;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int yw = y0 + warp * RY;
+    const int lc = lane * CX;
+    const int rows = TY + 2 * Ri, chunk = (rows + P - 1) / P;
+    const int iy_lo = y0 - Ri + p * chunk;
+    const int iy_end = y0 + TY - 1 + Ri;
+    const int iy_hi = iy_lo + chunk - 1 < iy_end ? iy_lo + chunk - 1 : iy_end;
+
+    auto stage = [&](int iy) {  // this thread's copies of input row iy into its buffer
+        float *buf = reinterpret_cast<float *>(s2 + ((iy - iy_lo) & 1) * pw);
+        const bool rin = iy >= 0 && iy < n;
+        for (int c = threadIdx.x; c < width; c += NW * 32) {
+            const int gx = x0 - Ri + c;
+            const bool in = rin && gx >= 0 && gx < n;
+            const long off = in ? (long)iy * n + gx : 0;
+            cp_async4(buf + 2 * padc(c), g1 + off, in ? 4 : 0);
+            cp_async4(buf + 2 * padc(c) + 1, g2 + off, in ? 4 : 0);
+        }
+        cp_async_commit();
+    };
+
+    float acc[RY][CX];
+#pragma unroll
+    for (int k = 0; k < RY; ++k)
+#pragma unroll
+        for (int o = 0; o < CX; ++o) acc[k][o] = 0.f;
+
+    if (iy_lo <= iy_hi) stage(iy_lo);
+    for (int iy = iy_lo; iy <= iy_hi; ++iy) {
+        cp_async_wait_all();  // this thread's copies of row iy have landed
+        __syncthreads();      // everyone's have; the other buffer is no longer read
+        if (iy < iy_hi) stage(iy + 1);
+        const float2 *buf = s2 + ((iy - iy_lo) & 1) * pw;
+
+        int dy[RY];
+        bool act[RY];
+        int dxm = -1;
+#pragma unroll
+        for (int k = 0; k < RY; ++k) {
+            dy[k] = iy - (yw + k);
+            act[k] = dy[k] >= -Ri && dy[k] <= Ri && (yw + k) < n;
+            if (act[k]) {
+                const int m = __ldg(dxmax + dy[k] + Ri);
+                dxm = m > dxm ? m : dxm;
+            }
+        }
+        if (dxm < 0) continue;
+        float2 part[RY][CX];
+#pragma unroll
+        for (int k = 0; k < RY; ++k)
+#pragma unroll
+            for (int o = 0; o < CX; ++o) part[k][o] = make_float2(0.f, 0.f);
+        for (int dx0 = -dxm; dx0 <= dxm; dx0 += 8) {
+            float2 w[CX + 7];
+            const int base = lc + dx0 + Ri;
+#pragma unroll
+            for (int q = 0; q < CX + 7; ++q) w[q] = buf[padc(base + q)];
+#pragma unroll
+            for (int k = 0; k < RY; ++k) {
+                if (!act[k]) continue;
+                const float2 *trow = taps + (long)(dy[k] + Ri) * tw + (dx0 + Ri);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const float2 ab = __ldg(trow + t);
+#pragma unroll
+                    for (int o = 0; o < CX; ++o) part[k][o] = __ffma2_rn(ab, w[o + t], part[k][o]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RY; ++k)
+#pragma unroll
+            for (int o = 0; o < CX; ++o) acc[k][o] += part[k][o].x + part[k][o].y;
+    }
+#pragma unroll
+    for (int k = 0; k < RY; ++k) {
+        const int y = yw + k;
+        if (y >= n) continue;
+#pragma unroll
+        for (int o = 0; o < CX; ++o) {
+            const int x = x0 + lc + o;
+            if (x < n) out[(long)y * n + x] = acc[k][o];
+        }
+    }
+}
+
+// out[i] = sum over p of part[p][i], p in order (float4 where the size allows)
+__global__ void k_sum_parts(const float *__restrict__ part, float *__restrict__ out, long total, int P)
+{
+    pdl_entry();
+    const long i4 = ((long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    const bool vec = (reinterpret_cast<uintptr_t>(out) & 15) == 0;  // `part` is 256-byte aligned scratch
+    if (vec && i4 + 3 < total) {
+        float4 a = *reinterpret_cast<const float4 *>(part + i4);
+        for (int p = 1; p < P; ++p) {
+            const float4 v = *reinterpret_cast<const float4 *>(part + (long)p * total + i4);
+            a.x += v.x;
+            a.y += v.y;
+            a.z += v.z;
+            a.w += v.w;
+        }
+        *reinterpret_cast<float4 *>(out + i4) = a;
+    } else {
+        for (long i = i4; i < total && i < i4 + 4; ++i) {
+            float a = part[i];
+            for (int p = 1; p < P; ++p) a += part[(long)p * total + i];
+            out[i] = a;
+        }
+    }
+}
+
+// kernel form of the unmasked fp32 direct map: 0 = scalar FMAs (k_map_direct),
+// 1 .. 4 = k_map_direct_f2 shapes (fm_tune FM_TUNE_DIRECT), -1 = by radius:
+// measured on one 1024^2 map (ms, forms 1 / 2 / 3 / 4), S98 theta = 8:
+// 0.084 / 0.062 / 0.068 / 0.070, theta = 32: 0.531 / 0.435 / 0.484 / 0.496,
+// theta = 64: 1.53 / 1.48 / 1.46 / 1.52, starlet Q theta = 64 (R = 128):
+// 5.01 / 5.08 / 4.99 / 5.13; the scalar form 0.091, 0.597, 1.98, 7.01
+std::atomic<int> g_direct_form{-1};
+static int direct_form(int Ri)
+{
+    const int f = g_direct_form.load();
+    return f >= 0 ? f : (Ri < 48 ? 2 : 3);
+}
+
+// parts of the input-row walk: about 32 rows each, at most 8 (a function of
+// the tile height and radius only, so results never depend on the batch)
+static int direct_parts(int TY, int Ri)
+{
+    const int P = (TY + 2 * Ri) / 32;
+    return P < 1 ? 1 : (P > 8 ? 8 : P);
+}
+
+template <int RY, int NW>
+static int launch_direct_f2(const float *g1, const float *g2, const float2 *dtaps, int tw, const int *ddx, float *map,
+                            float *parts, int n, int batch, int Ri, cudaStream_t s)
+{
+    constexpr int CX = 8, TX = 32 * CX, TY = NW * RY;
+    const int width = TX + 2 * Ri + 8;
+    const int pw = width + (width >> 3) + 1;
+    const size_t smem = 2ull * pw * sizeof(float2);
+    const int P = direct_parts(TY, Ri);
+    auto k = k_map_direct_f2<CX, RY, NW>;
+    FM_CUDA_TRY(fm::smem_attr((const void *)k, smem));
+    dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, batch * P);
+    FM_LAUNCH(FM_K_MAP_DIRECT, k, grid, NW * 32, smem, s, g1, g2, dtaps, tw, ddx, P > 1 ? parts : map, n, Ri, P,
+              batch);
+    if (P > 1) {
+        const long total = (long)batch * n * n;
+        const unsigned g = (unsigned)((total / 4 + 255) / 256 + 1);
+        FM_LAUNCH(FM_K_MAP_DIRECT, k_sum_parts, g, 256, 0, s, (const float *)parts, map, total, P);
+    }
+    return FM_OK;
+}
+
+static size_t direct_parts_bytes(int form, int n, int batch, int Ri)
+{
+    const int TY = form == 2 ? 8 : form == 3 ? 8 : 16;
+    const int P = direct_parts(TY, Ri);
+    return P > 1 ? (size_t)P * batch * n * n * sizeof(float) : 0;
+}
+
 template <typename T>
 static int map_direct_impl(const T *g1, const T *g2, const T *wgt, long w_bs, T *map, T *cov, int n, int batch,
                            int filter, double theta, int ell, double cut, cudaStream_t s)
@@ -254,12 +460,15 @@ static int map_direct_impl(const T *g1, const T *g2, const T *wgt, long w_bs, T 
     const size_t tap_bytes = htaps.size() * sizeof(V);
     const size_t disc_bytes = hdisc.size() * sizeof(T);
     const size_t dx_bytes = hdx.size() * sizeof(int);
-    int st = scratch_alloc(sc, up(tap_bytes) + up(disc_bytes) + dx_bytes, s);
+    const int form = direct_form(Ri);
+    const size_t part_bytes = (sizeof(T) == 4 && !mask && form > 0) ? direct_parts_bytes(form, n, batch, Ri) : 0;
+    int st = scratch_alloc(sc, up(tap_bytes) + up(disc_bytes) + up(dx_bytes) + part_bytes, s);
     if (st != FM_OK) return st;
     char *base = static_cast<char *>(sc.p);
     V *dtaps = reinterpret_cast<V *>(base);
     T *ddisc = mask ? reinterpret_cast<T *>(base + up(tap_bytes)) : nullptr;
     int *ddx = reinterpret_cast<int *>(base + up(tap_bytes) + up(disc_bytes));
+    float *dparts = reinterpret_cast<float *>(base + up(tap_bytes) + up(disc_bytes) + up(dx_bytes));
     FM_CUDA_TRY(cudaMemcpyAsync(dtaps, htaps.data(), tap_bytes, cudaMemcpyHostToDevice, s));
     if (mask) FM_CUDA_TRY(cudaMemcpyAsync(ddisc, hdisc.data(), disc_bytes, cudaMemcpyHostToDevice, s));
     FM_CUDA_TRY(cudaMemcpyAsync(ddx, hdx.data(), dx_bytes, cudaMemcpyHostToDevice, s));
@@ -267,6 +476,13 @@ static int map_direct_impl(const T *g1, const T *g2, const T *wgt, long w_bs, T 
     constexpr int CX = 8, NW = 4;
     const int width = 32 * CX + 2 * Ri + 8;
     const int pw = width + (width >> 3) + 1;
+    if constexpr (sizeof(T) == 4) {
+        const float2 *ft = reinterpret_cast<const float2 *>(dtaps);
+        if (!mask && form == 1) return launch_direct_f2<4, 4>(g1, g2, ft, tw, ddx, map, dparts, n, batch, Ri, s);
+        if (!mask && form == 2) return launch_direct_f2<2, 4>(g1, g2, ft, tw, ddx, map, dparts, n, batch, Ri, s);
+        if (!mask && form == 3) return launch_direct_f2<4, 2>(g1, g2, ft, tw, ddx, map, dparts, n, batch, Ri, s);
+        if (!mask && form == 4) return launch_direct_f2<2, 8>(g1, g2, ft, tw, ddx, map, dparts, n, batch, Ri, s);
+    }
     if (!mask) {
         constexpr int RY = 4, TX = 32 * CX, TY = NW * RY;
         const size_t smem = 2ull * 2 * pw * sizeof(T);

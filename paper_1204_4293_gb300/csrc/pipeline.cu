@@ -536,6 +536,10 @@ int fm_tune(int knob, int64_t value)
         g_use_tma.store(value < 0 ? kDefaultTma : (int)value);
         return FM_OK;
     case FM_TUNE_WAIT_TEST: g_wait_test.store(value > 0 ? 1 : 0); return FM_OK;
+    case FM_TUNE_DIRECT:
+        if (value > 4) return einval("FM_TUNE_DIRECT takes 0 .. 4");
+        g_direct_form.store(value < 0 ? -1 : (int)value);
+        return FM_OK;
     case FM_TUNE_TILE:
         if (value > 1) return einval("FM_TUNE_TILE takes 0 or 1");
         g_tile_variant.store(value < 0 ? -1 : (int)value);

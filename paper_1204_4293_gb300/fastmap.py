@@ -64,6 +64,7 @@ _SIGS = {
     "fm_map_starlet": (_I, [_P, _P, _P, _I, _I, _I, _CFG, _P]),
     "fm_map_starlet_host": (_I, [_P, _P, _P, _I, _I, _I, _CFG, _P]),
     "fm_map_direct": (_I, [_P, _P, _P, _I, _I, _D, _I, _D, _CFG, _P]),
+    "fm_map_direct_batch": (_I, [_P, _P, _P, _I, _I, _I, _D, _I, _D, _CFG, _P]),
     "fm_map_direct_masked": (_I, [_P, _P, _P, ctypes.c_long, _P, _P, _I, _I, _I, _D, _I, _D, _CFG, _P]),
     "fm_map_noise": (_I, [_P, _P, _P, _P, _I, _I, _I, _U64, _CFG, _P]),
     "fm_map_noise_expected": (_I, [_P, _P, _P, _I, _I, _CFG, _P]),
@@ -223,14 +224,21 @@ def fm_map_starlet_host(g1, g2, J, out, boundary=FM_MIRROR, fuse_depth=0, stream
 
 
 def fm_map_direct(g1, g2, filt, theta, ell=3, cut_over_theta=0.0, out=None, stream=None):
-    """Brute-force M_ap map from tangential shear (eq. shearmap)."""
+    """Brute-force M_ap map from tangential shear (eq. shearmap): one [n, n]
+    map (fm_map_direct) or a batch [batch, n, n] in one launch
+    (fm_map_direct_batch)."""
     n, batch = _maps(g1, g2)
-    if batch != 1 or g1.dim() != 2:
-        raise ValueError("fm_map_direct takes one [n, n] map")
     m = torch.empty_like(g1) if out is None else out
+    if m.shape != g1.shape or m.dtype != g1.dtype or not m.is_contiguous():
+        raise ValueError("out must be a contiguous tensor of the maps' shape and dtype")
     c = _cfg(_prec(g1))
-    _check(_lib.fm_map_direct(_ptr(g1), _ptr(g2), _ptr(m), n, int(filt), float(theta), int(ell),
-                              float(cut_over_theta), ctypes.byref(c), _stream(stream)), "fm_map_direct")
+    if g1.dim() == 2:
+        _check(_lib.fm_map_direct(_ptr(g1), _ptr(g2), _ptr(m), n, int(filt), float(theta), int(ell),
+                                  float(cut_over_theta), ctypes.byref(c), _stream(stream)), "fm_map_direct")
+    else:
+        _check(_lib.fm_map_direct_batch(_ptr(g1), _ptr(g2), _ptr(m), n, batch, int(filt), float(theta), int(ell),
+                                        float(cut_over_theta), ctypes.byref(c), _stream(stream)),
+               "fm_map_direct_batch")
     return m
 
 
@@ -323,6 +331,7 @@ def fm_noise_finalize(sums, R_total, pyramid=None, dtype=torch.float32, stream=N
 
 FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS, FM_TUNE_CHUNK_STREAMS, FM_TUNE_PDL, FM_TUNE_TILE, FM_TUNE_TMA = 1, 2, 3, 4, 5, 6
 FM_TUNE_WAIT_TEST = 7
+FM_TUNE_DIRECT = 8
 
 
 def fm_tune(knob: int, value: int) -> None:

@@ -53,3 +53,48 @@ def test_map_direct_paper_size_sampled(filt, theta, n):
     ref = oracle.map_direct_at(g1.astype(np.float64), g2.astype(np.float64), ys, xs, filt, theta)
     rms = np.sqrt(np.mean(ref[:2000] ** 2))
     assert np.abs(m[ys, xs] - ref).max() / rms <= 1e-5
+
+
+@pytest.mark.parametrize("filt,theta,n,batch", [(1, 4.0, 300, 3), (0, 8.0, 129, 2), (2, 2.0, 64, 5)])
+def test_map_direct_batch_matches_oracle_and_single_calls(filt, theta, n, batch):
+    # one launch over a batch of maps (ragged n: partial tiles on both axes)
+    # against the oracle map by map, and against single-map calls
+    fm = _fm()
+    side = 1 << max(3, (n - 1).bit_length())
+    maps = []
+    for b in range(batch):
+        g1, g2 = shear(side, seed=50 + b, dtype=np.float32)
+        maps.append((np.ascontiguousarray(g1[:n, :n]), np.ascontiguousarray(g2[:n, :n])))
+    t1 = torch.from_numpy(np.stack([m[0] for m in maps])).cuda()
+    t2 = torch.from_numpy(np.stack([m[1] for m in maps])).cuda()
+    out = fm.fm_map_direct(t1, t2, filt, theta).cpu().numpy()
+    for b in range(batch):
+        ref = oracle.map_direct(maps[b][0].astype(np.float64), maps[b][1].astype(np.float64), filt, theta)
+        assert rel_err(out[b], ref) <= 1e-5
+        one = fm.fm_map_direct(t1[b].contiguous(), t2[b].contiguous(), filt, theta).cpu().numpy()
+        assert np.array_equal(one, out[b])
+
+
+@pytest.mark.parametrize("form", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("theta", [6.0, 40.0])
+def test_map_direct_kernel_forms_match_oracle(form, theta):
+    # every kernel form of the unmasked fp32 sum (scalar FMAs, packed
+    # two-lane FMAs in four tile shapes) on a ragged field; theta = 40 splits
+    # each tile's input rows into parts summed by a second kernel, written
+    # here into an output that is only 4-byte aligned
+    fm = _fm()
+    n = 160
+    g1, g2 = shear(256, seed=61, dtype=np.float32)
+    g1, g2 = np.ascontiguousarray(g1[:n, :n]), np.ascontiguousarray(g2[:n, :n])
+    ref = oracle.map_direct(g1.astype(np.float64), g2.astype(np.float64), 1, theta)
+    t1, t2 = torch.from_numpy(g1).cuda(), torch.from_numpy(g2).cuda()
+    base = torch.full((n * n + 1,), float("nan"), device="cuda")
+    out = base[1:].view(n, n)
+    fm.fm_tune(fm.FM_TUNE_DIRECT, form)
+    try:
+        m = fm.fm_map_direct(t1, t2, 1, theta).cpu().numpy()
+        fm.fm_map_direct(t1, t2, 1, theta, out=out)
+    finally:
+        fm.fm_tune(fm.FM_TUNE_DIRECT, -1)
+    assert rel_err(m, ref) <= 1e-5
+    assert np.array_equal(out.cpu().numpy(), m)
