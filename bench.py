@@ -44,17 +44,19 @@ def disc_taps(R):
     return sum(2 * int(np.floor(np.sqrt(R * R - dy * dy))) + 1 for dy in range(-Ri, Ri + 1)) - 1
 
 
-def algo_bytes_per_px_launch(kernel, fuse):
+def algo_bytes_per_px_launch(kernel, fuse, ks_real=False):
     """Algorithmic bytes per map pixel that one launch of `kernel` moves
     (fp32): what the kernel must read and write once.  FFT passes move
-    complex maps; the KS row passes the real shear / convergence; the tile
-    kernel reads kappa and writes `fuse` bands + c_fuse; a large scale's row
-    pass reads c and writes r; its column pass reads r and c and writes c
-    and w_j; the fused column + next-row kernel also writes the next r."""
+    complex maps (the real-output inverse: the column pass writes, and the
+    row inverse reads, the half spectrum, 4 B/px); the KS row passes the real
+    shear / convergence; the tile kernel reads kappa and writes `fuse` bands
+    + c_fuse; a large scale's row pass reads c and writes r; its column pass
+    reads r and c and writes c and w_j; the fused column + next-row kernel
+    also writes the next r."""
     return {
         "fft_rows_fwd": 8 + 8,
-        "fft_cols_ks": 8 + 8,
-        "fft_rows_inv": 8 + 4,
+        "fft_cols_ks": 8 + (4 if ks_real else 8),
+        "fft_rows_inv": (4 if ks_real else 8) + 4,
         "starlet_tile": 4 + 4 * fuse + 4,
         "starlet_row": 4 + 4,
         "starlet_col": 4 + 4 + 4 + 4,
@@ -114,7 +116,7 @@ def method_groups(J, fuse):
     }
 
 
-def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src):
+def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=False):
     """The roofline of the dominant kernel group on the method bytes above,
     each group's fraction, and the whole step's.  per_kind: kind -> (device
     ms per step, launches per step), from CUDA events around each launch."""
@@ -134,7 +136,7 @@ def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src):
         achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
         # the kernels' own reads and writes per unit launch (a large scale's
         # row pass 8 B/px and column pass 16 B/px through L2 or HBM)
-        kern_bytes = sum(algo_bytes_per_px_launch(k, fuse) for k in ks) * px_step / chunks
+        kern_bytes = sum(algo_bytes_per_px_launch(k, fuse, ks_real) for k in ks) * px_step / chunks
         trf = [ncu_traffic(k) for k in ks]
         groups[name] = {"kernels": ks, "method_bytes_per_px": bpp * units, "ms_per_step": ms,
                         "launches_per_step": launches, "avg_launch_ms": avg_ms,
@@ -445,7 +447,7 @@ def side_legs(fm, torch, n, J, g1, g2, pyr):
     return out
 
 
-def per_kernel_hbm(fm, fn, px, fuse, reps=3):
+def per_kernel_hbm(fm, fn, px, fuse, reps=3, ks_real=False):
     """Per kernel kind: device time per call (CUDA events around each launch,
     chunks on one stream), launches, algorithmic bytes per launch and the
     fraction of the measured HBM copy bandwidth that they reach."""
@@ -468,7 +470,7 @@ def per_kernel_hbm(fm, fn, px, fuse, reps=3):
     chunks = res["fft_rows_fwd"][1]
     out = {}
     for k, (ms, cnt) in res.items():
-        b = algo_bytes_per_px_launch(k, fuse) * px / chunks
+        b = algo_bytes_per_px_launch(k, fuse, ks_real) * px / chunks
         gbs = b * cnt / (ms * 1e-3) / 1e9
         out[k] = {"ms_per_call": ms, "launches": cnt, "algorithmic_bytes_per_launch": b, "gbs": gbs,
                   "frac_hbm": gbs / peak}
@@ -494,7 +496,9 @@ def large_fields_leg(fm, torch, J=9):
                            "hbm_algorithmic_gbs": (12 + 4 * (J + 1)) * n * n * B / (ms * 1e-3) / 1e9,
                            "plan": plan, "ms_builtin_plan": ms_builtin}
         if B > 1:  # maps far larger than L2: each kernel's HBM roofline fraction
-            out[f"{B}x{n}"]["per_kernel"] = per_kernel_hbm(fm, fn, n * n * B, plan["fuse_depth"])
+            out[f"{B}x{n}"]["per_kernel"] = per_kernel_hbm(fm, fn, n * n * B, plan["fuse_depth"],
+                                                           ks_real=fm.fm_ks_real_output(n))
+            out[f"{B}x{n}"]["ks_real_output"] = fm.fm_ks_real_output(n)
         del g1, g2, pyr
         torch.cuda.empty_cache()
     return out
@@ -730,7 +734,7 @@ def main():
                        "plan": plan if plan else "built-in rules (--no-autotune)",
                        "l2": f"inputs larger than L2: {2 * B * n * n * 4 / 2**20:.0f} MB shear in + "
                              f"{B * J * n * n * 4 / 2**20:.0f} MB pyramid out per step"},
-            "roofline": step_roofline(per_kind, px_step, J, fuse, ms_max, peak, peak_src),
+            "roofline": step_roofline(per_kind, px_step, J, fuse, ms_max, peak, peak_src, fm.fm_ks_real_output(n)),
             "kernel_breakdown_ms_per_step": {k: v[0] for k, v in per_kind.items()},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * B * n * n * 4,
                     "d2h_bytes_per_step": B * J * n * n * 4, "ms_per_step": float(te.item()),

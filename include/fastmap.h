@@ -286,6 +286,11 @@ int64_t fm_launch_count(void);     /* kernels launched by this library so far */
  * their number and the largest one in bytes; reset != 0 zeroes both after
  * reading.  Either pointer may be NULL. */
 int fm_alloc_stats(int64_t *count, int64_t *max_bytes, int reset);
+/* 1 if the inverse KS of n x n fp32 maps without kappa_B takes the
+ * real-output path (half spectrum) under the current FM_TUNE_KS_REAL
+ * setting, 0 if the complex one; batched != 0 asks for the chunks of
+ * fm_map_starlet / fm_map_noise, 0 for fm_ks_invert. */
+int fm_ks_real_output(int n, int batched);
 /* 1 if a kernel on the current device gave up waiting for a bulk tensor copy
  * (an iteration-bounded wait that ran out; its outputs are then missing),
  * else 0; clears the flag.  Synchronises with the device.  FM_EINVAL if no
@@ -327,6 +332,14 @@ int fm_device_error(void);
  *                        2, 3, 4 = the same with 2 x 8 per lane and 4 warps,
  *                        4 x 8 and 2 warps, 2 x 8 and 8 warps; default: 2
  *                        below a 48-pixel cut radius, else 3
+ *   FM_TUNE_KS_REAL      inverse KS without kappa_B: 1 = compute only the
+ *                        Hermitian half of kappa_E's spectrum (real-output
+ *                        column and row passes; fp32, n >= 64, kappa_E
+ *                        16-byte aligned), 0 = the complex inverse and its
+ *                        real part; default: the real output for
+ *                        fm_ks_invert with 64 <= n <= 4096 and for the
+ *                        batched pipeline's chunks of 4096^2 maps (the sizes
+ *                        where it measured faster)
  * FM_TUNE_CHUNK_BYTES set this way also overrides autotuned budgets. */
 #define FM_TUNE_CHUNK_BYTES 1
 #define FM_TUNE_GRAPHS 2
@@ -336,6 +349,7 @@ int fm_device_error(void);
 #define FM_TUNE_TMA 6
 #define FM_TUNE_WAIT_TEST 7
 #define FM_TUNE_DIRECT 8
+#define FM_TUNE_KS_REAL 9
 int fm_tune(int knob, int64_t value);
 
 /* ---- autotuner ----------------------------------------------------------------

@@ -169,13 +169,19 @@ int check_config(const fm_config &c);
 cudaError_t smem_attr(const void *kernel, size_t bytes);
 
 // ---- internal launchers (defined per .cu file) ------------------------------------
+// batched: a chunk of the batched KS + starlet pipeline (the real-output
+// inverse is chosen by ks_real_for(n, batched))
 int launch_ks(const void *in1, const void *in2, long in_bstride, void *out1, void *out2, void *work, int n, int batch,
-              int precision, bool forward, uint64_t rot_seed, int rot_r0, bool rotate, cudaStream_t s);
+              int precision, bool forward, uint64_t rot_seed, int rot_r0, bool rotate, cudaStream_t s,
+              bool batched = false);
 // bands_only: the smooth array c_{J-1} is not written (noise realisations)
 int launch_starlet(const void *kappa, void *pyr, long pyr_bstride, int n, int J, int batch, const fm_config &cfg,
                    void *scratch, cudaStream_t s, bool bands_only = false);
+// tw2: the twiddle table of n/2 (the real-output inverse), or null for the
+// complex inverse
 int launch_ks32(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int n,
-                int batch, bool forward, uint64_t seed, int r0, bool rotate, const float2 *tw, cudaStream_t s);
+                int batch, bool forward, uint64_t seed, int r0, bool rotate, const float2 *tw, const float2 *tw2,
+                cudaStream_t s);
 // Spectral operation of the column pass of the 2-D FFT pipeline
 // rows FFT -> columns FFT -> op -> columns IFFT -> rows IFFT (Re, Im):
 //   FFT_OP_KS_INV   multiply by conj(D)  (KS inversion, Sec. 4.5)
@@ -186,10 +192,15 @@ int launch_ks32(const float *in1, const float *in2, long in_bs, float *out1, flo
 enum { FFT_OP_KS_INV = 0, FFT_OP_KS_FWD = 1, FFT_OP_FILTER = 2, FFT_OP_SPECTRUM = 3 };
 int launch_fft_op(const void *in1, const void *in2, long in_bstride, void *out1, void *out2, void *work, int n,
                   int batch, int precision, int op, const void *filt, double out_scale, uint64_t rot_seed, int rot_r0,
-                  bool rotate, cudaStream_t s);
+                  bool rotate, cudaStream_t s, bool real_ok = false);
 int launch_fft32(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int n,
                  int batch, int op, const float2 *filt, float out_scale, uint64_t seed, int r0, bool rotate,
-                 const float2 *tw, cudaStream_t s);
+                 const float2 *tw, const float2 *tw2, cudaStream_t s);
+// inverse KS with a real output (kappa_E only) through the half spectrum
+// (FM_TUNE_KS_REAL): -1 = by size (default), 0 = never, 1 = whenever
+// possible (fp32, n >= 64)
+extern std::atomic<int> g_ks_real;
+bool ks_real_for(int n, bool batched);
 size_t starlet_scratch_elems(int n, int J, int batch, const fm_config &cfg);
 // ---- autotuned plans (tune.cu) ----------------------------------------------------
 // A plan for maps of n^2, J scales, one precision: fused depth, large-scale

@@ -279,7 +279,7 @@ static int ks_impl(const T *in1, const T *in2, long in_bstride, T *out1, T *out2
 
 int launch_fft_op(const void *in1, const void *in2, long in_bstride, void *out1, void *out2, void *work, int n,
                   int batch, int precision, int op, const void *filt, double out_scale, uint64_t rot_seed, int rot_r0,
-                  bool rotate, cudaStream_t s)
+                  bool rotate, cudaStream_t s, bool real_ok)
 {
     if (precision == FM_F64)
         return ks_impl<double>((const double *)in1, (const double *)in2, in_bstride, (double *)out1, (double *)out2,
@@ -289,9 +289,13 @@ int launch_fft_op(const void *in1, const void *in2, long in_bstride, void *out1,
         int st = FM_OK;
         const float2 *tw = static_cast<const float2 *>(twiddles(n, FM_F32, s, &st));
         if (!tw) return st;
+        const float2 *tw2 = nullptr;  // the half-length table of the real-output inverse
+        if (real_ok && n >= 64 && op == FFT_OP_KS_INV && !out2 &&
+            !(tw2 = static_cast<const float2 *>(twiddles(n / 2, FM_F32, s, &st))))
+            return st;
         return launch_fft32((const float *)in1, (const float *)in2, in_bstride, (float *)out1, (float *)out2,
                             (float2 *)work, n, batch, op, (const float2 *)filt, (float)out_scale, rot_seed, rot_r0,
-                            rotate, tw, s);
+                            rotate, tw, tw2, s);
     }
     return ks_impl<float>((const float *)in1, (const float *)in2, in_bstride, (float *)out1, (float *)out2,
                           (float2 *)work, n, batch, op, (const float2 *)filt, (float)out_scale, rot_seed, rot_r0,
@@ -299,10 +303,11 @@ int launch_fft_op(const void *in1, const void *in2, long in_bstride, void *out1,
 }
 
 int launch_ks(const void *in1, const void *in2, long in_bstride, void *out1, void *out2, void *work, int n, int batch,
-              int precision, bool forward, uint64_t rot_seed, int rot_r0, bool rotate, cudaStream_t s)
+              int precision, bool forward, uint64_t rot_seed, int rot_r0, bool rotate, cudaStream_t s, bool batched)
 {
     return launch_fft_op(in1, in2, in_bstride, out1, out2, work, n, batch, precision,
-                         forward ? FFT_OP_KS_FWD : FFT_OP_KS_INV, nullptr, 1.0, rot_seed, rot_r0, rotate, s);
+                         forward ? FFT_OP_KS_FWD : FFT_OP_KS_INV, nullptr, 1.0, rot_seed, rot_r0, rotate, s,
+                         !forward && ks_real_for(n, batched));
 }
 
 }  // namespace fm

@@ -18,6 +18,26 @@
 //                stays in registers.  The spectrum-only mode stores the 2-D
 //                spectrum after the forward transform.
 //   rows_inv32 : row inverse FFT -> (Re, Im) * scale / n^2
+//
+// Real-output inverse (kappa_E alone, n >= 64).  kappa_E is real, so half of
+// its spectrum carries it.  With Gamma1, Gamma2 the 2-D spectra of the real
+// maps gamma1 and gamma2, the Hermitian part of conj(D) gamma_hat is
+//   kappa_E_hat = Re(D) Gamma1 + Im(D) Gamma2,
+// except on the Nyquist row and column (one index n/2, the other neither 0
+// nor n/2), where the index convention k = -n/2 makes D(-k) = conj(D(k)) and
+// the Hermitian part is conj(D) Gamma1.  Three passes, 36 instead of 44 bytes
+// per pixel and three quarters of the butterflies:
+//   rows_fwd32<SPLIT> : the complex row FFT Z of gamma1 + i gamma2 split into
+//                       the half spectra Gamma1 = (Z(kx) + conj Z(-kx)) / 2,
+//                       Gamma2 = (Z(kx) - conj Z(-kx)) / 2i, kx = 0 .. n/2,
+//                       each row stored as [Gamma1 | Gamma2], n/2 float2 each,
+//                       slot 0 packing the real pair (X(0), X(n/2));
+//   cols_ks32_e       : per strip of WS slots, column FFTs of the Gamma1 and
+//                       Gamma2 slots, kappa_E_hat, column inverse FFT; writes
+//                       the half spectrum H [n][n/2] into kappa's buffer;
+//   rows_inv32_c2r    : in place in kappa's buffer, each row's length-n
+//                       complex-to-real inverse as one length-n/2 complex
+//                       inverse FFT (even samples real part, odd imaginary).
 #include "common.cuh"
 #include "dft.cuh"
 #include "rng.cuh"
@@ -58,16 +78,26 @@ template <bool INV> __device__ __forceinline__ float2 twid(const float2 *__restr
 // In: v[r] = x[j + r TV].  Out: v[m RL + r] = X[j + m TV + r NSL].
 // Element i of the vector lives at sm[pad32(i W + c)] between passes.
 // Every thread of the CTA must call this (it holds barriers).
-template <int LOGN, int W, bool INV>
+// barrier of the threads taking part: the whole CTA (NB = 0) or the first NB
+// threads (named barrier 1; NB a multiple of 32)
+template <int NB> __device__ __forceinline__ void part_sync()
+{
+    if constexpr (NB == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync 1, %0;" ::"n"(NB) : "memory");
+}
+
+template <int LOGN, int W, bool INV, int NB = 0>
 __device__ __forceinline__ void fft_vec(float2 (&v)[32], float2 *sm, int c, int j, const float2 *__restrict__ tw)
 {
     using P = Plan32<LOGN>;
     Dft<32, INV, float2>::run(v);  // pass 1: Ns = 1, no twiddles; outputs at 32 j + r
     if constexpr (P::NPASS > 1) {
-        __syncthreads();  // the buffer may still be read by an earlier pass
+        part_sync<NB>();  // the buffer may still be read by an earlier pass
 #pragma unroll
         for (int r = 0; r < 32; ++r) sm[pad32((j * 32 + r) * W + c)] = v[r];
-        __syncthreads();
+        part_sync<NB>();
         if constexpr (P::NPASS > 2) {
             // pass 2: radix 32, Ns = 32
             constexpr int NS = 32;
@@ -78,11 +108,11 @@ __device__ __forceinline__ void fft_vec(float2 (&v)[32], float2 *sm, int c, int 
 #pragma unroll
             for (int r = 1; r < 32; ++r) v[r] = cmul(v[r], twid<INV>(tw, r * step));
             Dft<32, INV, float2>::run(v);
-            __syncthreads();
+            part_sync<NB>();
             const int o = (j - k) * 32 + k;
 #pragma unroll
             for (int r = 0; r < 32; ++r) sm[pad32((o + r * NS) * W + c)] = v[r];
-            __syncthreads();
+            part_sync<NB>();
         }
         // last pass: radix RL, Ns = NSL, butterfly b = j + m TV (< NSL), twiddle W_n^(r b)
 #pragma unroll
@@ -103,7 +133,7 @@ __device__ __forceinline__ void fft_vec(float2 (&v)[32], float2 *sm, int c, int 
 // rows of gamma1 (m1) and gamma2 (m2) arrive by bulk tensor copies into the
 // exchange buffer, viewed as [RPC][n] floats per array, before the first
 // pass reads them.
-template <int LOGN>
+template <int LOGN, bool SPLIT>
 __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__ in1, const float *__restrict__ in2,
                                                        long in_bs, float2 *__restrict__ work, long total_rows,
                                                        const float2 *__restrict__ tw, uint64_t seed, int r0,
@@ -166,6 +196,33 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__
         for (int r = 0; r < 32; ++r) v[r] = make_float2(0.f, 0.f);
     }
     fft_vec<LOGN, 1, false>(v, sm, 0, j, tw);
+    if constexpr (SPLIT && P::NPASS > 1) {
+        // Z through the exchange buffer so that Z(kx) and Z(n - kx) meet
+        __syncthreads();  // the last pass's reads of the buffer
+#pragma unroll
+        for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+            for (int r = 0; r < P::RL; ++r) sm[pad32(j + m * P::TV + r * P::NSL)] = v[m * P::RL + r];
+        __syncthreads();
+        if (live) {
+            float2 *d1 = work + row * P::N, *d2 = d1 + P::N / 2;  // Gamma1 slots, Gamma2 slots
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const int kx = j + t * P::TV;
+                const float2 a = sm[pad32(kx)];
+                if (kx == 0) {
+                    const float2 h = sm[pad32(P::N / 2)];
+                    d1[0] = make_float2(a.x, h.x);
+                    d2[0] = make_float2(a.y, h.y);
+                } else {
+                    const float2 bm = sm[pad32(P::N - kx)];  // Z(n - kx); B = conj of it
+                    d1[kx] = make_float2(0.5f * (a.x + bm.x), 0.5f * (a.y - bm.y));
+                    d2[kx] = make_float2(0.5f * (a.y + bm.y), -0.5f * (a.x - bm.x));
+                }
+            }
+        }
+        return;
+    }
     if (live) {
         float2 *dst = work + row * P::N;
 #pragma unroll
@@ -336,12 +393,308 @@ __global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, co
         for (int r = 0; r < P::RL; ++r) base[(long)(j + m * P::TV + r * P::NSL) * N] = v[m * P::RL + r];
 }
 
+// ---- real-output inverse: column and row kernels ------------------------------
+// Slots per column strip (WS, 16-byte or wider row segments for the bulk
+// tensor copies).  A CTA of 2 WS n/32 threads: its first half transforms the
+// strip's Gamma1 columns, the second half the Gamma2 columns, at the same
+// time (the occupancy of the complex column pass); the second half hands its
+// spectra over through shared memory and leaves, and the first half forms
+// kappa_E_hat and runs the one inverse transform per slot on its own named
+// barrier.
+template <int LOGN> struct PlanE {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int WS = N <= 256 ? 16 : (N == 512 ? 8 : (N == 1024 ? 4 : (N <= 4096 ? 2 : 1)));
+    static constexpr int RSZ = (N * WS + N * WS / 32 + 1 + 15) & ~15;  // float2 per region, 128-byte multiple
+    // the corner strip's dense exchange (2n elements) goes to the Gamma1
+    // region after its transform; its second half needs a region of its own
+    // when that one is too small (WS = 1)
+    static constexpr int R3 = RSZ >= 2 * N ? 0 : N;
+    static constexpr int NH = WS * N / 32;  // threads of one half
+    static constexpr int NT = 2 * NH;
+    // CTAs per SM the register budget must allow: at most 128 registers a thread
+    static constexpr int MINB = 65536 / (NT * 128) < 1 ? 1 : (65536 / (NT * 128) > 8 ? 8 : 65536 / (NT * 128));
+};
+
+// With use_tma (WS >= 2; mw: the work buffer as floats {2n, n, batch}, box
+// {2 WS, min(n, 256), 1}) the strip's Gamma1 and Gamma2 slots arrive by bulk
+// tensor copies, else by per-thread loads.
+template <int LOGN>
+__global__ void __launch_bounds__(PlanE<LOGN>::NT, PlanE<LOGN>::MINB)
+    k_cols_ks32_e(const float2 *__restrict__ work, float2 *__restrict__ half, const float2 *__restrict__ tw,
+                  const __grid_constant__ CUtensorMap mw, int use_tma)
+{
+    pdl_entry();
+    using P = Plan32<LOGN>;
+    using E = PlanE<LOGN>;
+    constexpr int N = P::N, WS = E::WS, NH = E::NH;
+    constexpr int STRIPS = N / 2 / WS;
+    extern __shared__ __align__(16) unsigned char smem_col[];
+    float2 *R1 = align128<float2>(smem_col);
+    float2 *R2 = R1 + E::RSZ;
+    float2 *U1 = R1, *U2 = E::R3 ? R2 + E::RSZ : R1 + N;  // corner exchange
+    const long b = blockIdx.x / STRIPS;
+    const int s0 = (blockIdx.x % STRIPS) * WS;
+    const int tid = threadIdx.x, hf = tid / NH, t = tid % NH, c = t % WS, j = t / WS;
+    float2 *R = hf ? R2 : R1;  // this half's strip and exchange region
+    float2 v[32];
+    if (use_tma) {
+        __shared__ uint64_t bar;
+        constexpr int BR = N < 256 ? N : 256;  // rows per copy
+        if (tid == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        if (tid == 0) {
+            mbar_expect_tx(&bar, (uint32_t)(2 * N * WS * sizeof(float2)));
+            for (int k = 0; k < N / BR; ++k) {
+                tma_load_3d(R1 + k * BR * WS, &mw, 2 * s0, k * BR, (int)b, &bar);
+                tma_load_3d(R2 + k * BR * WS, &mw, N + 2 * s0, k * BR, (int)b, &bar);
+            }
+        }
+        if (!tma_wait_all(&bar, 0)) return;  // the copies never completed (flagged)
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = R[(j + r * P::TV) * WS + c];
+    } else {
+        // rows of n float2: [Gamma1 | Gamma2]
+        const float2 *src = work + b * (long)N * N + hf * (N / 2) + s0 + c;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = src[(long)(j + r * P::TV) * N];
+    }
+    fft_vec<LOGN, WS, false>(v, R, c, j, tw);  // Gamma1_hat (first half), Gamma2_hat (second)
+    __syncthreads();                           // the last passes' reads of R1 and R2 are done
+    if (hf) {
+#pragma unroll
+        for (int e = 0; e < 32; ++e) R2[e * NH + t] = v[e];  // for the thread t of the first half
+    }
+    __syncthreads();
+    if (hf) return;  // the rest runs on named barrier 1 of the first NH threads
+    const bool corner = s0 == 0 && c == 0;  // slot 0: kx = 0 and kx = n/2 packed
+    if (!corner) {
+        const int k1 = s0 + c;  // 1 .. n/2 - 1
+#pragma unroll
+        for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+            for (int r = 0; r < P::RL; ++r) {
+                const int e = m * P::RL + r, yi = j + m * P::TV + r * P::NSL;
+                const int k2 = yi < N / 2 ? yi : yi - N;
+                const float inv = 1.f / (float)(k1 * k1 + k2 * k2);
+                const float dr = (float)(k1 * k1 - k2 * k2) * inv, di = (float)(2 * k1 * k2) * inv;
+                const float2 a = v[e], g = R2[e * NH + t];
+                v[e] = yi == N / 2 ? make_float2(dr * a.x + di * a.y, dr * a.y - di * a.x)  // conj(D) Gamma1
+                                   : make_float2(dr * a.x + di * g.x, dr * a.y + di * g.y);
+            }
+    }
+    if (s0 == 0) {  // CTA-uniform: the corner column pair needs ky and -ky together
+        if (c == 0) {
+#pragma unroll
+            for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+                for (int r = 0; r < P::RL; ++r) {
+                    const int e = m * P::RL + r, yi = j + m * P::TV + r * P::NSL;
+                    U1[yi] = v[e];
+                    U2[yi] = R2[e * NH + t];
+                }
+        }
+        part_sync<NH>();
+        if (c == 0) {
+#pragma unroll
+            for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+                for (int r = 0; r < P::RL; ++r) {
+                    const int e = m * P::RL + r, yi = j + m * P::TV + r * P::NSL;
+                    const int yp = (N - yi) & (N - 1);
+                    const float2 p1 = U1[yi], q1 = U1[yp], p2 = U2[yi], q2 = U2[yp];
+                    // A = Gamma(ky, 0) = (P + conj P(-ky)) / 2, B = Gamma(ky, n/2) = (P - conj P(-ky)) / 2i
+                    const float2 a1 = make_float2(0.5f * (p1.x + q1.x), 0.5f * (p1.y - q1.y));
+                    const float2 b1 = make_float2(0.5f * (p1.y + q1.y), -0.5f * (p1.x - q1.x));
+                    const float2 b2 = make_float2(0.5f * (p2.y + q2.y), -0.5f * (p2.x - q2.x));
+                    const int k2 = yi < N / 2 ? yi : yi - N;
+                    // kx = 0: D = -1 (0 at k = 0)
+                    const float2 kz = yi == 0 ? make_float2(0.f, 0.f) : make_float2(-a1.x, -a1.y);
+                    // kx = n/2 (k1 = -n/2)
+                    const float inv = 1.f / (float)(N / 2 * (N / 2) + k2 * k2);
+                    const float dr = (float)(N / 2 * (N / 2) - k2 * k2) * inv, di = (float)(-N * k2) * inv;
+                    const float2 kh = (yi == 0 || yi == N / 2)
+                                          ? make_float2(dr * b1.x + di * b2.x, dr * b1.y + di * b2.y)
+                                          : make_float2(dr * b1.x + di * b1.y, dr * b1.y - di * b1.x);
+                    v[e] = make_float2(kz.x - kh.y, kz.y + kh.x);  // packed kz + i kh
+                }
+        }
+    }
+    if constexpr (!(P::RL == 32 || P::NPASS == 1)) {
+        // bring the spectrum back to the inverse's input order x[j + r TV]
+        part_sync<NH>();
+#pragma unroll
+        for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+            for (int r = 0; r < P::RL; ++r) R1[pad32((j + m * P::TV + r * P::NSL) * WS + c)] = v[m * P::RL + r];
+        part_sync<NH>();
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = R1[pad32((j + r * P::TV) * WS + c)];
+    }
+    fft_vec<LOGN, WS, true, NH>(v, R1, c, j, tw);
+    float2 *dst = half + b * (long)N * (N / 2) + s0 + c;
+#pragma unroll
+    for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+        for (int r = 0; r < P::RL; ++r) dst[(long)(j + m * P::TV + r * P::NSL) * (N / 2)] = v[m * P::RL + r];
+}
+
+// In place: row y of kap holds the half spectrum H(y, 0 .. n/2) as n/2 float2
+// (slot 0 = the real pair H(0), H(n/2)) and receives kappa_E's row.  With
+// use_tma (n >= 128; mk: kap as floats {d0, n/d0, rows}) the CTA's rows are
+// staged by one bulk tensor copy.  Every read of the row precedes the
+// transform's first barrier, and every write follows it.
+template <int LOGN>
+__global__ void __launch_bounds__(256, 2) k_rows_inv32_c2r(float *kap, long total_rows, const float2 *__restrict__ tw,
+                                                           const float2 *__restrict__ tw2, float scale,
+                                                           const __grid_constant__ CUtensorMap mk, int use_tma)
+{
+    pdl_entry();
+    using P = Plan32<LOGN - 1>;  // the length n/2 complex transform
+    constexpr int N2 = P::N;
+    constexpr int RPC = P::TV >= kRowThreads ? 1 : kRowThreads / P::TV;
+    extern __shared__ __align__(16) float2 sm32[];
+    __shared__ uint64_t bar;
+    float2 *smb = align128<float2>(sm32);
+    const int vr = threadIdx.x / P::TV, j = threadIdx.x % P::TV;
+    const long row = (long)blockIdx.x * RPC + vr;
+    float2 *sm = smb + vr * (N2 + N2 / 32);
+    const bool live = row < total_rows;
+    const float2 *h = reinterpret_cast<const float2 *>(kap) + row * N2;
+    if constexpr (P::NPASS > 1) {
+        if (use_tma) {
+            if (threadIdx.x == 0) mbar_init(&bar, 1);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                mbar_expect_tx(&bar, (uint32_t)(RPC * N2 * sizeof(float2)));
+                tma_load_3d(smb, &mk, 0, 0, (int)((long)blockIdx.x * RPC), &bar);
+            }
+            if (!tma_wait_all(&bar, 0)) return;  // the copy never completed (flagged)
+            h = smb + vr * N2;
+        }
+    }
+    float2 v[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const int k = j + r * P::TV;
+        float2 z = make_float2(0.f, 0.f);
+        if (live) {
+            const float2 hk = h[k];
+            if (k == 0) {
+                z = make_float2(hk.x + hk.y, hk.x - hk.y);
+            } else {
+                const float2 hm = h[N2 - k];
+                const float2 ee = make_float2(hk.x + hm.x, hk.y - hm.y);  // H(k) + conj H(n/2 - k)
+                float2 od = make_float2(hk.x - hm.x, hk.y + hm.y);        // H(k) - conj H(n/2 - k)
+                od = cmul(od, twid<true>(tw, k));                         // times exp(+2 pi i k / n)
+                z = make_float2(ee.x - od.y, ee.y + od.x);
+            }
+        }
+        v[r] = z;
+    }
+    fft_vec<LOGN - 1, 1, true>(v, sm, 0, j, tw2);
+    if (live) {
+        float2 *out = reinterpret_cast<float2 *>(kap) + row * N2;  // (kappa(2m), kappa(2m + 1))
+#pragma unroll
+        for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+            for (int r = 0; r < P::RL; ++r) {
+                const float2 z = v[m * P::RL + r];
+                out[j + m * P::TV + r * P::NSL] = make_float2(z.x * scale, z.y * scale);
+            }
+    }
+}
+
+std::atomic<int> g_ks_real{-1};
+
+// Measured on GB300 (ms, complex / real-output inverse): the inverse alone,
+// 32 x 1024^2 0.320 / 0.298, 16 x 2048^2 0.846 / 0.772, 16 x 4096^2 4.20 /
+// 3.81, 64 x 512^2 0.171 / 0.163, 1 x 8192^2 1.45 / 2.03 (its strips of one
+// slot are too narrow for bulk copies); inside the batched KS + starlet
+// chunks (two streams) 32 x 1024^2 0.814 / 0.832, 16 x 2048^2 1.99 / 2.06,
+// 16 x 4096^2 10.83 / 10.50, 64 x 512^2 0.445 / 0.459: there the split row
+// pass and the column pass, whose second half of threads idles through the
+// inverse, overlap worse with the other stream's kernels; on maps larger
+// than L2 the saved bytes win.
+bool ks_real_for(int n, bool batched)
+{
+    const int mode = g_ks_real.load(std::memory_order_relaxed);
+    if (mode >= 0) return mode == 1 && n >= 64;
+    return batched ? n == 4096 : (n >= 64 && n <= 4096);
+}
+
 // ---------------------------------------------------------------------------
+// Real-output inverse KS (kappa_E only): the split row FFT into `work`, the
+// column pass into kappa's buffer `out1` (the half spectrum, [rows][n/2]
+// float2, 16-byte aligned), the complex-to-real row pass in place there.
+template <int LOGN>
+static int ks32_real_impl(const float *in1, const float *in2, long in_bs, float *out1, float2 *work, int batch,
+                          float out_scale, uint64_t seed, int r0, bool rotate, const float2 *tw, const float2 *tw2,
+                          cudaStream_t s)
+{
+    using P = Plan32<LOGN>;
+    using P2 = Plan32<LOGN - 1>;
+    using E = PlanE<LOGN>;
+    constexpr int RPC = P::TV >= kRowThreads ? 1 : kRowThreads / P::TV;
+    constexpr int RPC2 = P2::TV >= kRowThreads ? 1 : kRowThreads / P2::TV;
+    const long total_rows = (long)batch * P::N;
+    const unsigned row_grid = (unsigned)((total_rows + RPC - 1) / RPC);
+    const unsigned row2_grid = (unsigned)((total_rows + RPC2 - 1) / RPC2);
+    const size_t row_smem = (size_t)RPC * (P::N + P::N / 32) * sizeof(float2) + 128;
+    const size_t row2_smem = P2::NPASS > 1 ? (size_t)RPC2 * (P2::N + P2::N / 32) * sizeof(float2) + 128 : 0;
+    const size_t col_smem = (size_t)(2 * E::RSZ + E::R3) * sizeof(float2) + 128;
+    const int col_threads = E::NT;
+    const unsigned col_grid = (unsigned)((long)batch * (P::N / 2 / E::WS));
+    FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_fwd32<LOGN, true>, row_smem));
+    FM_CUDA_TRY(fm::smem_attr((const void *)k_cols_ks32_e<LOGN>, col_smem));
+    if (row2_smem) FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_inv32_c2r<LOGN>, row2_smem));
+    CUtensorMap m1, m2, mc, mk;
+    memset(&m1, 0, sizeof(m1));
+    memset(&m2, 0, sizeof(m2));
+    memset(&mc, 0, sizeof(mc));
+    memset(&mk, 0, sizeof(mk));
+    int tma_in = 0, tma_col = 0, tma_out = 0;
+    const int tma_mode = g_use_tma.load(std::memory_order_relaxed);
+    {
+        const long nn = (long)P::N * P::N;
+        const uint32_t d0 = P::N < 256 ? P::N : 256;
+        const uint64_t rows = in_bs == 0 ? (uint64_t)P::N : (uint64_t)total_rows;
+        const uint64_t dims[3] = {d0, (uint64_t)(P::N / d0), rows};
+        const uint64_t strides[2] = {(uint64_t)d0 * 4, (uint64_t)P::N * 4};
+        const uint32_t box[3] = {d0, (uint32_t)(P::N / d0), (uint32_t)RPC};
+        tma_in = (tma_mode & 2) && (in_bs == nn || (in_bs == 0 && RPC <= P::N)) &&
+                 encode_map3d_f32(&m1, in1, dims, strides, box) && (!in2 || encode_map3d_f32(&m2, in2, dims, strides, box));
+        // kappa's buffer as rows of n floats (= n/2 float2 of half spectrum)
+        if (P2::NPASS > 1 && (tma_mode & 4)) {
+            const uint64_t kdims[3] = {d0, (uint64_t)(P::N / d0), (uint64_t)total_rows};
+            const uint32_t kbox[3] = {d0, (uint32_t)(P::N / d0), (uint32_t)RPC2};
+            tma_out = encode_map3d_f32(&mk, out1, kdims, strides, kbox);
+        }
+    }
+    if (E::WS >= 2 && P::N >= 1024 && (tma_mode & 32)) {
+        const uint64_t cdims[3] = {(uint64_t)2 * P::N, (uint64_t)P::N, (uint64_t)batch};
+        const uint64_t cstrides[2] = {(uint64_t)P::N * 8, (uint64_t)P::N * P::N * 8};
+        const uint32_t cbox[3] = {(uint32_t)(2 * E::WS), (uint32_t)(P::N < 256 ? P::N : 256), 1};
+        tma_col = encode_map3d_f32(&mc, work, cdims, cstrides, cbox) ? 1 : 0;
+    }
+    FM_LAUNCH(FM_K_FFT_ROWS_FWD, (k_rows_fwd32<LOGN, true>), row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs,
+              work, total_rows, tw, seed, r0, rotate ? 1 : 0, m1, m2, tma_in);
+    FM_LAUNCH(FM_K_FFT_COLS_KS, k_cols_ks32_e<LOGN>, col_grid, col_threads, col_smem, s, (const float2 *)work,
+              reinterpret_cast<float2 *>(out1), tw, mc, tma_col);
+    const float scale = out_scale / ((float)P::N * (float)P::N);
+    FM_LAUNCH(FM_K_FFT_ROWS_INV, k_rows_inv32_c2r<LOGN>, row2_grid, RPC2 * P2::TV, row2_smem, s, out1, total_rows, tw,
+              tw2, scale, mk, tma_out);
+    return FM_OK;
+}
+
 template <int LOGN>
 static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int batch,
                      int op, const float2 *filt, float out_scale, uint64_t seed, int r0, bool rotate,
-                     const float2 *tw, cudaStream_t s)
+                     const float2 *tw, const float2 *tw2, cudaStream_t s)
 {
+    if constexpr (LOGN >= 6) {
+        if (op == FFT_OP_KS_INV && !out2 && tw2 && (reinterpret_cast<uintptr_t>(out1) & 15) == 0)
+            return ks32_real_impl<LOGN>(in1, in2, in_bs, out1, work, batch, out_scale, seed, r0, rotate, tw, tw2, s);
+    }
     using P = Plan32<LOGN>;
     constexpr int RPC = P::TV >= kRowThreads ? 1 : kRowThreads / P::TV;
     const long total_rows = (long)batch * P::N;
@@ -353,7 +706,7 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
     // exchange buffer (also the TMA strip: n W float2) + 128 bytes of alignment
     const size_t col_smem = P::NPASS > 1 ? (size_t)(P::N * P::W + P::N * P::W / 32 + 1) * sizeof(float2) + 128 : 0;
     const unsigned col_grid = (unsigned)((long)batch * (P::N / P::W));
-    FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_fwd32<LOGN>, row_smem));
+    FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_fwd32<LOGN, false>, row_smem));
     FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_inv32<LOGN>, row_smem));
     FM_CUDA_TRY(fm::smem_attr((const void *)k_cols_ks32<LOGN>, col_smem));
     // bulk tensor copies of whole row groups (RPC consecutive rows of the
@@ -400,8 +753,8 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
                       ? (1 | ((tma_mode & 64) && P::N >= 8192 ? 2 : 0))
                       : 0;
     }
-    FM_LAUNCH(FM_K_FFT_ROWS_FWD, k_rows_fwd32<LOGN>, row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs, work,
-              total_rows, tw, seed, r0, rotate ? 1 : 0, m1, m2, tma_in);
+    FM_LAUNCH(FM_K_FFT_ROWS_FWD, (k_rows_fwd32<LOGN, false>), row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs,
+              work, total_rows, tw, seed, r0, rotate ? 1 : 0, m1, m2, tma_in);
     FM_LAUNCH(FM_K_FFT_COLS_KS, k_cols_ks32<LOGN>, col_grid, col_threads, col_smem, s, work, tw, op, filt, mc,
               tma_col);
     if (op == FFT_OP_SPECTRUM) return FM_OK;
@@ -415,10 +768,10 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
 // which then uses the generic shared-memory Stockham kernels.
 int launch_fft32(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int n,
                  int batch, int op, const float2 *filt, float out_scale, uint64_t seed, int r0, bool rotate,
-                 const float2 *tw, cudaStream_t s)
+                 const float2 *tw, const float2 *tw2, cudaStream_t s)
 {
 #define FM_KS32(L) \
-    ks32_impl<L>(in1, in2, in_bs, out1, out2, work, batch, op, filt, out_scale, seed, r0, rotate, tw, s)
+    ks32_impl<L>(in1, in2, in_bs, out1, out2, work, batch, op, filt, out_scale, seed, r0, rotate, tw, tw2, s)
     switch (n) {
     case 32: return FM_KS32(5);
     case 64: return FM_KS32(6);
@@ -437,10 +790,11 @@ int launch_fft32(const float *in1, const float *in2, long in_bs, float *out1, fl
 int fft_wait_error(bool clear) { return wait_error_flag(clear); }
 
 int launch_ks32(const float *in1, const float *in2, long in_bs, float *out1, float *out2, float2 *work, int n,
-                int batch, bool forward, uint64_t seed, int r0, bool rotate, const float2 *tw, cudaStream_t s)
+                int batch, bool forward, uint64_t seed, int r0, bool rotate, const float2 *tw, const float2 *tw2,
+                cudaStream_t s)
 {
     return launch_fft32(in1, in2, in_bs, out1, out2, work, n, batch, forward ? FFT_OP_KS_FWD : FFT_OP_KS_INV,
-                        nullptr, 1.f, seed, r0, rotate, tw, s);
+                        nullptr, 1.f, seed, r0, rotate, tw, tw2, s);
 }
 
 }  // namespace fm

@@ -97,6 +97,8 @@ extern "C" int fm_ks_invert_noalloc(const void *g1, const void *g2, void *kappa_
     int r = setup(dev, &st);
     if (r != FM_OK) return r;
     const float2 *tw = st->tw + (n - kTwMinN);  // sum of the smaller tables' sizes
+    // the half-length table for the real-output inverse where it is the faster one
+    const float2 *tw2 = n >= 2 * kTwMinN && ks_real_for(n, false) ? st->tw + (n / 2 - kTwMinN) : nullptr;
     return launch_ks32((const float *)g1, (const float *)g2, (long)n * n, (float *)kappa_E, (float *)kappa_B, st->work,
-                       n, batch, false, 0, 0, false, tw, (cudaStream_t)stream);
+                       n, batch, false, 0, 0, false, tw, tw2, (cudaStream_t)stream);
 }

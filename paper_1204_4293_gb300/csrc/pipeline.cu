@@ -103,7 +103,7 @@ int run_chunk(const char *g1, const char *g2, char *pyr, int n, int J, int b0, i
     char *work = slot, *kap = slot + p.work_b, *st = kap + p.kap_b;
     const size_t in_off = rotate ? 0 : b0 * nn * es;
     int r = launch_ks(g1 + in_off, g2 + in_off, rotate ? 0 : (long)nn, kap, nullptr, work, n, bc, cfg.precision, false,
-                      seed, r0, rotate, s);
+                      seed, r0, rotate, s, true);
     if (r != FM_OK) return r;
     // a noise realisation needs its bands only (the smooth array is not accumulated)
     return launch_starlet(kap, pyr + (size_t)b0 * J * nn * es, (long)J * nn, n, J, bc, cfg, st, s, rotate);
@@ -187,7 +187,7 @@ static int map_starlet_dev(const void *g1, const void *g2, void *pyramid, int n,
         return run_chunks(g1, g2, pyramid, n, J, batch, cfg, p, (char *)sc.p, s, *ds);
     }
     GraphKey key{g1, g2, pyramid, n, J, batch, 0, cfg, p.C, p.slots,
-                 g_pdl.load() | ((g_tile_variant.load() + 1) << 1) | (g_use_tma.load() << 3) | (g_wait_test.load() << 10)};
+                 g_pdl.load() | ((g_tile_variant.load() + 1) << 1) | (g_use_tma.load() << 3) | (g_wait_test.load() << 10) | ((g_ks_real.load() + 1) << 11)};
     FM_CUDA_TRY(cudaGetDevice(&key.dev));
     GraphEntry *hit = nullptr;
     for (auto &e : g_graphs)
@@ -387,7 +387,7 @@ int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out
     DevStreams *ds = nullptr;
     if ((st = dev_streams(&ds))) return st;
     NoiseKey key{g1, g2, var_out, snr_out, n, J, R, 0, seed, cfg, L.p.C, L.slots,
-                 g_pdl.load() | ((g_tile_variant.load() + 1) << 1) | (g_use_tma.load() << 3) | (g_wait_test.load() << 10)};
+                 g_pdl.load() | ((g_tile_variant.load() + 1) << 1) | (g_use_tma.load() << 3) | (g_wait_test.load() << 10) | ((g_ks_real.load() + 1) << 11)};
     FM_CUDA_TRY(cudaGetDevice(&key.dev));
     NoiseGraph *hit = nullptr;
     for (auto &e : g_noise_graphs)
@@ -536,6 +536,7 @@ int fm_tune(int knob, int64_t value)
         g_use_tma.store(value < 0 ? kDefaultTma : (int)value);
         return FM_OK;
     case FM_TUNE_WAIT_TEST: g_wait_test.store(value > 0 ? 1 : 0); return FM_OK;
+    case FM_TUNE_KS_REAL: g_ks_real.store(value < 0 ? -1 : (value != 0)); return FM_OK;
     case FM_TUNE_DIRECT:
         if (value > 4) return einval("FM_TUNE_DIRECT takes 0 .. 4");
         g_direct_form.store(value < 0 ? -1 : (int)value);

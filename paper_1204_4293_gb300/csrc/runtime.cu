@@ -92,7 +92,18 @@ std::mutex g_tw_mu;
 std::unordered_map<uint64_t, void *> g_tw;  // key: device, precision, n
 }  // namespace
 
+static const void *twiddles_one(int n, int precision, cudaStream_t s, int *status);
+
+// The table of n and, for fp32 n >= 64, the one of n / 2 as well, which the
+// real-output inverse transform uses: both exist once this returns, so a call
+// before a stream capture leaves nothing to allocate inside it.
 const void *twiddles(int n, int precision, cudaStream_t s, int *status)
+{
+    if (precision == FM_F32 && n >= 64 && !twiddles_one(n / 2, precision, s, status)) return nullptr;
+    return twiddles_one(n, precision, s, status);
+}
+
+static const void *twiddles_one(int n, int precision, cudaStream_t s, int *status)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -267,6 +278,8 @@ const char *fm_status_string(int status)
 const char *fm_last_error(void) { return t_last_error.c_str(); }
 
 int64_t fm_launch_count(void) { return g_launches.load(); }
+
+int fm_ks_real_output(int n, int batched) { return ks_real_for(n, batched != 0) ? 1 : 0; }
 
 int fm_alloc_stats(int64_t *count, int64_t *max_bytes, int reset)
 {

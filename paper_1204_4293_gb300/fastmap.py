@@ -80,6 +80,7 @@ _SIGS = {
     "fm_status_string": (ctypes.c_char_p, [_I]),
     "fm_last_error": (ctypes.c_char_p, []),
     "fm_launch_count": (ctypes.c_int64, []),
+    "fm_ks_real_output": (_I, [_I, _I]),
     "fm_alloc_stats": (_I, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _I]),
     "fm_device_error": (_I, []),
     "fm_profile_select": (_I, [_I]),
@@ -332,6 +333,7 @@ def fm_noise_finalize(sums, R_total, pyramid=None, dtype=torch.float32, stream=N
 FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS, FM_TUNE_CHUNK_STREAMS, FM_TUNE_PDL, FM_TUNE_TILE, FM_TUNE_TMA = 1, 2, 3, 4, 5, 6
 FM_TUNE_WAIT_TEST = 7
 FM_TUNE_DIRECT = 8
+FM_TUNE_KS_REAL = 9
 
 
 def fm_tune(knob: int, value: int) -> None:
@@ -401,6 +403,12 @@ def fm_trim() -> None:
 
 def fm_launch_count() -> int:
     return int(_lib.fm_launch_count())
+
+
+def fm_ks_real_output(n: int, batched: bool = True) -> bool:
+    """Whether the inverse KS of n x n fp32 maps (kappa_E only) takes the
+    real-output path: in the batched pipeline's chunks, or in fm_ks_invert."""
+    return bool(_lib.fm_ks_real_output(int(n), 1 if batched else 0))
 
 
 def fm_alloc_stats(reset: bool = False):
