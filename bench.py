@@ -75,11 +75,12 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes (read + write) per map pixel of one launch of `kernel`, from
-    the committed ncu summary (a warm capture of that kernel alone on a small
-    case), valid only while the kernel source is unchanged (sha at capture);
-    None otherwise."""
+def ncu_traffic(kernel, field="dram_bytes_per_px"):
+    """Bytes per map pixel of one launch of `kernel` from the committed ncu
+    summary (a warm capture on a small case): DRAM read + write
+    (dram_bytes_per_px) or SM <-> L2 read + write (l2_bytes_per_px), valid
+    only while the kernel source is unchanged (sha at capture); None
+    otherwise."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -91,13 +92,13 @@ def ncu_traffic(kernel):
         parts = dict(kv.split("=", 1) for kv in line.split())
         if parts.get("kernel") == kernel:
             rec = parts
-    if not rec or "dram_bytes_per_px" not in rec:
+    if not rec or field not in rec:
         return None
     src = os.path.join(ROOT, "paper_1204_4293_gb300", "csrc", rec["source"])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if sha != rec.get("sha"):
         return None
-    return float(rec["dram_bytes_per_px"])
+    return float(rec[field])
 
 
 # Method bytes per map pixel of the fast path (fp32), the algorithmic traffic
@@ -116,7 +117,7 @@ def method_groups(J, fuse):
     }
 
 
-def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=False):
+def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=False, l2_peak=None):
     """The roofline of the dominant kernel group on the method bytes above,
     each group's fraction, and the whole step's.  per_kind: kind -> (device
     ms per step, launches per step), from CUDA events around each launch."""
@@ -138,14 +139,27 @@ def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=F
         # row pass 8 B/px and column pass 16 B/px through L2 or HBM)
         kern_bytes = sum(algo_bytes_per_px_launch(k, fuse, ks_real) for k in ks) * px_step / chunks
         trf = [ncu_traffic(k) for k in ks]
+        l2 = [ncu_traffic(k, "l2_bytes_per_px") for k in ks]
         groups[name] = {"kernels": ks, "method_bytes_per_px": bpp * units, "ms_per_step": ms,
                         "launches_per_step": launches, "avg_launch_ms": avg_ms,
                         "method_bytes_per_launch": bytes_launch, "achieved_gbs": achieved, "frac": achieved / peak,
                         "traffic_per_launch": (sum(trf) * px_step / chunks) if all(
                             t is not None for t in trf) else None,
+                        "l2_bytes_per_launch": (sum(l2) * px_step / chunks) if all(
+                            t is not None for t in l2) else None,
                         "kernel_bytes_per_launch": kern_bytes}
     dom = max(groups, key=lambda g: groups[g]["ms_per_step"])
     d = groups[dom]
+    # SM <-> L2 traffic of the whole step (the chunks' intermediates stay in
+    # L2): every launch of every kind at its captured bytes per pixel
+    l2_px = [ncu_traffic(k, "l2_bytes_per_px") for k in per_kind]
+    l2 = None
+    if l2_peak and all(v is not None for v in l2_px):
+        l2_bpp = sum(v * per_kind[k][1] / chunks for v, k in zip(l2_px, per_kind))
+        l2_gbs = l2_bpp * px_step / (ms_step * 1e-3) / 1e9
+        l2 = {"bytes_per_px": l2_bpp, "achieved": l2_gbs, "peak": l2_peak["copy_gbs"], "unit": "GB/s",
+              "frac": l2_gbs / l2_peak["copy_gbs"], "peak_source": l2_peak["source"],
+              "bytes_source": "profiles/ncu_traffic.txt (lts__t_sectors_srcunit_tex read + write, warm capture)"}
     bpp_step = 12.0 + 4.0 * (J + 1)
     floor_bpp = 8.0 + 4.0 * J
     step_gbs = bpp_step * px_step / (ms_step * 1e-3) / 1e9
@@ -161,7 +175,7 @@ def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=F
         "groups": groups,
         "step": {"method_bytes_per_px": bpp_step, "achieved": step_gbs, "frac": step_gbs / peak,
                  "floor_bytes_per_px": floor_bpp, "floor_frac": floor_bpp * px_step / (ms_step * 1e-3) / 1e9 / peak,
-                 "floor_ms": floor_bpp * px_step / (peak * 1e9) * 1e3},
+                 "floor_ms": floor_bpp * px_step / (peak * 1e9) * 1e3, "l2": l2},
         "timing": "CUDA events around every launch of the group's kernels on their launch stream; the same steps "
                   "launched eagerly with the chunks on one stream (graph bypassed, no kernel overlap); the step's "
                   "figures use the timed graph-replayed steps",
@@ -722,6 +736,10 @@ def main():
 
     if rank == 0:
         peak, peak_src = load_peaks()
+        # the memory-side rates on this GPU: a 64 MiB working set stays in L2
+        l2_rd, l2_cp = fm.fm_measure_bandwidth(64 << 20, 50)
+        l2_peak = {"read_gbs": l2_rd, "copy_gbs": l2_cp,
+                   "source": "measured here: fm_measure_bandwidth, 32 MiB read / copied into 32 MiB, 50 sweeps"}
         px_step = n * n * B
         fuse = fm.fm_starlet_fuse_depth(n, J)  # the plan's fused depth for this size
         line = {
@@ -734,7 +752,8 @@ def main():
                        "plan": plan if plan else "built-in rules (--no-autotune)",
                        "l2": f"inputs larger than L2: {2 * B * n * n * 4 / 2**20:.0f} MB shear in + "
                              f"{B * J * n * n * 4 / 2**20:.0f} MB pyramid out per step"},
-            "roofline": step_roofline(per_kind, px_step, J, fuse, ms_max, peak, peak_src, fm.fm_ks_real_output(n)),
+            "roofline": step_roofline(per_kind, px_step, J, fuse, ms_max, peak, peak_src, fm.fm_ks_real_output(n),
+                                      l2_peak),
             "kernel_breakdown_ms_per_step": {k: v[0] for k, v in per_kind.items()},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * B * n * n * 4,
                     "d2h_bytes_per_step": B * J * n * n * 4, "ms_per_step": float(te.item()),

@@ -286,6 +286,13 @@ int64_t fm_launch_count(void);     /* kernels launched by this library so far */
  * their number and the largest one in bytes; reset != 0 zeroes both after
  * reading.  Either pointer may be NULL. */
 int fm_alloc_stats(int64_t *count, int64_t *max_bytes, int reset);
+/* Memory-side rates on the current device for a working set of `bytes`
+ * (two buffers of bytes / 2; 32 MiB stays in L2, a few GiB streams from
+ * HBM): GB/s of a streaming float4 read of one buffer and of a copy of one
+ * into the other (read + written bytes), `reps` sweeps in one launch each.
+ * Allocates and frees the buffers; synchronises.  A measurement aid for the
+ * rooflines, not part of the method. */
+int fm_measure_bandwidth(size_t bytes, int reps, double *read_gbs, double *copy_gbs);
 /* 1 if the inverse KS of n x n fp32 maps without kappa_B takes the
  * real-output path (half spectrum) under the current FM_TUNE_KS_REAL
  * setting, 0 if the complex one; batched != 0 asks for the chunks of

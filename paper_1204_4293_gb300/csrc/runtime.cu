@@ -281,6 +281,78 @@ int64_t fm_launch_count(void) { return g_launches.load(); }
 
 int fm_ks_real_output(int n, int batched) { return ks_real_for(n, batched != 0) ? 1 : 0; }
 
+}  // extern "C"
+
+namespace fm {
+// streaming read (sum of float4 loads that bypass L1) and copy over n4 float4,
+// `reps` sweeps inside one launch: the memory-side rates a kernel of this
+// library can reach for a working set of that size (L2-resident or not)
+__global__ void k_bw_read(const float4 *__restrict__ a, long n4, int reps, float *sink)
+{
+    float acc = 0.f;
+    for (int r = 0; r < reps; ++r)
+        for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x) {
+            const float4 v = __ldcg(a + i);
+            acc += v.x + v.y + v.z + v.w;
+        }
+    if (acc == 1.5f) sink[0] = acc;  // keeps the loads; the inputs are zeros
+}
+__global__ void k_bw_copy(const float4 *__restrict__ a, float4 *__restrict__ b, long n4, int reps)
+{
+    for (int r = 0; r < reps; ++r)
+        for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x)
+            __stcg(b + i, __ldcg(a + i));
+}
+}  // namespace fm
+
+extern "C" {
+
+int fm_measure_bandwidth(size_t bytes, int reps, double *read_gbs, double *copy_gbs)
+{
+    if (bytes < (1u << 20) || bytes > (64ull << 30) || reps < 1 || reps > 1000)
+        return einval("bytes must be in [1 MiB, 64 GiB] and reps in [1, 1000]");
+    const long n4 = (long)(bytes / 32);  // two buffers of bytes / 2 each
+    void *a = nullptr, *b = nullptr, *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = FM_OK;
+    float ms = 0.f;
+    cudaError_t e = dev_malloc(&a, (size_t)n4 * 16);
+    if (e == cudaSuccess) e = dev_malloc(&b, (size_t)n4 * 16);
+    if (e == cudaSuccess) e = dev_malloc(&sink, 16);
+    if (e == cudaSuccess) e = cudaMemset(a, 0, (size_t)n4 * 16);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const unsigned grid = 152 * 16;
+    if (e == cudaSuccess) {
+        // two buffers of bytes / 2: the read sweeps the first, the copy moves it into the second
+        k_bw_read<<<grid, 256>>>((const float4 *)a, n4, 1, (float *)sink);  // warm-up
+        cudaEventRecord(e0);
+        k_bw_read<<<grid, 256>>>((const float4 *)a, n4, reps, (float *)sink);
+        cudaEventRecord(e1);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && read_gbs) *read_gbs = (double)n4 * 16 * reps / (ms * 1e-3) / 1e9;
+    }
+    if (e == cudaSuccess) {
+        k_bw_copy<<<grid, 256>>>((const float4 *)a, (float4 *)b, n4, 1);
+        cudaEventRecord(e0);
+        k_bw_copy<<<grid, 256>>>((const float4 *)a, (float4 *)b, n4, reps);
+        cudaEventRecord(e1);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && copy_gbs) *copy_gbs = (double)n4 * 32 * reps / (ms * 1e-3) / 1e9;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(e, "fm_measure_bandwidth");
+    g_launches.fetch_add(4);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (a) cudaFree(a);
+    if (b) cudaFree(b);
+    if (sink) cudaFree(sink);
+    return st;
+}
+
 int fm_alloc_stats(int64_t *count, int64_t *max_bytes, int reset)
 {
     if (count) *count = g_alloc_count.load();

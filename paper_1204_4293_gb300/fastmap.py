@@ -81,6 +81,7 @@ _SIGS = {
     "fm_last_error": (ctypes.c_char_p, []),
     "fm_launch_count": (ctypes.c_int64, []),
     "fm_ks_real_output": (_I, [_I, _I]),
+    "fm_measure_bandwidth": (_I, [_SZ, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "fm_alloc_stats": (_I, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _I]),
     "fm_device_error": (_I, []),
     "fm_profile_select": (_I, [_I]),
@@ -409,6 +410,15 @@ def fm_ks_real_output(n: int, batched: bool = True) -> bool:
     """Whether the inverse KS of n x n fp32 maps (kappa_E only) takes the
     real-output path: in the batched pipeline's chunks, or in fm_ks_invert."""
     return bool(_lib.fm_ks_real_output(int(n), 1 if batched else 0))
+
+
+def fm_measure_bandwidth(nbytes: int, reps: int = 20):
+    """(read GB/s, copy GB/s) of streaming kernels over a working set of
+    nbytes on the current device (32 MiB: L2; GiBs: HBM)."""
+    r, c = ctypes.c_double(0), ctypes.c_double(0)
+    _check(_lib.fm_measure_bandwidth(int(nbytes), int(reps), ctypes.byref(r), ctypes.byref(c)),
+           "fm_measure_bandwidth")
+    return r.value, c.value
 
 
 def fm_alloc_stats(reset: bool = False):

@@ -47,3 +47,25 @@ def test_direct_map_tap_count_and_alu_peak():
     assert abs(bench.FP32_PEAK_TFLOPS - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
     assert bench.algo_bytes_per_px_launch("starlet_tile", 2) == 16
     assert bench.algo_bytes_per_px_launch("starlet_col", 2) == 16 and bench.algo_bytes_per_px_launch("starlet_row", 3) == 8
+
+
+def test_roofline_uses_the_method_bytes():
+    """The bench's roofline credits the method's bytes: a large scale is 12
+    B/px (read c_{j-1}, write c_j and w_j) over its row and column launches
+    together, KS 12 B/px over its three passes, the step 12 + 4 (J + 1) B/px
+    over the step time, the HBM floor 8 + 4J (shear in, J arrays out)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    px = 32 * 1024 * 1024
+    per_kind = {"fft_rows_fwd": (0.22, 8), "fft_cols_ks": (0.22, 8), "fft_rows_inv": (0.12, 8),
+                "starlet_tile": (0.18, 8), "starlet_row": (0.39, 32), "starlet_col": (0.39, 32)}
+    r = bench.step_roofline(per_kind, px, 7, 2, 0.8, 6800.0, "measured")
+    assert r["kernel"].startswith("starlet_large_scale")
+    pair_ms = (0.39 + 0.39) / 32  # one scale of one 4-map chunk
+    assert abs(r["achieved"] - 12 * px / 8 / (pair_ms * 1e-3) / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 6800.0) < 1e-12
+    assert abs(r["step"]["frac"] - 44 * px / 0.8e-3 / 1e9 / 6800.0) < 1e-12
+    assert abs(r["step"]["floor_frac"] - 36 * px / 0.8e-3 / 1e9 / 6800.0) < 1e-12
+    ks = r["groups"]["ks"]
+    assert abs(ks["achieved_gbs"] - 12 * px / 8 / ((0.56 / 8) * 1e-3) / 1e9) < 1e-6
+    assert r["groups"]["starlet_tile"]["method_bytes_per_px"] == 16
