@@ -36,6 +36,7 @@ UNIT = "Mpix*scales/s"
 L2_BYTES = 129 * 2 ** 20
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # unit counts x maximum SM clock
+SERVE_REQUESTS = [200, 60]  # serving trace length and requests per swept rate (set from the command line)
 
 
 def disc_taps(R):
@@ -447,7 +448,7 @@ def side_legs(fm, torch, n, J, g1, g2, pyr):
     del pyr_b
     torch.cuda.empty_cache()
     out["large_fields"] = large_fields_leg(fm, torch)
-    out["serving"] = serving_leg(fm, torch)
+    out["serving"] = serving_leg(fm, torch, nreq=SERVE_REQUESTS[0], sweep_nreq=SERVE_REQUESTS[1])
     # batched noise maps: R realisations of KS + starlet with FP64 accumulation
     R = 1000
     t_noise = cuda_time(torch, lambda: fm.fm_map_noise(s1, s2, J, R, seed=3), 2)
@@ -528,65 +529,117 @@ def _serve_trace(fm, sv, reqs, gaps):
         while time.perf_counter() < due:
             pass
         tickets.append(sv.submit(g1, g2, J, pyr, R=R, seed=7, out_var=var))
-    res = [sv.wait(t, 600.0) for t in tickets]
+    res = [sv.wait(t, 1800.0) for t in tickets]
     ok = [r for r in res if r.status == fm.FM_OK]
     span = (max(r.t_done_ns for r in ok) - min(r.t_submit_ns for r in ok)) / 1e9
     return ok, span
 
 
-def serving_leg(fm, torch, seed=5, nreq=48, lam=200.0, budget_gb=64, slots=8, load=0.7):
-    """Poisson stream of mixed-size requests through the continuous-batching
-    server: side in {256..4096}, J = log2(side) - 2, R in {0, 100, 1000}.
-    Two traces of the same requests: at the offered 200/s (far above what one
-    GPU serves, so the queue grows and latency is mostly waiting) and then at
-    `load` times the achieved rate of the first (a sustainable rate).
-    Reports offered vs achieved rate and p50/p99 latency (submit -> done)."""
+def _trace_stats(ok, span, offered):
+    lat = np.array([(r.t_done_ns - r.t_submit_ns) / 1e6 for r in ok])
+    wait = np.array([(r.t_admit_ns - r.t_submit_ns) / 1e6 for r in ok])
+    return {"offered_req_per_s": offered, "ok": len(ok), "achieved_req_per_s": len(ok) / span,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "p50_queue_ms": float(np.percentile(wait, 50)), "span_s": span}
+
+
+def serving_leg(fm, torch, seed=5, nreq=200, sweep_nreq=60, lam=200.0, budget_gb=64, slots=8,
+                fracs=(0.3, 0.5, 0.7, 0.9)):
+    """A seeded Poisson stream of mixed requests through the continuous-
+    batching server: side in {256..4096}, J = log2(side) - 2, R in {0, 100,
+    1000}.  The trace of `nreq` requests runs at the offered 200/s (far above
+    what one GPU serves: the queue grows and latency is mostly waiting), then
+    its first `sweep_nreq` requests at fractions of the achieved rate; the
+    highest swept rate whose p99 stays within twice the longest request's
+    own service time is the sustainable one.  Requests of one (side, R) class
+    share a small pool of device buffers (inputs are only read; outputs are
+    not checked here).  Also: the same trace with merging off, and the sum of
+    each request's standalone time (the library's fp32 calls one after
+    another, each class timed once) as the back-to-back reference."""
     rng = np.random.default_rng(seed)
     sides = rng.choice([256, 512, 1024, 2048, 4096], nreq)
     Rs = rng.choice([0, 100, 1000], nreq)
     gaps = rng.exponential(1.0 / lam, nreq)
+    pools, used = {}, {}
     reqs = []
     for side, R in zip(sides, Rs):
         side, R = int(side), int(R)
+        key = (side, R)
         J = int(np.log2(side)) - 2
-        g1 = 0.1 * torch.randn(side, side, device="cuda")
-        g2 = 0.1 * torch.randn(side, side, device="cuda")
-        pyr = torch.empty(J, side, side, device="cuda")
-        var = torch.empty(J - 1, side, side, dtype=torch.float64, device="cuda") if R else None
-        reqs.append((g1, g2, J, pyr, R, var))
+        cap = 4 if side >= 4096 else (8 if side >= 2048 else 24)
+        pool = pools.setdefault(key, [])
+        k = used.get(key, 0)
+        used[key] = k + 1
+        if len(pool) < cap:
+            g1 = 0.1 * torch.randn(side, side, device="cuda")
+            g2 = 0.1 * torch.randn(side, side, device="cuda")
+            pyr = torch.empty(J, side, side, device="cuda")
+            var = torch.empty(J - 1, side, side, dtype=torch.float64, device="cuda") if R else None
+            pool.append((g1, g2, J, pyr, R, var))
+        reqs.append(pool[k % cap])
     torch.cuda.synchronize()
-    pix_scales = sum(int(side) ** 2 * (int(np.log2(side)) - 2) * (1 + int(R)) for side, R in zip(sides, Rs))
-    out = {"requests": nreq, "slots": slots, "budget_gb": budget_gb,
+    pix = [int(sd) ** 2 * (int(np.log2(sd)) - 2) * (1 + int(R)) for sd, R in zip(sides, Rs)]
+    out = {"requests": nreq, "sweep_requests": sweep_nreq, "slots": slots, "budget_gb": budget_gb,
            "trace": f"seed {seed}, Poisson, side U{{256..4096}}, J=log2(side)-2, R U{{0,100,1000}}"}
+    # each class alone, fp32, through the library's calls on one stream
+    alone = {}
+    for (side, R) in sorted(set((int(a), int(b)) for a, b in zip(sides, Rs))):
+        g1, g2, J, pyr, _, var = pools[(side, R)][0]
+        ms = cuda_time(torch, lambda: fm.fm_map_starlet(g1, g2, J, out=pyr), 2)
+        if R:
+            ms += cuda_time(torch, lambda: fm.fm_map_noise(g1, g2, J, R, seed=7, with_snr=False), 1)
+        alone[(side, R)] = ms
+    back_to_back_s = sum(alone[(int(a), int(b))] for a, b in zip(sides, Rs)) / 1e3
+    longest_ms = max(alone[(int(a), int(b))] for a, b in zip(sides, Rs))
     with fm.Server(mem_budget_bytes=budget_gb << 30, max_slots=slots) as sv:
-        # warm the kernels of every size once so the traces measure steady state
-        for side in sorted(set(int(x) for x in sides)):
-            g = 0.1 * torch.randn(side, side, device="cuda")
-            Jw = int(np.log2(side)) - 2
-            sv.wait(sv.submit(g, g, Jw, torch.empty(Jw, side, side, device="cuda")), 120.0)
-        rate = lam
-        for name in ("saturated", "sustainable"):
-            ok, span = _serve_trace(fm, sv, reqs, gaps * (lam / rate))
-            lat = np.array([(r.t_done_ns - r.t_submit_ns) / 1e6 for r in ok])
-            wait = np.array([(r.t_admit_ns - r.t_submit_ns) / 1e6 for r in ok])
-            achieved = len(ok) / span
-            out[name] = {"offered_req_per_s": rate, "ok": len(ok), "achieved_req_per_s": achieved,
-                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                         "p50_queue_ms": float(np.percentile(wait, 50)),
-                         "mpix_scales_per_s": pix_scales / span / 1e6}
-            rate = load * achieved
+        for (side, R), ms in alone.items():  # warm every size once
+            g1, g2, J, pyr, _, _ = pools[(side, R)][0]
+            sv.wait(sv.submit(g1, g2, J, pyr), 120.0)
+        ok, span = _serve_trace(fm, sv, reqs, gaps)
+        sat = _trace_stats(ok, span, lam)
+        sat["mpix_scales_per_s"] = sum(pix) / span / 1e6
+        out["saturated"] = sat
+        fm.fm_tune(fm.FM_TUNE_SERVE_MERGE, 1)
+        try:
+            ok, span = _serve_trace(fm, sv, reqs, gaps)
+        finally:
+            fm.fm_tune(fm.FM_TUNE_SERVE_MERGE, -1)
+        out["saturated_no_merging"] = _trace_stats(ok, span, lam)
+        fm.fm_tune(fm.FM_TUNE_SERVE_HEAVY, 0)
+        try:
+            ok, span = _serve_trace(fm, sv, reqs, gaps)
+        finally:
+            fm.fm_tune(fm.FM_TUNE_SERVE_HEAVY, -1)
+        out["saturated_heavy_unlimited"] = _trace_stats(ok, span, lam)
+        sweep = []
+        sub, subg = reqs[:sweep_nreq], gaps[:sweep_nreq]
+        for f in fracs:
+            rate = f * sat["achieved_req_per_s"]
+            ok, span = _serve_trace(fm, sv, sub, subg * (lam / rate))
+            st = _trace_stats(ok, span, rate)
+            st["drains"] = st["p99_ms"] <= 2 * longest_ms
+            st["p99_over_longest_alone"] = st["p99_ms"] / longest_ms
+            sweep.append(st)
+        out["sweep"] = sweep
+    drained = [st["offered_req_per_s"] for st in sweep if st["drains"]]
+    out["sustainable_req_per_s"] = max(drained) if drained else None
+    out["longest_request_alone_ms"] = longest_ms
+    out["sustainable_rule"] = (f"p99 within twice the longest request's own service time "
+                               f"({2 * longest_ms:.0f} ms) on the first {sweep_nreq} requests")
+    out["back_to_back_fp32"] = {"trace_s": back_to_back_s, "req_per_s": nreq / back_to_back_s,
+                                "mpix_scales_per_s": sum(pix) / back_to_back_s / 1e6,
+                                "server_over_back_to_back": back_to_back_s / (nreq / sat["achieved_req_per_s"]),
+                                "sample": "each (side, R) class timed once alone (fp32), summed over the trace"}
     # the contract's flat keys: the saturated trace
-    out.update({k: out["saturated"][k] for k in ("offered_req_per_s", "achieved_req_per_s", "p50_ms", "p99_ms",
-                                                  "mpix_scales_per_s")})
+    out.update({k: sat[k] for k in ("offered_req_per_s", "achieved_req_per_s", "p50_ms", "p99_ms",
+                                    "mpix_scales_per_s")})
     # plain-FP64 estimate of the same trace: each distinct (side, R) class timed
     # once in the plain form (one map, FP64, one starlet scale per pass; the
     # noise pass at R = 20, scaled to the class's R) and summed over the
     # trace as one request after another
-    classes = {}
-    for side, R in zip(sides, Rs):
-        classes[(int(side), int(R))] = classes.get((int(side), int(R)), 0) + 1
     total_s = 0.0
-    for (side, R), count in classes.items():
+    for (side, R), ms_alone in alone.items():
+        count = sum(1 for a, b in zip(sides, Rs) if (int(a), int(b)) == (side, R))
         J = int(np.log2(side)) - 2
         g = (0.1 * torch.randn(2, side, side, device="cuda", dtype=torch.float64)).contiguous()
         pyr = torch.empty(J, side, side, dtype=torch.float64, device="cuda")
@@ -597,6 +650,7 @@ def serving_leg(fm, torch, seed=5, nreq=48, lam=200.0, budget_gb=64, slots=8, lo
                                                            with_snr=False), 1) * (R / rs)
         total_s += count * ms / 1e3
         del g, pyr
+    del pools, reqs
     torch.cuda.empty_cache()
     out["plain_fp64_estimate"] = {"trace_s": total_s, "achieved_req_per_s": nreq / total_s,
                                   "sample": "each (side, R) class once; noise at R = 20 scaled to R"}
@@ -639,9 +693,19 @@ def main():
     ap.add_argument("--no-side", action="store_true", help="skip the side legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in plan (no autotuning)")
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests in the serving trace")
+    ap.add_argument("--serve-sweep-requests", type=int, default=60, help="requests per swept rate")
+    ap.add_argument("--serving-only", action="store_true", help="run only the serving leg and print it")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    SERVE_REQUESTS[:] = [args.serve_requests, args.serve_sweep_requests]
+    if args.serving_only:
+        import torch
+        from paper_1204_4293_gb300 import fastmap as fm
+        print(json.dumps({"serving": serving_leg(fm, torch, nreq=args.serve_requests,
+                                                 sweep_nreq=args.serve_sweep_requests)}), flush=True)
+        return 0
 
     import torch
     import torch.distributed as dist

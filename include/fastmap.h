@@ -268,8 +268,16 @@ typedef struct {
 /* A server owns a host thread, max_slots CUDA streams and the scratch of the
  * requests it runs.  A request is admitted when a slot is free and its
  * scratch fits in mem_budget_bytes minus the scratch of running requests;
- * requests run concurrently on their own streams.  submit copies the
- * request descriptor (device buffers are borrowed) and returns a ticket. */
+ * requests run concurrently on their own streams.  A pyramid-only request
+ * (R = 0) of a map up to 1024^2 at the head of the queue takes the queued
+ * requests of the same n, J and precision with it (at most
+ * FM_TUNE_SERVE_MERGE maps, within the budget): they run as one batched
+ * call on one slot (inputs gathered and pyramids scattered by one
+ * device-to-device copy per request), with results identical to running
+ * alone.  Heavy requests (n^2 J (1 + R) >= 2^32 pixel-scales) run at most
+ * FM_TUNE_SERVE_HEAVY at a time; light requests queued behind a waiting heavy
+ * one are admitted past it.  submit copies the request descriptor (device
+ * buffers are borrowed) and returns a ticket. */
 int fm_serve_create(size_t mem_budget_bytes, int max_slots, void **server);
 int fm_serve_submit(void *server, const fm_request *req, uint64_t *ticket);
 int fm_serve_poll(void *server, uint64_t ticket, fm_result *result);
@@ -347,6 +355,14 @@ int fm_device_error(void);
  *                        fm_ks_invert with 64 <= n <= 4096 and for the
  *                        batched pipeline's chunks of 4096^2 maps (the sizes
  *                        where it measured faster)
+ *   FM_TUNE_SERVE_MERGE  servers: most maps that one merged run of queued
+ *                        pyramid-only requests (R = 0, n <= 1024) of one
+ *                        shape may hold (default 16; 1 = every request runs
+ *                        alone)
+ *   FM_TUNE_SERVE_HEAVY  servers: heavy requests (n^2 J (1 + R) >= 2^32
+ *                        pixel-scales) running at once (default 1; 0 = no
+ *                        limit); light requests queued behind a waiting heavy
+ *                        one are admitted past it
  * FM_TUNE_CHUNK_BYTES set this way also overrides autotuned budgets. */
 #define FM_TUNE_CHUNK_BYTES 1
 #define FM_TUNE_GRAPHS 2
@@ -357,6 +373,8 @@ int fm_device_error(void);
 #define FM_TUNE_WAIT_TEST 7
 #define FM_TUNE_DIRECT 8
 #define FM_TUNE_KS_REAL 9
+#define FM_TUNE_SERVE_MERGE 10
+#define FM_TUNE_SERVE_HEAVY 11
 int fm_tune(int knob, int64_t value);
 
 /* ---- autotuner ----------------------------------------------------------------

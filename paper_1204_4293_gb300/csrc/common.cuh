@@ -218,14 +218,26 @@ int starlet_fuse_depth(int n, int J, const fm_config &cfg);  // scales of the fu
 int launch_map_direct(const void *g1, const void *g2, const void *weight, long w_bs, void *map, void *coverage, int n,
                       int batch, int filter, double theta, int ell, double cut, int precision, cudaStream_t s);
 // batched pipeline (pipeline.cu)
+// allow_graph: batches of several chunks are recorded into a CUDA graph kept
+// per (pointers, sizes, config) and replayed; false launches them eagerly
+// (callers whose buffers change from call to call)
 int map_starlet_run(const void *g1, const void *g2, void *pyramid, int n, int J, int batch, const fm_config &cfg,
-                    cudaStream_t s);
+                    cudaStream_t s, bool allow_graph = true);
+// serving (serve.cu): most maps one merged run of queued pyramid-only requests
+// of one shape holds (FM_TUNE_SERVE_MERGE; 1 = no merging)
+extern std::atomic<int> g_serve_merge;
+// serving: heavy requests running at once (FM_TUNE_SERVE_HEAVY; 0 = no limit)
+extern std::atomic<int> g_serve_heavy;
 int map_starlet_host_run(const char *g1h, const char *g2h, char *pyrh, int n, int J, int batch, const fm_config &cfg,
                          cudaStream_t origin);
-size_t noise_scratch_bytes(int n, int J, int R, const fm_config &cfg, bool with_snr);
+// multi_stream: the layout of map_noise_run's internal-stream forms
+size_t noise_scratch_bytes(int n, int J, int R, const fm_config &cfg, bool with_snr, bool multi_stream = false);
 size_t map_starlet_scratch_bytes(int n, int J, int batch, const fm_config &cfg);
+// allow_graph: record the call into a cached CUDA graph and replay it;
+// otherwise launch now, on `s` alone or, with multi_eager, with the chunks
+// over the internal streams (the serving path's heavy requests)
 int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
-                  const fm_config &cfg, cudaStream_t s, bool allow_graph);
+                  const fm_config &cfg, cudaStream_t s, bool allow_graph, bool multi_eager = false);
 int map_noise_accumulate_run(const void *g1, const void *g2, double *sums, int n, int J, int r0, int R, uint64_t seed,
                              const fm_config &cfg, cudaStream_t s);
 int launch_modulus2(const void *a, long a_bs, const void *b, long b_bs, void *out, long nn, int count, int precision,

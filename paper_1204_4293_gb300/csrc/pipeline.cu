@@ -372,10 +372,20 @@ void drop_noise_graph(NoiseGraph &e)
 // scratch, LRU of two) and replay it; otherwise launch eagerly with
 // stream-ordered scratch (the serving path, whose buffers change per call).
 int map_noise_run(const void *g1, const void *g2, double *var_out, void *snr_out, int n, int J, int R, uint64_t seed,
-                  const fm_config &cfg, cudaStream_t s, bool allow_graph)
+                  const fm_config &cfg, cudaStream_t s, bool allow_graph, bool multi_eager)
 {
     int st = FM_OK;
     if (!twiddles(n, cfg.precision, s, &st)) return st;  // tables before any capture
+    if (multi_eager && !allow_graph) {
+        // launched now, chunks over the internal streams (stream-ordered scratch on s)
+        const NoiseLayout L = noise_layout(n, J, R, cfg, true);
+        Scratch sc;
+        if ((st = scratch_alloc(sc, L.total, s))) return st;
+        std::lock_guard<std::mutex> lk(g_ds_mu);
+        DevStreams *ds = nullptr;
+        if ((st = dev_streams(&ds))) return st;
+        return noise_submit(g1, g2, var_out, snr_out, n, J, R, seed, cfg, L, (char *)sc.p, s, ds);
+    }
     if (!allow_graph || g_prof_kid.load() != 0 || !g_use_graphs.load()) {
         const NoiseLayout L = noise_layout(n, J, R, cfg, false);
         Scratch sc;
@@ -448,16 +458,16 @@ int map_noise_accumulate_run(const void *g1, const void *g2, double *sums, int n
 }
 
 // scratch of a noise call on the caller's stream (the serving path)
-size_t noise_scratch_bytes(int n, int J, int R, const fm_config &cfg, bool with_snr)
+size_t noise_scratch_bytes(int n, int J, int R, const fm_config &cfg, bool with_snr, bool multi_stream)
 {
     (void)with_snr;
-    return noise_layout(n, J, R, cfg, false).total + 256;
+    return noise_layout(n, J, R, cfg, multi_stream).total + 256;
 }
 
 int map_starlet_run(const void *g1, const void *g2, void *pyramid, int n, int J, int batch, const fm_config &cfg,
-                    cudaStream_t s)
+                    cudaStream_t s, bool allow_graph)
 {
-    return map_starlet_dev(g1, g2, pyramid, n, J, batch, cfg, s);
+    return map_starlet_dev(g1, g2, pyramid, n, J, batch, cfg, s, allow_graph);
 }
 
 // Host buffers: the chunks of the batch stream through the slots of the
@@ -536,6 +546,14 @@ int fm_tune(int knob, int64_t value)
         g_use_tma.store(value < 0 ? kDefaultTma : (int)value);
         return FM_OK;
     case FM_TUNE_WAIT_TEST: g_wait_test.store(value > 0 ? 1 : 0); return FM_OK;
+    case FM_TUNE_SERVE_MERGE:
+        if (value > 256) return einval("FM_TUNE_SERVE_MERGE takes at most 256 maps");
+        g_serve_merge.store(value < 0 ? 16 : (value < 1 ? 1 : (int)value));
+        return FM_OK;
+    case FM_TUNE_SERVE_HEAVY:
+        if (value > 64) return einval("FM_TUNE_SERVE_HEAVY takes at most 64");
+        g_serve_heavy.store(value < 0 ? 1 : (int)value);
+        return FM_OK;
     case FM_TUNE_KS_REAL: g_ks_real.store(value < 0 ? -1 : (value != 0)); return FM_OK;
     case FM_TUNE_DIRECT:
         if (value > 4) return einval("FM_TUNE_DIRECT takes 0 .. 4");

@@ -9,6 +9,22 @@
 // Completion is seen through one CUDA event per request; the thread then
 // frees the slot and the budget and stamps the finish time.  Results are
 // read (once) with fm_serve_poll / fm_serve_wait.
+//
+// Heavy requests (at least 2^32 pixel-scales of work: large noise maps) run
+// at most FM_TUNE_SERVE_HEAVY at a time (default one): several of them side
+// by side stretch one another for no gain in throughput (the serving trace's
+// heaviest request, 4096^2 with R = 1000, takes ~1 s alone and ~3 s beside
+// others), while the light requests queued behind a waiting heavy one are
+// admitted past it.
+//
+// Continuous batching: when the request at the head of the queue asks for the
+// pyramid only (R = 0) of a map of at most 1024^2, the queued requests of the
+// same (n, J, precision) join it, up to FM_TUNE_SERVE_MERGE maps and within
+// the budget, and the group runs as one batched KS + starlet call on one
+// slot: each input is copied into a gathered batch (one device-to-device
+// copy per request), the batch runs through the chunked pipeline, and each
+// pyramid is copied out.  Every map's arithmetic is the same as alone, so
+// the results are bit for bit those of single runs.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -36,7 +52,28 @@ struct Req {
     int slot = -1;
     size_t bytes = 0;
     cudaEvent_t ev = nullptr;
+    std::vector<uint64_t> members;  // a merged group's other requests (held by its first)
+    bool heavy = false;             // counted in Server::heavy_running while it runs
 };
+
+// pyramid-only requests of maps up to 1024^2 may run merged
+bool mergeable(const fm_request &r) { return r.R == 0 && r.n <= 1024; }
+// heavy: at least 2^32 pixel-scales of work (n^2 J (1 + R)), e.g. noise maps
+// of 4096^2 with R = 100 or 1024^2 with R = 1000
+bool heavy(const fm_request &r) { return (double)r.n * r.n * r.J * (1.0 + (r.R >= 2 ? r.R : 0)) >= 4294967296.0; }
+bool same_shape(const fm_request &a, const fm_request &b)
+{
+    return a.n == b.n && a.J == b.J && a.precision == b.precision;
+}
+// device bytes of a merged run of `count` maps: gathered inputs and pyramids
+// plus the batched pipeline's scratch
+size_t group_bytes(const fm_request &r, int count)
+{
+    fm_config cfg{};
+    cfg.precision = r.precision;
+    const size_t es = r.precision == FM_F64 ? 8 : 4, nn = (size_t)r.n * r.n;
+    return (size_t)count * (2 + r.J) * nn * es + map_starlet_scratch_bytes(r.n, r.J, count, cfg) + 512;
+}
 
 struct Server {
     size_t budget = 0;
@@ -50,6 +87,7 @@ struct Server {
     std::unordered_map<uint64_t, Req> reqs;
     std::vector<uint64_t> running;
     size_t in_use = 0;
+    int heavy_running = 0;
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread th;
@@ -63,6 +101,7 @@ struct Server {
             slot_busy[q.slot] = 0;
             q.slot = -1;
             in_use -= q.bytes;
+            if (q.heavy) --heavy_running;
         }
         if (q.ev) {
             cudaEventDestroy(q.ev);
@@ -76,8 +115,32 @@ struct Server {
         cfg.precision = r.precision;
         int st = map_starlet_run(r.g1, r.g2, r.out_pyramid, r.n, r.J, 1, cfg, s);
         if (st == FM_OK && r.R >= 2 && r.out_var)
-            st = map_noise_run(r.g1, r.g2, r.out_var, nullptr, r.n, r.J, r.R, r.seed, cfg, s, false);
+            // heavy requests run few at a time: their chunks take the internal streams
+            st = map_noise_run(r.g1, r.g2, r.out_var, nullptr, r.n, r.J, r.R, r.seed, cfg, s, false, heavy(r));
         return st;
+    }
+
+    // one batched call over a group of same-shape pyramid-only requests
+    static int run_group(const std::vector<fm_request> &rs, cudaStream_t s)
+    {
+        const fm_request &r0 = rs[0];
+        fm_config cfg{};
+        cfg.precision = r0.precision;
+        const size_t es = r0.precision == FM_F64 ? 8 : 4, map_b = (size_t)r0.n * r0.n * es;
+        const size_t B = rs.size();
+        Scratch sc;  // freed on s after the copies out
+        int st = scratch_alloc(sc, B * (2 + r0.J) * map_b, s);
+        if (st) return st;
+        char *g1b = static_cast<char *>(sc.p), *g2b = g1b + B * map_b, *pyb = g2b + B * map_b;
+        for (size_t i = 0; i < B; ++i) {
+            FM_CUDA_TRY(cudaMemcpyAsync(g1b + i * map_b, rs[i].g1, map_b, cudaMemcpyDeviceToDevice, s));
+            FM_CUDA_TRY(cudaMemcpyAsync(g2b + i * map_b, rs[i].g2, map_b, cudaMemcpyDeviceToDevice, s));
+        }
+        if ((st = map_starlet_run(g1b, g2b, pyb, r0.n, r0.J, (int)B, cfg, s, false))) return st;
+        for (size_t i = 0; i < B; ++i)
+            FM_CUDA_TRY(cudaMemcpyAsync(rs[i].out_pyramid, pyb + i * r0.J * map_b, r0.J * map_b,
+                                        cudaMemcpyDeviceToDevice, s));
+        return FM_OK;
     }
 
     void loop()
@@ -95,20 +158,29 @@ struct Server {
                     continue;
                 }
                 if (e != cudaSuccess) set_error(std::string("request failed: ") + cudaGetErrorString(e));
+                for (uint64_t m : q.members) finish(reqs[m], e == cudaSuccess ? FM_OK : FM_ECUDA);
+                q.members.clear();
                 finish(q, e == cudaSuccess ? FM_OK : FM_ECUDA);
                 running[i] = running.back();
                 running.pop_back();
                 progress = true;
             }
             if (stop && running.empty()) break;
-            // admissions, in arrival order
-            while (!stop && !queue.empty()) {
-                const uint64_t t = queue.front();
+            // admissions, in arrival order; a heavy request waits while
+            // FM_TUNE_SERVE_HEAVY others run, and the light ones queued
+            // behind it may go first
+            for (auto it = queue.begin(); !stop && it != queue.end();) {
+                const uint64_t t = *it;
                 Req &q = reqs[t];
                 if (q.bytes > budget) {
-                    queue.pop_front();
+                    it = queue.erase(it);
                     finish(q, FM_EBUDGET);
                     progress = true;
+                    continue;
+                }
+                const int heavy_max = g_serve_heavy.load();
+                if (heavy(q.r) && heavy_max > 0 && heavy_running >= heavy_max) {
+                    ++it;
                     continue;
                 }
                 int slot = -1;
@@ -118,15 +190,40 @@ struct Server {
                         break;
                     }
                 if (slot < 0 || in_use + q.bytes > budget) break;
-                queue.pop_front();
+                it = queue.erase(it);
+                // later queued requests of the same shape join a mergeable one
+                std::vector<uint64_t> group;
+                const int merge_max = g_serve_merge.load();
+                if (merge_max > 1 && mergeable(q.r)) {
+                    for (auto jt = it; jt != queue.end() && (int)group.size() + 1 < merge_max;) {
+                        const Req &o = reqs[*jt];
+                        if (mergeable(o.r) && same_shape(o.r, q.r) &&
+                            in_use + group_bytes(q.r, (int)group.size() + 2) <= budget) {
+                            group.push_back(*jt);
+                            jt = queue.erase(jt);
+                        } else {
+                            ++jt;
+                        }
+                    }
+                }
+                const size_t bytes = group.empty() ? q.bytes : group_bytes(q.r, (int)group.size() + 1);
                 slot_busy[slot] = 1;
                 q.slot = slot;
-                in_use += q.bytes;
+                q.bytes = bytes;
+                in_use += bytes;
+                q.heavy = heavy(q.r);
+                if (q.heavy) ++heavy_running;
                 q.t_admit = now_ns();
+                std::vector<fm_request> rs{q.r};
+                for (uint64_t m : group) {
+                    reqs[m].t_admit = q.t_admit;
+                    rs.push_back(reqs[m].r);
+                }
+                q.members = group;
                 const fm_request r = q.r;
                 cudaStream_t s = streams[slot];
                 lk.unlock();
-                int st = run(r, s);
+                int st = group.empty() ? run(r, s) : run_group(rs, s);
                 cudaEvent_t ev = nullptr;
                 if (st == FM_OK) {
                     cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -141,12 +238,15 @@ struct Server {
                     lk.unlock();
                     cudaStreamSynchronize(s);
                     lk.lock();
+                    for (uint64_t m : q2.members) finish(reqs[m], st);
+                    q2.members.clear();
                     finish(q2, st);
                 } else {
                     q2.ev = ev;
                     running.push_back(t);
                 }
                 progress = true;
+                it = queue.begin();  // submissions may have changed the queue meanwhile
             }
             if (stop && queue.empty() && running.empty()) break;
             if (!progress) cv.wait_for(lk, std::chrono::microseconds(running.empty() ? 2000 : 50));
@@ -156,6 +256,11 @@ struct Server {
 
 }  // namespace
 }  // namespace fm
+
+namespace fm {
+std::atomic<int> g_serve_merge{16};
+std::atomic<int> g_serve_heavy{1};
+}
 
 using namespace fm;
 
@@ -167,7 +272,7 @@ size_t fm_request_scratch_bytes(const fm_request *req)
     fm_config cfg{};
     cfg.precision = req->precision;
     size_t a = map_starlet_scratch_bytes(req->n, req->J, 1, cfg);
-    size_t b = (req->R >= 2 && req->out_var) ? noise_scratch_bytes(req->n, req->J, req->R, cfg, false) : 0;
+    size_t b = (req->R >= 2 && req->out_var) ? noise_scratch_bytes(req->n, req->J, req->R, cfg, false, heavy(*req)) : 0;
     return a > b ? a : b;  // stream-ordered frees let the noise pass reuse the first pass's scratch
 }
 

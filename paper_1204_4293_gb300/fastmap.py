@@ -335,6 +335,8 @@ FM_TUNE_CHUNK_BYTES, FM_TUNE_GRAPHS, FM_TUNE_CHUNK_STREAMS, FM_TUNE_PDL, FM_TUNE
 FM_TUNE_WAIT_TEST = 7
 FM_TUNE_DIRECT = 8
 FM_TUNE_KS_REAL = 9
+FM_TUNE_SERVE_MERGE = 10
+FM_TUNE_SERVE_HEAVY = 11
 
 
 def fm_tune(knob: int, value: int) -> None:

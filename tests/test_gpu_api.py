@@ -168,3 +168,38 @@ def test_bounded_wait_runs_out_and_is_reported():
     again = fm.fm_starlet_forward(kap, 5)
     torch.cuda.synchronize()
     assert torch.equal(again, ref) and fm.fm_device_error() == 0
+
+
+@pytest.mark.parametrize("merge", [16, 1])
+def test_serving_merged_runs_equal_alone(merge):
+    # 24 pyramid-only requests of three shapes submitted at once (plus two
+    # noise requests between them): the server merges queued requests of one
+    # shape into batched runs (or, with merging off, runs each alone); every
+    # pyramid equals its single fm_map_starlet call bit for bit
+    fm = _fm()
+    rng = np.random.default_rng(9)
+    reqs = []
+    for i in range(26):
+        n = int(rng.choice([128, 256, 512]))
+        J = int(np.log2(n)) - 2
+        R = 3 if i in (5, 17) else 0
+        g1 = torch.empty(n, n, device="cuda").normal_(0, 0.1)
+        g2 = torch.empty_like(g1).normal_(0, 0.1)
+        reqs.append((g1, g2, J, R))
+    alone = [fm.fm_map_starlet(g1, g2, J) for g1, g2, J, _ in reqs]
+    fm.fm_tune(fm.FM_TUNE_SERVE_MERGE, merge)
+    try:
+        with fm.Server(mem_budget_bytes=2 << 30, max_slots=2) as sv:
+            outs, tickets = [], []
+            for g1, g2, J, R in reqs:
+                n = g1.shape[-1]
+                pyr = torch.full((J, n, n), float("nan"), device="cuda")
+                var = torch.empty(J - 1, n, n, dtype=torch.float64, device="cuda") if R else None
+                tickets.append(sv.submit(g1, g2, J, pyr, R=R, seed=3, out_var=var))
+                outs.append(pyr)
+            res = [sv.wait(t, 60.0) for t in tickets]
+    finally:
+        fm.fm_tune(fm.FM_TUNE_SERVE_MERGE, -1)
+    assert all(r.status == fm.FM_OK for r in res)
+    for a, b in zip(alone, outs):
+        assert torch.equal(a, b)
