@@ -352,7 +352,9 @@ __global__ void k_sum_parts(const float *__restrict__ part, float *__restrict__ 
 {
     pdl_entry();
     const long i4 = ((long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    const bool vec = (reinterpret_cast<uintptr_t>(out) & 15) == 0;  // `part` is 256-byte aligned scratch
+    // float4 access needs `out` 16-byte aligned and every part's start too
+    // (`part` is 256-byte aligned scratch, part p starts p * total floats on)
+    const bool vec = (reinterpret_cast<uintptr_t>(out) & 15) == 0 && (total & 3) == 0;
     if (vec && i4 + 3 < total) {
         float4 a = *reinterpret_cast<const float4 *>(part + i4);
         for (int p = 1; p < P; ++p) {
@@ -385,12 +387,26 @@ static int direct_form(int Ri)
     return f >= 0 ? f : (Ri < 48 ? 2 : 3);
 }
 
-// parts of the input-row walk: about 32 rows each, at most 8 (a function of
-// the tile height and radius only, so results never depend on the batch)
+// parts of the input-row walk: about 16 rows each, at most 16 (a function of
+// the tile height and radius only, so results never depend on the batch).
+// Measured on one 1024^2 map (ms), parts of ~32 rows (at most 8) / ~16 (16) /
+// ~64 (4): S98 theta = 64 1.41 / 1.33 / 1.65, starlet Q theta = 64 4.83 /
+// 4.71 / 5.19, JBJ04 theta = 16 (cut 5 theta) 2.01 / 1.92 / 2.46.
 static int direct_parts(int TY, int Ri)
 {
-    const int P = (TY + 2 * Ri) / 32;
-    return P < 1 ? 1 : (P > 8 ? 8 : P);
+    const int P = (TY + 2 * Ri) / 16;
+    return P < 1 ? 1 : (P > 16 ? 16 : P);
+}
+// maps per launch pair when the parts go through scratch: at most 256 MiB of
+// partial sums (the order of the sums is per map, so the slicing of a batch
+// does not change any result)
+static int direct_slice(int P, int n, int batch)
+{
+    if (P <= 1) return batch;
+    const long per_map = (long)P * n * n * (long)sizeof(float);
+    long m = (256L << 20) / per_map;
+    m = m < 1 ? 1 : m;
+    return m < batch ? (int)m : batch;
 }
 
 template <int RY, int NW>
@@ -402,15 +418,20 @@ static int launch_direct_f2(const float *g1, const float *g2, const float2 *dtap
     const int pw = width + (width >> 3) + 1;
     const size_t smem = 2ull * pw * sizeof(float2);
     const int P = direct_parts(TY, Ri);
+    const int slice = direct_slice(P, n, batch);
     auto k = k_map_direct_f2<CX, RY, NW>;
     FM_CUDA_TRY(fm::smem_attr((const void *)k, smem));
-    dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, batch * P);
-    FM_LAUNCH(FM_K_MAP_DIRECT, k, grid, NW * 32, smem, s, g1, g2, dtaps, tw, ddx, P > 1 ? parts : map, n, Ri, P,
-              batch);
-    if (P > 1) {
-        const long total = (long)batch * n * n;
-        const unsigned g = (unsigned)((total / 4 + 255) / 256 + 1);
-        FM_LAUNCH(FM_K_MAP_DIRECT, k_sum_parts, g, 256, 0, s, (const float *)parts, map, total, P);
+    const long nn = (long)n * n;
+    for (int b0 = 0; b0 < batch; b0 += slice) {
+        const int bs = batch - b0 < slice ? batch - b0 : slice;
+        dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, bs * P);
+        FM_LAUNCH(FM_K_MAP_DIRECT, k, grid, NW * 32, smem, s, g1 + b0 * nn, g2 + b0 * nn, dtaps, tw, ddx,
+                  P > 1 ? parts : map + b0 * nn, n, Ri, P, bs);
+        if (P > 1) {
+            const long total = (long)bs * nn;
+            const unsigned g = (unsigned)((total / 4 + 255) / 256 + 1);
+            FM_LAUNCH(FM_K_MAP_DIRECT, k_sum_parts, g, 256, 0, s, (const float *)parts, map + b0 * nn, total, P);
+        }
     }
     return FM_OK;
 }
@@ -419,7 +440,7 @@ static size_t direct_parts_bytes(int form, int n, int batch, int Ri)
 {
     const int TY = form == 2 ? 8 : form == 3 ? 8 : 16;
     const int P = direct_parts(TY, Ri);
-    return P > 1 ? (size_t)P * batch * n * n * sizeof(float) : 0;
+    return P > 1 ? (size_t)P * direct_slice(P, n, batch) * n * n * sizeof(float) : 0;
 }
 
 template <typename T>
