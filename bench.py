@@ -76,7 +76,7 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel, field="dram_bytes_per_px"):
+def ncu_traffic(kernel, field="dram_bytes_per_px", shape=None):
     """Bytes per map pixel of one launch of `kernel` from the committed ncu
     summary (a warm capture on a small case): DRAM read + write
     (dram_bytes_per_px) or SM <-> L2 read + write (l2_bytes_per_px), valid
@@ -95,6 +95,8 @@ def ncu_traffic(kernel, field="dram_bytes_per_px"):
             rec = parts
     if not rec or field not in rec:
         return None
+    if shape is not None and (rec.get("n"), rec.get("J"), rec.get("fuse")) != tuple(str(v) for v in shape):
+        return None  # captured on another workload
     src = os.path.join(ROOT, "paper_1204_4293_gb300", "csrc", rec["source"])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if sha != rec.get("sha"):
@@ -118,11 +120,12 @@ def method_groups(J, fuse):
     }
 
 
-def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=False, l2_peak=None):
+def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=False, l2_peak=None, n=1024):
     """The roofline of the dominant kernel group on the method bytes above,
     each group's fraction, and the whole step's.  per_kind: kind -> (device
     ms per step, launches per step), from CUDA events around each launch."""
     chunks = per_kind["fft_rows_fwd"][1]  # one row-FFT launch per chunk of maps
+    shape = (n, J, fuse)  # the workload a committed ncu capture must match
     groups = {}
     for name, (kinds, bpp, units) in method_groups(J, fuse).items():
         ks = [k for k in kinds if k in per_kind]
@@ -139,8 +142,8 @@ def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=F
         # the kernels' own reads and writes per unit launch (a large scale's
         # row pass 8 B/px and column pass 16 B/px through L2 or HBM)
         kern_bytes = sum(algo_bytes_per_px_launch(k, fuse, ks_real) for k in ks) * px_step / chunks
-        trf = [ncu_traffic(k) for k in ks]
-        l2 = [ncu_traffic(k, "l2_bytes_per_px") for k in ks]
+        trf = [ncu_traffic(k, shape=shape) for k in ks]
+        l2 = [ncu_traffic(k, "l2_bytes_per_px", shape) for k in ks]
         groups[name] = {"kernels": ks, "method_bytes_per_px": bpp * units, "ms_per_step": ms,
                         "launches_per_step": launches, "avg_launch_ms": avg_ms,
                         "method_bytes_per_launch": bytes_launch, "achieved_gbs": achieved, "frac": achieved / peak,
@@ -153,7 +156,7 @@ def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=F
     d = groups[dom]
     # SM <-> L2 traffic of the whole step (the chunks' intermediates stay in
     # L2): every launch of every kind at its captured bytes per pixel
-    l2_px = [ncu_traffic(k, "l2_bytes_per_px") for k in per_kind]
+    l2_px = [ncu_traffic(k, "l2_bytes_per_px", shape) for k in per_kind]
     l2 = None
     if l2_peak and all(v is not None for v in l2_px):
         l2_bpp = sum(v * per_kind[k][1] / chunks for v, k in zip(l2_px, per_kind))
@@ -817,7 +820,7 @@ def main():
                        "l2": f"inputs larger than L2: {2 * B * n * n * 4 / 2**20:.0f} MB shear in + "
                              f"{B * J * n * n * 4 / 2**20:.0f} MB pyramid out per step"},
             "roofline": step_roofline(per_kind, px_step, J, fuse, ms_max, peak, peak_src, fm.fm_ks_real_output(n),
-                                      l2_peak),
+                                      l2_peak, n),
             "kernel_breakdown_ms_per_step": {k: v[0] for k, v in per_kind.items()},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * B * n * n * 4,
                     "d2h_bytes_per_step": B * J * n * n * 4, "ms_per_step": float(te.item()),
