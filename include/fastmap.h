@@ -81,14 +81,18 @@ typedef struct {
                        1..k (at most 4 in fp32, 3 in fp64, J - 1), -1 = none
                        (the plain one-scale-per-pass form) */
     int large_path; /* scales after the fused ones: 0 = automatic (the
-                       autotuned plan, else 3 after fused small scales on
-                       maps up to 256^2 and 1 otherwise),
+                       autotuned plan, else 4 where it applies after at
+                       least two fused scales, 3 after fused small scales
+                       on maps up to 256^2, 1 otherwise),
                        1 = one row pass + one column pass per scale, 2 = all
                        large scales in one row kernel + one column-strip
                        kernel, 3 = the column pass of each scale fused with
                        the row pass of the next (one row pass, then one
                        kernel per scale; the pyramid's smooth-array slot
-                       serves as scratch until its final write) */
+                       serves as scratch until its final write), 4 = one
+                       pass per scale that row-filters c_{j-1} from shared
+                       memory (fp32, n a multiple of 512, scales with
+                       spacing 4..128 px; otherwise the form 1) */
 } fm_config;
 
 /* ---- Kaiser-Squires (Sec. 4.5) ---------------------------------------------
@@ -400,7 +404,7 @@ int fm_tune(int knob, int64_t value);
  * fm_autotune. */
 typedef struct {
     int fuse_depth; /* scales of the fused tile kernel */
-    int large_path; /* 1 or 3 (see fm_config) */
+    int large_path; /* 1, 3 or 4 (see fm_config) */
     int tile;       /* fp32 tile kernel: 1 = register window, 0 = shared buffer */
     int chunk_mb;   /* chunk budget of batched calls, MiB (0 = the default) */
     double ms;         /* fm_map_starlet with this plan, per call (tuning batch) */

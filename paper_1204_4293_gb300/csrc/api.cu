@@ -25,7 +25,7 @@ int check_config(const fm_config &c)
     if (c.accum != 0 && c.accum != 1) return einval("accum must be 0 (FP64 sums) or 1 (Kahan fp32 sums)");
     if (c.accum == 1 && c.precision != FM_F32) return einval("accum = 1 (Kahan fp32 sums) needs FM_F32 maps");
     if (c.fuse_depth < -1 || c.fuse_depth > 8) return einval("fuse_depth out of range [-1, 8]");
-    if (c.large_path < 0 || c.large_path > 3) return einval("large_path must be 0, 1, 2 or 3");
+    if (c.large_path < 0 || c.large_path > 4) return einval("large_path must be 0, 1, 2, 3 or 4");
     return FM_OK;
 }
 

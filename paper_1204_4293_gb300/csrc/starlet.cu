@@ -691,6 +691,91 @@ __global__ void __launch_bounds__(128) k_st_col(const T *__restrict__ r, long r_
 }
 
 // ---------------------------------------------------------------------------
+// One large scale in one pass (fp32, large_path 4: maps whose arrays stream
+// through HBM).  A CTA owns 512 columns (128 threads x float4) and KR output
+// rows y_k = r0 + s (mb + k) of one map, like k_st_col.  Its KR + 4 window
+// rows of c_{j-1} (rows r0 + s (mb + t - 2), folded at the map's top and
+// bottom) arrive by one bulk tensor copy each, 512 + 4s columns wide
+// (x0 - 2s .. x0 + 512 + 2s; mc views c_{j-1} as {2s, n / 2s, rows}), into
+// shared memory; halo columns outside the map are then loaded folded.  Each
+// thread row-filters its window rows there (taps +-s, +-2s) into a five-row
+// register window and filters that down the column: c_j, and w_j = c_{j-1} -
+// c_j with c_{j-1} the centre of the window row.  The row-filtered map never
+// goes through memory (the pair k_st_row + k_st_col moves 24 bytes per pixel,
+// this pass 8 + 4 (KR + 4) / KR (512 + 4s) / 512).  c_next must not alias
+// c_prev: other CTAs read its rows and halo columns.  4 <= s <= 128.
+template <int KR>
+__global__ void __launch_bounds__(128) k_st_scale(const float *c_prev, float *c_next, long next_bs,
+                                                  float *__restrict__ w_out, long w_bs, int n, int s, int boundary,
+                                                  const __grid_constant__ CUtensorMap mc)
+{
+    pdl_entry();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint64_t bar;
+    const int RW = (512 + 4 * s + 31) & ~31;  // floats per staged row: 512 + 4s, padded so that every row (a
+                                              // bulk tensor copy destination) starts 128-byte aligned
+    float *sw = align128<float>(smem_raw);    // [KR + 4][RW]
+    const int x0 = blockIdx.x * 512;
+    const int r0 = blockIdx.y % s, mb = (blockIdx.y / s) * KR;
+    const long b = blockIdx.z;
+    const float *cb = c_prev + b * (long)n * n;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bar, (uint32_t)((KR + 4) * (512 + 4 * s) * sizeof(float)));
+        for (int t = 0; t < KR + 4; ++t) {
+            const int y = fold_index(r0 + s * (mb + t - 2), n, boundary);
+            tma_load_3d(sw + t * RW, &mc, 0, x0 / (2 * s) - 1, (int)(b * n + y), &bar);
+        }
+    }
+    if (!tma_wait_all(&bar, 0)) return;  // the copies never completed (flagged)
+    if (x0 - 2 * s < 0 || x0 + 512 + 2 * s > n) {
+        // halo columns outside the map (the copies filled them with zeros)
+        for (int e = threadIdx.x; e < (KR + 4) * 4 * s; e += blockDim.x) {
+            const int t = e / (4 * s), h = e % (4 * s);
+            const int xl = h < 2 * s ? h : 512 + h;  // left halo, then right halo
+            const int x = x0 - 2 * s + xl;
+            if (x < 0 || x >= n) {
+                const int y = fold_index(r0 + s * (mb + t - 2), n, boundary);
+                sw[t * RW + xl] = cb[(long)y * n + fold_index(x, n, boundary)];
+            }
+        }
+        __syncthreads();
+    }
+    const int xl = 2 * s + 4 * threadIdx.x, x = x0 + 4 * threadIdx.x;
+    float4 win[5], ctr[3];
+#pragma unroll
+    for (int t = 0; t < KR + 4; ++t) {
+        const float *row = sw + t * RW + xl;
+        const float4 m2 = f4(row - 2 * s), m1 = f4(row - s), c0 = f4(row), p1 = f4(row + s), p2 = f4(row + 2 * s);
+        // the same arithmetic as k_st_row
+        win[t % 5] = make_float4(B3<float>::apply(m2.x, m1.x, c0.x, p1.x, p2.x),
+                                 B3<float>::apply(m2.y, m1.y, c0.y, p1.y, p2.y),
+                                 B3<float>::apply(m2.z, m1.z, c0.z, p1.z, p2.z),
+                                 B3<float>::apply(m2.w, m1.w, c0.w, p1.w, p2.w));
+        ctr[t % 3] = c0;
+        if (t >= 4) {
+            const int k = t - 4;
+            const int y = r0 + s * (mb + k);
+            if (y < n) {
+                // the same arithmetic as k_st_col
+                const float4 &a = win[k % 5], &bq = win[(k + 1) % 5], &c = win[(k + 2) % 5], &d = win[(k + 3) % 5],
+                             &e = win[(k + 4) % 5];
+                alignas(16) float cj[4] = {B3<float>::apply(a.x, bq.x, c.x, d.x, e.x),
+                                           B3<float>::apply(a.y, bq.y, c.y, d.y, e.y),
+                                           B3<float>::apply(a.z, bq.z, c.z, d.z, e.z),
+                                           B3<float>::apply(a.w, bq.w, c.w, d.w, e.w)};
+                const float4 p = ctr[(k + 2) % 3];
+                alignas(16) float w[4] = {p.x - cj[0], p.y - cj[1], p.z - cj[2], p.w - cj[3]};
+                const long px = (long)y * n + x;
+                emit_band<float>(w, w_out + b * w_bs, px, y, x, n, true);
+                if (c_next) emit_band<float>(cj, c_next + b * next_bs, px, y, x, n, true, true);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Column pass of large scale j fused with the row pass of scale j + 1.  A CTA
 // owns KR whole rows y_k = r0 + s (m KR + k) of one map (rows at the stride s
 // of scale j, like k_st_col): each thread runs the column filter down CPT
@@ -952,12 +1037,17 @@ static int auto_fuse(int n, int J, const fm_config &cfg)
     return starlet_builtin_fuse(n, J, cfg);
 }
 
-// Large-scale path when cfg.large_path = 0: the autotuned plan's, else the
+// Large-scale path when cfg.large_path = 0: the autotuned plan's, else one
+// pass per scale (k_st_scale) where it applies (n a multiple of 512, large
+// scales of spacing 4..128 px; fp32 only, fp64 takes the form 1), else the
 // column pass fused with the next row pass on maps up to 256^2 after fused
-// small scales (measured below), else one row and one column pass per scale.
+// small scales, else one row and one column pass per scale.  One pass per
+// scale against the row + column pair (KS + starlet per batch, ms): 32 x
+// 1024^2 J = 7 0.818 -> 0.715, 16 x 2048^2 J = 8 1.99 -> 1.78, 16 x 4096^2
+// J = 9 10.52 -> 8.25, 1 x 8192^2 J = 9 3.16 -> 2.56.
 int starlet_builtin_large_path(int n, int J, int fuse)
 {
-    (void)J;
+    if (fuse >= 2 && n % 512 == 0 && (1 << (J - 2)) <= 128) return 4;
     return fuse >= 1 && n <= 256 ? 3 : 1;
 }
 
@@ -1129,6 +1219,45 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
         }
 #undef FM_COLS_MULTI
         return FM_OK;
+    }
+    if constexpr (sizeof(T) == 4) {
+        // large_path 4: one pass per large scale, row filter from shared memory
+        const int s_lo = 1 << f, s_hi = 1 << (J - 2);  // spacing of the first and last large scale
+        if (K >= 1 && lpath == 4 && vec_ok && n % 512 == 0 && s_lo >= 4 && s_hi <= 128 && Bb) {
+            constexpr int KRS = 8;
+            // c_j alternates between A and Bb (never in place); the last goes to
+            // the smooth-array slot.  Tensor maps first: if the driver refuses
+            // one, the two-pass path below runs instead.
+            const T *srcs[20];
+            T *dsts[20];
+            CUtensorMap maps[20];
+            bool ok = true;
+            const T *src = f >= 1 ? A : kappa;
+            for (int j = f + 1; j <= J - 1 && ok; ++j) {
+                const int sp = 1 << (j - 1);
+                T *dst = j == J - 1 ? (bands_only ? nullptr : last) : (src == Bb ? A : Bb);
+                const uint64_t dims[3] = {(uint64_t)(2 * sp), (uint64_t)(n / (2 * sp)), (uint64_t)batch * n};
+                const uint64_t str[2] = {(uint64_t)(2 * sp) * 4, (uint64_t)n * 4};
+                const uint32_t box[3] = {(uint32_t)(2 * sp), (uint32_t)(256 / sp + 2), 1};
+                ok = encode_map3d_f32(&maps[j], src, dims, str, box);
+                srcs[j] = src;
+                dsts[j] = dst;
+                src = dst;
+            }
+            if (ok) {
+                for (int j = f + 1; j <= J - 1; ++j) {
+                    const int sp = 1 << (j - 1);
+                    const long dst_bs = j == J - 1 ? pyr_bs : nn;
+                    const size_t ssm = 128 + (size_t)(KRS + 4) * ((512 + 4 * sp + 31) & ~31) * sizeof(float);
+                    FM_CUDA_TRY(fm::smem_attr((const void *)k_st_scale<KRS>, ssm));
+                    const unsigned gys = (unsigned)(sp * ((((n + sp - 1) / sp) + KRS - 1) / KRS));
+                    FM_LAUNCH(FM_K_STARLET_COL, k_st_scale<KRS>, dim3(n / 512, gys, batch), 128, ssm, s,
+                              (const float *)srcs[j], (float *)dsts[j], dst_bs, (float *)(pyr + (long)(j - 1) * nn),
+                              pyr_bs, n, sp, bnd, maps[j]);
+                }
+                return FM_OK;
+            }
+        }
     }
     const unsigned gx = (unsigned)((n + 128 * VW - 1) / (128 * VW));
     // row pass: up to 256 threads (1024 fp32 pixels) of one row per CTA, so

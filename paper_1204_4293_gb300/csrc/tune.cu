@@ -1,6 +1,6 @@
 // tune.cu -- the autotuner of the batched KS + starlet path: it times
 // fm_map_starlet on synthetic maps for candidate plans (fused depth,
-// large-scale path, fp32 tile kernel form, chunk budget) and keeps the
+// large-scale path 1 / 3 / 4, fp32 tile kernel form, chunk budget) and keeps the
 // fastest per (n, J, precision) in a process-wide table that the automatic
 // fields of fm_config follow; the table saves to and loads from JSON.
 #include <math.h>
@@ -25,7 +25,8 @@ std::map<std::tuple<int, int, int>, TunedPlan> g_table;  // (n, J, precision) ->
 bool valid_plan(const TunedPlan &p, int precision)
 {
     const int fmax = precision == FM_F64 ? 3 : 4;
-    return p.fuse >= 1 && p.fuse <= fmax && (p.large_path == 1 || p.large_path == 3) && (p.tile == 0 || p.tile == 1) &&
+    return p.fuse >= 1 && p.fuse <= fmax && (p.large_path == 1 || p.large_path == 3 || p.large_path == 4) &&
+           (p.tile == 0 || p.tile == 1) &&
            p.chunk_mb >= 0 && p.chunk_mb <= 65536;
 }
 
@@ -209,7 +210,7 @@ int fm_autotune(int n, int J, int batch, const fm_config *cfgp, fm_plan *best)
                     cand.push_back(p);
                 }
             if (dim == 1 && cur.fuse < J - 1)
-                for (int lp : {1, 3}) {
+                for (int lp : {1, 3, 4}) {
                     TunedPlan p = cur;
                     p.large_path = lp;
                     cand.push_back(p);
@@ -282,7 +283,7 @@ int fm_autotune_set(int n, int J, int precision, const fm_plan *plan)
     p.ms = plan->ms;
     p.default_ms = plan->default_ms;
     if (!valid_plan(p, precision))
-        return einval("plan: fuse_depth 1..4 (fp64 1..3), large_path 1 or 3, tile 0 or 1, chunk_mb 0..65536");
+        return einval("plan: fuse_depth 1..4 (fp64 1..3), large_path 1, 3 or 4, tile 0 or 1, chunk_mb 0..65536");
     table_put(n, J, precision, p);
     return fm_trim();
 }

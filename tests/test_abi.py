@@ -84,11 +84,11 @@ def test_validation_before_any_device_work(fm):
     assert lib.fm_map_noise_accumulate(1, 1, 1, 64, 4, 0, 3, 0, ctypes.byref(kahan), None) == fm.FM_EINVAL
     # the allocation-free KS takes the configs fm_ks_invert takes, and n up to
     # 2048 (a batch of one fills its static buffer)
-    for bad in (fm._cfg(0, large_path=4), fm._cfg(0, boundary=5), fm._cfg(1)):
+    for bad in (fm._cfg(0, large_path=5), fm._cfg(0, boundary=5), fm._cfg(1)):
         assert lib.fm_ks_invert_noalloc(1, 1, 1, None, 256, 1, ctypes.byref(bad), None) == fm.FM_EINVAL
     assert lib.fm_ks_invert_noalloc(1, 1, 1, None, 4096, 1, cfg, None) == fm.FM_EINVAL
     assert b"[32, 2048]" in lib.fm_last_error()
-    bad = fm._cfg(0, large_path=4)
+    bad = fm._cfg(0, large_path=5)
     assert lib.fm_starlet_forward(1, 1, 64, 3, 1, ctypes.byref(bad), None) == fm.FM_EINVAL
     h = ctypes.c_void_p()
     assert lib.fm_serve_create(0, 2, ctypes.byref(h)) == fm.FM_EINVAL

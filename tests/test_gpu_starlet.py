@@ -166,3 +166,25 @@ def test_fused_column_row_pass_is_bit_exact(n, J, batch, boundary, dtype):
     r = oracle.starlet(kappa[-1].double().cpu().numpy(), J, boundary) if n <= 1024 else None
     if r is not None:
         assert max(band_errs(ref[-1].cpu().numpy(), r)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("n,J,batch,boundary", [(4096, 9, 1, 0), (2048, 8, 2, 1), (512, 7, 3, 0), (1024, 7, 2, 1),
+                                                (8192, 9, 1, 0)])
+def test_one_pass_large_scales_match_two_pass(n, J, batch, boundary):
+    # large_path 4 (each large scale in one pass, the row filter from shared
+    # memory, bulk tensor copies of the window rows, mirrored or wrapped halo
+    # columns at the strip edges) against the row + column passes, and the
+    # oracle on the first map where it finishes quickly
+    from paper_1204_4293_gb300 import fastmap as fm
+    g = torch.Generator(device="cuda").manual_seed(n + J)
+    kap = torch.empty((batch, n, n), device="cuda").normal_(0, 0.02, generator=g)
+    a = fm.fm_starlet_forward(kap, J, boundary=boundary, large_path=4)
+    b = fm.fm_starlet_forward(kap, J, boundary=boundary, large_path=1)
+    torch.cuda.synchronize()
+    assert fm.fm_device_error() == 0
+    for m in range(batch):
+        errs = band_errs(a[m].double().cpu().numpy(), b[m].double().cpu().numpy())
+        assert max(errs) <= 1e-6, errs
+    if n <= 1024:
+        ref = oracle.starlet(kap[0].double().cpu().numpy(), J, boundary)
+        assert max(band_errs(a[0].cpu().numpy(), ref)) <= 1e-5
