@@ -76,7 +76,7 @@ typedef struct {
                        compensation (FM_F32 maps only); same scratch size */
     int fuse_depth; /* starlet scales done by the fused 2-D tile kernel:
                        0 = automatic (the autotuned plan, else 2 for fp32
-                       maps of 1024^2 to 2048^2 and 3 otherwise; see
+                       maps of 512^2 to 2048^2 and 3 otherwise; see
                        fm_starlet_fuse_depth, fm_autotune), k > 0 = scales
                        1..k (at most 4 in fp32, 3 in fp64, J - 1), -1 = none
                        (the plain one-scale-per-pass form) */

@@ -1007,14 +1007,11 @@ __global__ void __launch_bounds__(512) k_st_cols_multi(const T *__restrict__ c_a
 
 // ---------------------------------------------------------------------------
 // Scales handled by the fused tile kernel; never more than fit a tile with
-// its halo (two buffers) in shared memory.  Automatic choice, measured on
-// GB300 (fp32 KS + starlet, ms per batch, fusing 1 / 2 / 3 scales):
-// 128 x 256^2 J = 6 0.281 / 0.253 / 0.228, 64 x 512^2 J = 7 0.489 / 0.451
-// / 0.446, 32 x 1024^2 J = 7 0.898 / 0.812 / 0.837, 16 x 2048^2 J = 8
-// 2.216 / 2.051 / 2.151:
-// two scales for 1024^2 and 2048^2 maps, whose chunked large-scale passes
-// run from L2, else three.
-// An autotuned plan for (n, J, precision) overrides this rule.
+// its halo (two buffers) in shared memory.  Automatic choice: see
+// starlet_builtin_fuse (measured with the large scales in one pass each; with
+// a row and a column pass per large scale it was 0.898 / 0.812 / 0.837 ms for
+// 32 x 1024^2 fusing 1 / 2 / 3 scales and 0.489 / 0.451 / 0.446 for 64 x
+// 512^2).  An autotuned plan for (n, J, precision) overrides the rule.
 static int clamp_fuse(int f, int J, const fm_config &cfg)
 {
     const int fmax = cfg.precision == FM_F64 ? 3 : 4;  // tile + halo must fit shared memory
@@ -1023,10 +1020,15 @@ static int clamp_fuse(int f, int J, const fm_config &cfg)
     return f;
 }
 
+// Built-in fused depth: two scales for fp32 maps of 512^2 to 2048^2, three
+// otherwise.  With one pass per large scale (KS + starlet per batch, ms,
+// fusing 1 / 2 / 3 scales): 64 x 512^2 (J = 7) 0.490 / 0.366 / 0.376, 32 x
+// 1024^2 (J = 7) 0.878 / 0.709 / 0.726, 16 x 2048^2 (J = 8) 2.14 / 1.77 /
+// 1.80, 16 x 4096^2 (J = 9) 11.9 / 8.28 / 8.24.
 int starlet_builtin_fuse(int n, int J, const fm_config &cfg)
 {
     if (cfg.fuse_depth < 0) return 0;
-    const int f = cfg.fuse_depth != 0 ? cfg.fuse_depth : (cfg.precision == FM_F32 && n >= 1024 && n <= 2048 ? 2 : 3);
+    const int f = cfg.fuse_depth != 0 ? cfg.fuse_depth : (cfg.precision == FM_F32 && n >= 512 && n <= 2048 ? 2 : 3);
     return clamp_fuse(f, J, cfg);
 }
 

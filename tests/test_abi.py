@@ -110,15 +110,15 @@ def test_request_scratch_bytes_is_monotone(fm):
 
 def test_fuse_depth_rule(fm):
     """The automatic fused depth (host only): two scales for fp32 maps of
-    1024^2 and 2048^2, three otherwise; bounded by J - 1 and the tile's
+    512^2 to 2048^2, three otherwise; bounded by J - 1 and the tile's
     shared-memory limit (4 in fp32, 3 in fp64); -1 turns fusion off."""
     d = fm.fm_starlet_fuse_depth
-    assert [d(n, 7) for n in (256, 512, 1024, 2048, 4096, 8192)] == [3, 3, 2, 2, 3, 3]
+    assert [d(n, 7) for n in (256, 512, 1024, 2048, 4096, 8192)] == [3, 2, 2, 2, 3, 3]
     assert d(1024, 7, precision=fm.FM_F64) == 3
     assert d(1024, 3) == 2 and d(256, 3) == 2 and d(256, 2) == 1
     assert d(1024, 7, fuse_depth=4) == 4 and d(1024, 7, fuse_depth=8) == 4
     assert d(1024, 7, precision=fm.FM_F64, fuse_depth=4) == 3
-    assert d(1000, 7) == 3  # non-power-of-two starlet sizes follow the same rule
+    assert d(1000, 7) == 2 and d(400, 7) == 3  # non-power-of-two starlet sizes follow the same rule
     assert d(1024, 7, fuse_depth=-1) == 0
     with pytest.raises(fm.FastmapError):
         d(16, 5)  # n < 2^J
