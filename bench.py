@@ -45,22 +45,22 @@ def disc_taps(R):
     return sum(2 * int(np.floor(np.sqrt(R * R - dy * dy))) + 1 for dy in range(-Ri, Ri + 1)) - 1
 
 
-def algo_bytes_per_px_launch(kernel, fuse, ks_real=False):
+def algo_bytes_per_px_launch(kernel, fuse, ks_real=False, one_pass=False):
     """Algorithmic bytes per map pixel that one launch of `kernel` moves
     (fp32): what the kernel must read and write once.  FFT passes move
     complex maps (the real-output inverse: the column pass writes, and the
     row inverse reads, the half spectrum, 4 B/px); the KS row passes the real
     shear / convergence; the tile kernel reads kappa and writes `fuse` bands
     + c_fuse; a large scale's row pass reads c and writes r; its column pass
-    reads r and c and writes c and w_j; the fused column + next-row kernel
-    also writes the next r."""
+    reads r and c and writes c and w_j (one pass per scale: reads c, writes c
+    and w_j); the fused column + next-row kernel also writes the next r."""
     return {
         "fft_rows_fwd": 8 + 8,
         "fft_cols_ks": 8 + (4 if ks_real else 8),
         "fft_rows_inv": (4 if ks_real else 8) + 4,
         "starlet_tile": 4 + 4 * fuse + 4,
         "starlet_row": 4 + 4,
-        "starlet_col": 4 + 4 + 4 + 4,
+        "starlet_col": (4 + 4 + 4) if one_pass else (4 + 4 + 4 + 4),
         "starlet_colrow": 4 + 4 + 4 + 4 + 4,
     }[kernel]
 
@@ -126,6 +126,7 @@ def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=F
     ms per step, launches per step), from CUDA events around each launch."""
     chunks = per_kind["fft_rows_fwd"][1]  # one row-FFT launch per chunk of maps
     shape = (n, J, fuse)  # the workload a committed ncu capture must match
+    one_pass = "starlet_col" in per_kind and "starlet_row" not in per_kind  # large scales in one pass each
     groups = {}
     for name, (kinds, bpp, units) in method_groups(J, fuse).items():
         ks = [k for k in kinds if k in per_kind]
@@ -141,7 +142,7 @@ def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=F
         achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
         # the kernels' own reads and writes per unit launch (a large scale's
         # row pass 8 B/px and column pass 16 B/px through L2 or HBM)
-        kern_bytes = sum(algo_bytes_per_px_launch(k, fuse, ks_real) for k in ks) * px_step / chunks
+        kern_bytes = sum(algo_bytes_per_px_launch(k, fuse, ks_real, one_pass) for k in ks) * px_step / chunks
         trf = [ncu_traffic(k, shape=shape) for k in ks]
         l2 = [ncu_traffic(k, "l2_bytes_per_px", shape) for k in ks]
         groups[name] = {"kernels": ks, "method_bytes_per_px": bpp * units, "ms_per_step": ms,
@@ -152,7 +153,9 @@ def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=F
                         "l2_bytes_per_launch": (sum(l2) * px_step / chunks) if all(
                             t is not None for t in l2) else None,
                         "kernel_bytes_per_launch": kern_bytes}
-    dom = max(groups, key=lambda g: groups[g]["ms_per_step"])
+    # the dominant kernel: the kind with the most device time per step; its group gets the roofline
+    top = max(per_kind, key=lambda k: per_kind[k][0])
+    dom = next(g for g in groups if top in groups[g]["kernels"])
     d = groups[dom]
     # SM <-> L2 traffic of the whole step (the chunks' intermediates stay in
     # L2): every launch of every kind at its captured bytes per pixel
@@ -174,7 +177,9 @@ def step_roofline(per_kind, px_step, J, fuse, ms_step, peak, peak_src, ks_real=F
         "algorithmic_bytes_per_launch": d["method_bytes_per_launch"], "avg_launch_ms": d["avg_launch_ms"],
         "launches_per_step": d["launches_per_step"], "kernel_bytes_per_launch": d["kernel_bytes_per_launch"],
         "bytes_basis": "method bytes per pixel: KS 12, fused tile of F scales 8 + 4F, each unfused large scale 12 "
-                      "(read c_{j-1}, write c_j and w_j), credited to the group's launches together",
+                      "(read c_{j-1}, write c_j and w_j), credited to the group's launches together; the group is "
+                      "the one of the kernel kind with the most device time per step",
+        "dominant_kernel": top,
         "fused_scales": fuse,
         "groups": groups,
         "step": {"method_bytes_per_px": bpp_step, "achieved": step_gbs, "frac": step_gbs / peak,

@@ -47,6 +47,7 @@ def test_direct_map_tap_count_and_alu_peak():
     assert abs(bench.FP32_PEAK_TFLOPS - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
     assert bench.algo_bytes_per_px_launch("starlet_tile", 2) == 16
     assert bench.algo_bytes_per_px_launch("starlet_col", 2) == 16 and bench.algo_bytes_per_px_launch("starlet_row", 3) == 8
+    assert bench.algo_bytes_per_px_launch("starlet_col", 2, one_pass=True) == 12
 
 
 def test_roofline_uses_the_method_bytes():
@@ -69,3 +70,18 @@ def test_roofline_uses_the_method_bytes():
     ks = r["groups"]["ks"]
     assert abs(ks["achieved_gbs"] - 12 * px / 8 / ((0.56 / 8) * 1e-3) / 1e9) < 1e-6
     assert r["groups"]["starlet_tile"]["method_bytes_per_px"] == 16
+
+
+def test_roofline_one_pass_scales_take_the_dominant_kernel():
+    """With one pass per large scale the kernel with the most device time
+    (here the one-pass scale kernel, 0.48 ms) sets the roofline, even when
+    the three KS passes together take longer."""
+    sys.path.insert(0, ROOT)
+    import bench
+    px = 32 * 1024 * 1024
+    per_kind = {"fft_rows_fwd": (0.22, 8), "fft_cols_ks": (0.22, 8), "fft_rows_inv": (0.12, 8),
+                "starlet_tile": (0.19, 8), "starlet_col": (0.48, 32)}
+    r = bench.step_roofline(per_kind, px, 7, 2, 0.7, 6800.0, "measured")
+    assert r["dominant_kernel"] == "starlet_col" and r["kernel"].startswith("starlet_large_scale")
+    assert abs(r["achieved"] - 12 * px / 8 / ((0.48 / 32) * 1e-3) / 1e9) < 1e-6
+    assert r["kernel_bytes_per_launch"] == 12 * px / 8
