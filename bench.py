@@ -491,9 +491,10 @@ def per_kernel_hbm(fm, fn, px, fuse, reps=3, ks_real=False):
         fm.fm_profile_select(0)
         fm.fm_tune(fm.FM_TUNE_CHUNK_STREAMS, -1)
     chunks = res["fft_rows_fwd"][1]
+    one_pass = "starlet_col" in res and "starlet_row" not in res  # large scales in one pass each
     out = {}
     for k, (ms, cnt) in res.items():
-        b = algo_bytes_per_px_launch(k, fuse, ks_real) * px / chunks
+        b = algo_bytes_per_px_launch(k, fuse, ks_real, one_pass) * px / chunks
         gbs = b * cnt / (ms * 1e-3) / 1e9
         out[k] = {"ms_per_call": ms, "launches": cnt, "algorithmic_bytes_per_launch": b, "gbs": gbs,
                   "frac_hbm": gbs / peak}

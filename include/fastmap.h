@@ -356,9 +356,9 @@ int fm_device_error(void);
  *                        column and row passes; fp32, n >= 64, kappa_E
  *                        16-byte aligned), 0 = the complex inverse and its
  *                        real part; default: the real output for
- *                        fm_ks_invert with 64 <= n <= 4096 and for the
- *                        batched pipeline's chunks of 4096^2 maps (the sizes
- *                        where it measured faster)
+ *                        fm_ks_invert with n >= 64 and for the batched
+ *                        pipeline's chunks of maps from 4096^2 up (the
+ *                        sizes where it measured faster)
  *   FM_TUNE_SERVE_MERGE  servers: most maps that one merged run of queued
  *                        pyramid-only requests (R = 0, n <= 1024) of one
  *                        shape may hold (default 16; 1 = every request runs

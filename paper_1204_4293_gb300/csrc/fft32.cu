@@ -30,8 +30,9 @@
 //   rows_fwd32<SPLIT> : the complex row FFT Z of gamma1 + i gamma2 split into
 //                       the half spectra Gamma1 = (Z(kx) + conj Z(-kx)) / 2,
 //                       Gamma2 = (Z(kx) - conj Z(-kx)) / 2i, kx = 0 .. n/2,
-//                       each row stored as [Gamma1 | Gamma2], n/2 float2 each,
-//                       slot 0 packing the real pair (X(0), X(n/2));
+//                       each row stored as n/2 slots (Gamma1(kx), Gamma2(kx)),
+//                       16 bytes each, slot 0 packing the real pairs
+//                       (X(0), X(n/2));
 //   cols_ks32_e       : per strip of WS slots, column FFTs of the Gamma1 and
 //                       Gamma2 slots, kappa_E_hat, column inverse FFT; writes
 //                       the half spectrum H [n][n/2] into kappa's buffer;
@@ -205,19 +206,19 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__
             for (int r = 0; r < P::RL; ++r) sm[pad32(j + m * P::TV + r * P::NSL)] = v[m * P::RL + r];
         __syncthreads();
         if (live) {
-            float2 *d1 = work + row * P::N, *d2 = d1 + P::N / 2;  // Gamma1 slots, Gamma2 slots
+            // slot kx of the row: (Gamma1(kx), Gamma2(kx)) as one 16-byte element
+            float4 *d = reinterpret_cast<float4 *>(work + row * P::N);
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
                 const int kx = j + t * P::TV;
                 const float2 a = sm[pad32(kx)];
                 if (kx == 0) {
                     const float2 h = sm[pad32(P::N / 2)];
-                    d1[0] = make_float2(a.x, h.x);
-                    d2[0] = make_float2(a.y, h.y);
+                    d[0] = make_float4(a.x, h.x, a.y, h.y);
                 } else {
                     const float2 bm = sm[pad32(P::N - kx)];  // Z(n - kx); B = conj of it
-                    d1[kx] = make_float2(0.5f * (a.x + bm.x), 0.5f * (a.y - bm.y));
-                    d2[kx] = make_float2(0.5f * (a.y + bm.y), -0.5f * (a.x - bm.x));
+                    d[kx] = make_float4(0.5f * (a.x + bm.x), 0.5f * (a.y - bm.y), 0.5f * (a.y + bm.y),
+                                        -0.5f * (a.x - bm.x));
                 }
             }
         }
@@ -394,30 +395,34 @@ __global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, co
 }
 
 // ---- real-output inverse: column and row kernels ------------------------------
-// Slots per column strip (WS, 16-byte or wider row segments for the bulk
-// tensor copies).  A CTA of 2 WS n/32 threads: its first half transforms the
-// strip's Gamma1 columns, the second half the Gamma2 columns, at the same
-// time (the occupancy of the complex column pass); the second half hands its
-// spectra over through shared memory and leaves, and the first half forms
-// kappa_E_hat and runs the one inverse transform per slot on its own named
-// barrier.
+// Slots per column strip (WS; a strip is WS 16-byte (Gamma1, Gamma2) pairs
+// per row, one bulk tensor copy box wide).  A CTA of 2 WS n/32 threads: its
+// first half transforms the strip's Gamma1 columns, the second half the
+// Gamma2 columns, at the same time; the second half hands its spectra over
+// through shared memory and leaves, and the first half forms kappa_E_hat and
+// runs the one inverse transform per slot on its own named barrier.  The two
+// halves' exchange regions overlay the staged strip.  One-slot strips at
+// 4096^2 (68 KB, two 256-thread CTAs per SM) measured slower than two-slot
+// ones (one 512-thread CTA): 3.09 against 2.65 ms per 16 maps.
 template <int LOGN> struct PlanE {
     static constexpr int N = 1 << LOGN;
     static constexpr int WS = N <= 256 ? 16 : (N == 512 ? 8 : (N == 1024 ? 4 : (N <= 4096 ? 2 : 1)));
     static constexpr int RSZ = (N * WS + N * WS / 32 + 1 + 15) & ~15;  // float2 per region, 128-byte multiple
-    // the corner strip's dense exchange (2n elements) goes to the Gamma1
-    // region after its transform; its second half needs a region of its own
-    // when that one is too small (WS = 1)
-    static constexpr int R3 = RSZ >= 2 * N ? 0 : N;
+    // the corner strip's dense exchange (2n elements): with WS >= 2 both
+    // halves go to the Gamma1 region after its transform (the Gamma2 region
+    // carries the other slots' hand-over); with WS = 1 the strip is the
+    // corner slot alone and the second half writes its half in row order to
+    // its own region
+    static_assert(WS == 1 || RSZ >= 2 * N, "corner exchange");
     static constexpr int NH = WS * N / 32;  // threads of one half
     static constexpr int NT = 2 * NH;
     // CTAs per SM the register budget must allow: at most 128 registers a thread
     static constexpr int MINB = 65536 / (NT * 128) < 1 ? 1 : (65536 / (NT * 128) > 8 ? 8 : 65536 / (NT * 128));
 };
 
-// With use_tma (WS >= 2; mw: the work buffer as floats {2n, n, batch}, box
-// {2 WS, min(n, 256), 1}) the strip's Gamma1 and Gamma2 slots arrive by bulk
-// tensor copies, else by per-thread loads.
+// With use_tma (mw: the work buffer as floats {2n, n, batch}, box {4 WS,
+// min(n, 256), 1}) the strip's slots arrive by bulk tensor copies, else by
+// per-thread loads.
 template <int LOGN>
 __global__ void __launch_bounds__(PlanE<LOGN>::NT, PlanE<LOGN>::MINB)
     k_cols_ks32_e(const float2 *__restrict__ work, float2 *__restrict__ half, const float2 *__restrict__ tw,
@@ -431,7 +436,7 @@ __global__ void __launch_bounds__(PlanE<LOGN>::NT, PlanE<LOGN>::MINB)
     extern __shared__ __align__(16) unsigned char smem_col[];
     float2 *R1 = align128<float2>(smem_col);
     float2 *R2 = R1 + E::RSZ;
-    float2 *U1 = R1, *U2 = E::R3 ? R2 + E::RSZ : R1 + N;  // corner exchange
+    float2 *U1 = R1, *U2 = WS == 1 ? R2 : R1 + N;  // corner exchange
     const long b = blockIdx.x / STRIPS;
     const int s0 = (blockIdx.x % STRIPS) * WS;
     const int tid = threadIdx.x, hf = tid / NH, t = tid % NH, c = t % WS, j = t / WS;
@@ -443,26 +448,33 @@ __global__ void __launch_bounds__(PlanE<LOGN>::NT, PlanE<LOGN>::MINB)
         if (tid == 0) mbar_init(&bar, 1);
         __syncthreads();
         if (tid == 0) {
+            // the strip, [n][WS] (Gamma1, Gamma2) pairs, over both regions
             mbar_expect_tx(&bar, (uint32_t)(2 * N * WS * sizeof(float2)));
-            for (int k = 0; k < N / BR; ++k) {
-                tma_load_3d(R1 + k * BR * WS, &mw, 2 * s0, k * BR, (int)b, &bar);
-                tma_load_3d(R2 + k * BR * WS, &mw, N + 2 * s0, k * BR, (int)b, &bar);
-            }
+            for (int k = 0; k < N / BR; ++k) tma_load_3d(R1 + 2 * k * BR * WS, &mw, 4 * s0, k * BR, (int)b, &bar);
         }
         if (!tma_wait_all(&bar, 0)) return;  // the copies never completed (flagged)
+        // fft_vec's first barrier orders every thread's reads of the strip
+        // before the exchange writes that overlay it
 #pragma unroll
-        for (int r = 0; r < 32; ++r) v[r] = R[(j + r * P::TV) * WS + c];
+        for (int r = 0; r < 32; ++r) v[r] = R1[((j + r * P::TV) * WS + c) * 2 + hf];
     } else {
-        // rows of n float2: [Gamma1 | Gamma2]
-        const float2 *src = work + b * (long)N * N + hf * (N / 2) + s0 + c;
+        // rows of n/2 slots (Gamma1, Gamma2)
+        const float2 *src = work + b * (long)N * N + 2 * (s0 + c) + hf;
 #pragma unroll
         for (int r = 0; r < 32; ++r) v[r] = src[(long)(j + r * P::TV) * N];
     }
     fft_vec<LOGN, WS, false>(v, R, c, j, tw);  // Gamma1_hat (first half), Gamma2_hat (second)
     __syncthreads();                           // the last passes' reads of R1 and R2 are done
     if (hf) {
+        if (WS == 1 && s0 == 0) {  // the corner slot: in row order
 #pragma unroll
-        for (int e = 0; e < 32; ++e) R2[e * NH + t] = v[e];  // for the thread t of the first half
+            for (int m = 0; m < P::ML; ++m)
+#pragma unroll
+                for (int r = 0; r < P::RL; ++r) U2[j + m * P::TV + r * P::NSL] = v[m * P::RL + r];
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) R2[e * NH + t] = v[e];  // for the thread t of the first half
+        }
     }
     __syncthreads();
     if (hf) return;  // the rest runs on named barrier 1 of the first NH threads
@@ -490,7 +502,7 @@ __global__ void __launch_bounds__(PlanE<LOGN>::NT, PlanE<LOGN>::MINB)
                 for (int r = 0; r < P::RL; ++r) {
                     const int e = m * P::RL + r, yi = j + m * P::TV + r * P::NSL;
                     U1[yi] = v[e];
-                    U2[yi] = R2[e * NH + t];
+                    if (WS > 1) U2[yi] = R2[e * NH + t];
                 }
         }
         part_sync<NH>();
@@ -607,19 +619,20 @@ __global__ void __launch_bounds__(256, 2) k_rows_inv32_c2r(float *kap, long tota
 std::atomic<int> g_ks_real{-1};
 
 // Measured on GB300 (ms, complex / real-output inverse): the inverse alone,
-// 32 x 1024^2 0.320 / 0.298, 16 x 2048^2 0.846 / 0.772, 16 x 4096^2 4.20 /
-// 3.81, 64 x 512^2 0.171 / 0.163, 1 x 8192^2 1.45 / 2.03 (its strips of one
-// slot are too narrow for bulk copies); inside the batched KS + starlet
-// chunks (two streams) 32 x 1024^2 0.814 / 0.832, 16 x 2048^2 1.99 / 2.06,
-// 16 x 4096^2 10.83 / 10.50, 64 x 512^2 0.445 / 0.459: there the split row
-// pass and the column pass, whose second half of threads idles through the
-// inverse, overlap worse with the other stream's kernels; on maps larger
-// than L2 the saved bytes win.
+// 32 x 1024^2 0.320 / 0.298, 16 x 2048^2 0.840 / 0.755, 16 x 4096^2 4.20 /
+// 3.81, 64 x 512^2 0.171 / 0.163, 1 x 8192^2 1.454 / 1.426 (one-slot strips
+// by bulk copies since the slots are stored as 16-byte pairs; 2.03 with
+// per-thread loads); inside the batched KS + starlet chunks (two streams,
+// one pass per large scale) 32 x 1024^2 0.685 / 0.707, 16 x 2048^2 1.735 /
+// 1.770, 16 x 4096^2 8.45 / 8.25, 1 x 8192^2 2.544 / 2.497: at 1024^2 and
+// 2048^2 the split row pass and the column pass, whose second half of
+// threads idles through the inverse, overlap worse with the other stream's
+// kernels; on maps larger than L2 the saved bytes win.
 bool ks_real_for(int n, bool batched)
 {
     const int mode = g_ks_real.load(std::memory_order_relaxed);
     if (mode >= 0) return mode == 1 && n >= 64;
-    return batched ? n == 4096 : (n >= 64 && n <= 4096);
+    return batched ? n >= 4096 : n >= 64;
 }
 
 // ---------------------------------------------------------------------------
@@ -641,7 +654,7 @@ static int ks32_real_impl(const float *in1, const float *in2, long in_bs, float 
     const unsigned row2_grid = (unsigned)((total_rows + RPC2 - 1) / RPC2);
     const size_t row_smem = (size_t)RPC * (P::N + P::N / 32) * sizeof(float2) + 128;
     const size_t row2_smem = P2::NPASS > 1 ? (size_t)RPC2 * (P2::N + P2::N / 32) * sizeof(float2) + 128 : 0;
-    const size_t col_smem = (size_t)(2 * E::RSZ + E::R3) * sizeof(float2) + 128;
+    const size_t col_smem = (size_t)(2 * E::RSZ) * sizeof(float2) + 128;
     const int col_threads = E::NT;
     const unsigned col_grid = (unsigned)((long)batch * (P::N / 2 / E::WS));
     FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_fwd32<LOGN, true>, row_smem));
@@ -670,10 +683,10 @@ static int ks32_real_impl(const float *in1, const float *in2, long in_bs, float 
             tma_out = encode_map3d_f32(&mk, out1, kdims, strides, kbox);
         }
     }
-    if (E::WS >= 2 && P::N >= 1024 && (tma_mode & 32)) {
+    if (P::N >= 1024 && (tma_mode & 32)) {
         const uint64_t cdims[3] = {(uint64_t)2 * P::N, (uint64_t)P::N, (uint64_t)batch};
         const uint64_t cstrides[2] = {(uint64_t)P::N * 8, (uint64_t)P::N * P::N * 8};
-        const uint32_t cbox[3] = {(uint32_t)(2 * E::WS), (uint32_t)(P::N < 256 ? P::N : 256), 1};
+        const uint32_t cbox[3] = {(uint32_t)(4 * E::WS), (uint32_t)(P::N < 256 ? P::N : 256), 1};
         tma_col = encode_map3d_f32(&mc, work, cdims, cstrides, cbox) ? 1 : 0;
     }
     FM_LAUNCH(FM_K_FFT_ROWS_FWD, (k_rows_fwd32<LOGN, true>), row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs,

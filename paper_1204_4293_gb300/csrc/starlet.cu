@@ -457,7 +457,8 @@ template <int F> constexpr size_t tile2_smem()
 }
 
 // tmap (when use_tma): kappa as a 3-D tensor {n, n, batch} of fp32 with a
-// P x P x 1 box; interior tiles then arrive by one bulk tensor copy.
+// P x P x 1 box; every tile's box then arrives by one bulk tensor copy (edge
+// tiles fold the part outside the map afterwards).
 template <int F>
 __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3)
     k_st_tile32v2(const float *__restrict__ in, long in_bs, float *__restrict__ w_out, long w_bs, long w_ss,
@@ -482,10 +483,11 @@ __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3)
     const bool vok = vec_ok != 0;
 
     const bool interior = vok && ty0 >= HP && tx0 >= HP && ty0 + TS + HP <= n && tx0 + TS + HP <= n;
-    if (interior && (use_tma & 1)) {
+    if (use_tma & 1) {
         // one bulk tensor copy of the P x P halo box, completion on the mbarrier
         // (use_tma bit 1, a test hook: 16 bytes more are announced than the
-        // copy delivers, so the bounded wait runs out and is flagged)
+        // copy delivers, so the bounded wait runs out and is flagged).  Box
+        // columns and rows outside the map arrive as zeros.
         if (threadIdx.x == 0) mbar_init(bar, 1);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -493,6 +495,24 @@ __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3)
             tma_load_3d(b0, &tmap, tx0 - HP, ty0 - HP, (int)b, bar);
         }
         if (!tma_wait_all(bar, 0)) return;  // the copy never completed (flagged)
+        if (!interior) {
+            // Edge tile: each box position outside the map takes the value at
+            // its folded position.  Mirrored, that position lies in the box
+            // for every position the scales read (the halo H is at most HP,
+            // and a ragged last tile starts at most n - 1); it came with the
+            // copy and is not itself rewritten here.  Periodic positions, and
+            // far ones of a ragged tile, load from global memory.
+            const int oy = ty0 - HP, ox = tx0 - HP;
+            for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+                const int i = e / P, q = e - (e / P) * P;
+                const int gy = oy + i, gx = ox + q;
+                if (gy >= 0 && gy < n && gx >= 0 && gx < n) continue;
+                const int fy = fold_index(gy, n, boundary), fx = fold_index(gx, n, boundary);
+                const int si = fy - oy, sq = fx - ox;
+                b0[e] = boundary != FM_PERIODIC && si >= 0 && si < P && sq >= 0 && sq < P ? b0[si * P + sq]
+                                                                                          : src[(long)fy * n + fx];
+            }
+        }
     } else if (interior) {
         // interior tile: no folding; every thread's loads are in flight together
         constexpr int IT = (P * NQ + 255) / 256;
@@ -730,14 +750,23 @@ __global__ void __launch_bounds__(128) k_st_scale(const float *c_prev, float *c_
     }
     if (!tma_wait_all(&bar, 0)) return;  // the copies never completed (flagged)
     if (x0 - 2 * s < 0 || x0 + 512 + 2 * s > n) {
-        // halo columns outside the map (the copies filled them with zeros)
+        // halo columns outside the map (the copies filled them with zeros).
+        // Mirrored, they fold onto columns inside the map that this CTA
+        // staged itself (2s < 512 <= n: one reflection, within x0 - 2s ..
+        // x0 + 512 + 2s); periodic ones wrap to the map's other edge and come
+        // from global memory.
         for (int e = threadIdx.x; e < (KR + 4) * 4 * s; e += blockDim.x) {
             const int t = e / (4 * s), h = e % (4 * s);
             const int xl = h < 2 * s ? h : 512 + h;  // left halo, then right halo
             const int x = x0 - 2 * s + xl;
             if (x < 0 || x >= n) {
-                const int y = fold_index(r0 + s * (mb + t - 2), n, boundary);
-                sw[t * RW + xl] = cb[(long)y * n + fold_index(x, n, boundary)];
+                const int xf = fold_index(x, n, boundary);
+                if (boundary == FM_PERIODIC) {
+                    const int y = fold_index(r0 + s * (mb + t - 2), n, boundary);
+                    sw[t * RW + xl] = cb[(long)y * n + xf];
+                } else {
+                    sw[t * RW + xl] = sw[t * RW + xf - x0 + 2 * s];
+                }
             }
         }
         __syncthreads();

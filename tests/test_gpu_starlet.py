@@ -123,25 +123,29 @@ def test_tile_kernel_variants(variant, n, J):
         fm.fm_tune(fm.FM_TUNE_TILE, -1)
 
 
-@pytest.mark.parametrize("n,J,batch", [(256, 5, 3), (1024, 7, 2), (200, 4, 1), (4096, 9, 1)])
-def test_bulk_copy_halo_equals_thread_loads(n, J, batch):
-    # interior tiles take their halo, and interior column-pass row groups
-    # their window and c_{j-1} rows, by bulk tensor copies (default) or by
-    # per-thread loads: identical pyramids, no wait ran out
+@pytest.mark.parametrize("n,J,batch,boundary", [(256, 5, 3, 0), (1024, 7, 2, 0), (1024, 7, 2, 1), (200, 4, 1, 0),
+                                                 (968, 6, 2, 0), (968, 6, 2, 1), (1000, 7, 1, 1), (4096, 9, 1, 0)])
+def test_bulk_copy_halo_equals_thread_loads(n, J, batch, boundary):
+    # tiles take their halo box (edge tiles: then folded in shared memory),
+    # and interior column-pass row groups their window and c_{j-1} rows, by
+    # bulk tensor copies (default) or by per-thread loads: identical
+    # pyramids for every fused depth, both boundaries and ragged maps (968:
+    # the last tile's far halo folds outside its box), no wait ran out
     fm = _fm()
     maps = np.stack([synth.grf_kappa(n, seed=7 + b) for b in range(batch)]).astype(np.float32)
     kap = torch.from_numpy(maps).cuda()
-    fm.fm_tune(fm.FM_TUNE_TMA, 63)
-    with_tma = fm.fm_starlet_forward(kap, J)
-    fm.fm_tune(fm.FM_TUNE_TMA, 0)
-    try:
-        without = fm.fm_starlet_forward(kap, J)
-    finally:
-        fm.fm_tune(fm.FM_TUNE_TMA, -1)
-    torch.cuda.synchronize()
-    assert fm.fm_device_error() == 0
-    assert torch.equal(with_tma, without)
-    ref = oracle.starlet(maps[batch - 1].astype(np.float64), J)
+    for fuse in range(1, min(3, J - 1) + 1):
+        fm.fm_tune(fm.FM_TUNE_TMA, 63)
+        with_tma = fm.fm_starlet_forward(kap, J, boundary=boundary, fuse_depth=fuse)
+        fm.fm_tune(fm.FM_TUNE_TMA, 0)
+        try:
+            without = fm.fm_starlet_forward(kap, J, boundary=boundary, fuse_depth=fuse)
+        finally:
+            fm.fm_tune(fm.FM_TUNE_TMA, -1)
+        torch.cuda.synchronize()
+        assert fm.fm_device_error() == 0
+        assert torch.equal(with_tma, without), fuse
+    ref = oracle.starlet(maps[batch - 1].astype(np.float64), J, boundary)
     assert max(band_errs(with_tma[batch - 1].cpu().numpy(), ref)) <= 1e-5
 
 
