@@ -134,11 +134,13 @@ __device__ __forceinline__ void fft_vec(float2 (&v)[32], float2 *sm, int c, int 
 // rows of gamma1 (m1) and gamma2 (m2) arrive by bulk tensor copies into the
 // exchange buffer, viewed as [RPC][n] floats per array, before the first
 // pass reads them.
-template <int LOGN, bool SPLIT>
+// ROT: the noise maps' rotated shear (a separate instantiation, so that the
+// plain transform carries none of the generator's code)
+template <int LOGN, bool SPLIT, bool ROT>
 __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__ in1, const float *__restrict__ in2,
                                                        long in_bs, float2 *__restrict__ work, long total_rows,
                                                        const float2 *__restrict__ tw, uint64_t seed, int r0,
-                                                       int rotate, const __grid_constant__ CUtensorMap m1,
+                                                       const __grid_constant__ CUtensorMap m1,
                                                        const __grid_constant__ CUtensorMap m2, int use_tma)
 {
     pdl_entry();
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__
                 const int x = j + r * P::TV;
                 float a = st1[vr * P::N + x];
                 float cc = in2 ? st2[vr * P::N + x] : 0.f;
-                if (rotate) rotate_shear(a, cc, seed, r0 + b, y, x, P::N);
+                if constexpr (ROT) rotate_shear(a, cc, seed, r0 + b, y, x, P::N);
                 v[r] = make_float2(a, cc);
             }
             staged = true;  // fft_vec's first barrier orders these reads before the exchange writes
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__
             const int x = j + r * P::TV;
             float a = __ldcs(p1 + x);  // the shear is read once
             float cc = p2 ? __ldcs(p2 + x) : 0.f;
-            if (rotate) rotate_shear(a, cc, seed, r0 + b, y, x, P::N);
+            if constexpr (ROT) rotate_shear(a, cc, seed, r0 + b, y, x, P::N);
             v[r] = make_float2(a, cc);
         }
     } else if (!staged) {
@@ -657,7 +659,8 @@ static int ks32_real_impl(const float *in1, const float *in2, long in_bs, float 
     const size_t col_smem = (size_t)(2 * E::RSZ) * sizeof(float2) + 128;
     const int col_threads = E::NT;
     const unsigned col_grid = (unsigned)((long)batch * (P::N / 2 / E::WS));
-    FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_fwd32<LOGN, true>, row_smem));
+    auto krf = rotate ? k_rows_fwd32<LOGN, true, true> : k_rows_fwd32<LOGN, true, false>;
+    FM_CUDA_TRY(fm::smem_attr((const void *)krf, row_smem));
     FM_CUDA_TRY(fm::smem_attr((const void *)k_cols_ks32_e<LOGN>, col_smem));
     if (row2_smem) FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_inv32_c2r<LOGN>, row2_smem));
     CUtensorMap m1, m2, mc, mk;
@@ -689,8 +692,8 @@ static int ks32_real_impl(const float *in1, const float *in2, long in_bs, float 
         const uint32_t cbox[3] = {(uint32_t)(4 * E::WS), (uint32_t)(P::N < 256 ? P::N : 256), 1};
         tma_col = encode_map3d_f32(&mc, work, cdims, cstrides, cbox) ? 1 : 0;
     }
-    FM_LAUNCH(FM_K_FFT_ROWS_FWD, (k_rows_fwd32<LOGN, true>), row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs,
-              work, total_rows, tw, seed, r0, rotate ? 1 : 0, m1, m2, tma_in);
+    FM_LAUNCH(FM_K_FFT_ROWS_FWD, krf, row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs, work, total_rows, tw, seed,
+              r0, m1, m2, tma_in);
     FM_LAUNCH(FM_K_FFT_COLS_KS, k_cols_ks32_e<LOGN>, col_grid, col_threads, col_smem, s, (const float2 *)work,
               reinterpret_cast<float2 *>(out1), tw, mc, tma_col);
     const float scale = out_scale / ((float)P::N * (float)P::N);
@@ -719,7 +722,8 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
     // exchange buffer (also the TMA strip: n W float2) + 128 bytes of alignment
     const size_t col_smem = P::NPASS > 1 ? (size_t)(P::N * P::W + P::N * P::W / 32 + 1) * sizeof(float2) + 128 : 0;
     const unsigned col_grid = (unsigned)((long)batch * (P::N / P::W));
-    FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_fwd32<LOGN, false>, row_smem));
+    auto krf = rotate ? k_rows_fwd32<LOGN, false, true> : k_rows_fwd32<LOGN, false, false>;
+    FM_CUDA_TRY(fm::smem_attr((const void *)krf, row_smem));
     FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_inv32<LOGN>, row_smem));
     FM_CUDA_TRY(fm::smem_attr((const void *)k_cols_ks32<LOGN>, col_smem));
     // bulk tensor copies of whole row groups (RPC consecutive rows of the
@@ -766,8 +770,8 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
                       ? (1 | ((tma_mode & 64) && P::N >= 8192 ? 2 : 0))
                       : 0;
     }
-    FM_LAUNCH(FM_K_FFT_ROWS_FWD, (k_rows_fwd32<LOGN, false>), row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs,
-              work, total_rows, tw, seed, r0, rotate ? 1 : 0, m1, m2, tma_in);
+    FM_LAUNCH(FM_K_FFT_ROWS_FWD, krf, row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs, work, total_rows, tw, seed,
+              r0, m1, m2, tma_in);
     FM_LAUNCH(FM_K_FFT_COLS_KS, k_cols_ks32<LOGN>, col_grid, col_threads, col_smem, s, work, tw, op, filt, mc,
               tma_col);
     if (op == FFT_OP_SPECTRUM) return FM_OK;
