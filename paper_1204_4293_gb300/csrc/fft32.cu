@@ -238,7 +238,9 @@ __global__ void __launch_bounds__(256, 2) k_rows_fwd32(const float *__restrict__
 // With use_tma (n >= 64, every CTA's RPC rows inside the batch), the CTA's
 // complex rows arrive by one bulk tensor copy (mw: the work buffer as floats)
 // into the exchange buffer, viewed as [RPC][n] float2.
-template <int LOGN>
+// WITH_B: kappa_B (the imaginary part) written too, a separate instantiation
+// so that the kappa_E-only store loop has no per-element branch
+template <int LOGN, bool WITH_B>
 __global__ void __launch_bounds__(256, 2) k_rows_inv32(const float2 *__restrict__ work, float *__restrict__ out1,
                                                        float *__restrict__ out2, long total_rows,
                                                        const float2 *__restrict__ tw, float scale,
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(256, 2) k_rows_inv32(const float2 *__restrict_
                 const long pos = row * P::N + j + m * P::TV + r * P::NSL;
                 const float2 x = v[m * P::RL + r];
                 out1[pos] = x.x * scale;
-                if (out2) out2[pos] = x.y * scale;
+                if constexpr (WITH_B) out2[pos] = x.y * scale;
             }
     }
 }
@@ -294,12 +296,15 @@ __global__ void __launch_bounds__(256, 2) k_rows_inv32(const float2 *__restrict_
 // n / min(n, 256) bulk tensor copies into the exchange buffer, densely as
 // [n][W] float2, instead of 32 strided loads per thread; with bit 1 the
 // result leaves the same way (the spectrum-only mode stores per thread).
-template <int LOGN>
+// KSINV: the inverse KS multiply fixed at compile time (the pipeline's
+// instantiation, no per-element branch on op); else op chooses at run time.
+template <int LOGN, bool KSINV>
 __global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, const float2 *__restrict__ tw,
-                                                   int op, const float2 *__restrict__ filt,
+                                                   int op_arg, const float2 *__restrict__ filt,
                                                    const __grid_constant__ CUtensorMap mw, int use_tma)
 {
     pdl_entry();
+    const int op = KSINV ? FFT_OP_KS_INV : op_arg;
     using P = Plan32<LOGN>;
     constexpr int W = P::W, N = P::N;
     constexpr int STRIPS = N / W;
@@ -724,8 +729,10 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
     const unsigned col_grid = (unsigned)((long)batch * (P::N / P::W));
     auto krf = rotate ? k_rows_fwd32<LOGN, false, true> : k_rows_fwd32<LOGN, false, false>;
     FM_CUDA_TRY(fm::smem_attr((const void *)krf, row_smem));
-    FM_CUDA_TRY(fm::smem_attr((const void *)k_rows_inv32<LOGN>, row_smem));
-    FM_CUDA_TRY(fm::smem_attr((const void *)k_cols_ks32<LOGN>, col_smem));
+    auto kri = out2 ? k_rows_inv32<LOGN, true> : k_rows_inv32<LOGN, false>;
+    auto kcl = op == FFT_OP_KS_INV ? k_cols_ks32<LOGN, true> : k_cols_ks32<LOGN, false>;
+    FM_CUDA_TRY(fm::smem_attr((const void *)kri, row_smem));
+    FM_CUDA_TRY(fm::smem_attr((const void *)kcl, col_smem));
     // bulk tensor copies of whole row groups (RPC consecutive rows of the
     // batch): n >= 64; the input rows either contiguous over the batch
     // (in_bs = n^2) or one broadcast map (in_bs = 0) holding a CTA's rows
@@ -772,12 +779,11 @@ static int ks32_impl(const float *in1, const float *in2, long in_bs, float *out1
     }
     FM_LAUNCH(FM_K_FFT_ROWS_FWD, krf, row_grid, RPC * P::TV, row_smem, s, in1, in2, in_bs, work, total_rows, tw, seed,
               r0, m1, m2, tma_in);
-    FM_LAUNCH(FM_K_FFT_COLS_KS, k_cols_ks32<LOGN>, col_grid, col_threads, col_smem, s, work, tw, op, filt, mc,
-              tma_col);
+    FM_LAUNCH(FM_K_FFT_COLS_KS, kcl, col_grid, col_threads, col_smem, s, work, tw, op, filt, mc, tma_col);
     if (op == FFT_OP_SPECTRUM) return FM_OK;
     const float scale = out_scale / ((float)P::N * (float)P::N);
-    FM_LAUNCH(FM_K_FFT_ROWS_INV, k_rows_inv32<LOGN>, row_grid, RPC * P::TV, row_smem, s, work, out1, out2,
-              total_rows, tw, scale, mw, tma_out);
+    FM_LAUNCH(FM_K_FFT_ROWS_INV, kri, row_grid, RPC * P::TV, row_smem, s, work, out1, out2, total_rows, tw, scale,
+              mw, tma_out);
     return FM_OK;
 }
 

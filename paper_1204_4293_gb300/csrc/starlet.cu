@@ -458,8 +458,10 @@ template <int F> constexpr size_t tile2_smem()
 
 // tmap (when use_tma): kappa as a 3-D tensor {n, n, batch} of fp32 with a
 // P x P x 1 box; every tile's box then arrives by one bulk tensor copy (edge
-// tiles fold the part outside the map afterwards).
-template <int F>
+// tiles fold the part outside the map afterwards).  VOK (16-byte row
+// accesses valid: vec_ok) is a template parameter, so that the stores of the
+// usual case carry no scalar fallback.
+template <int F, bool VOK>
 __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3)
     k_st_tile32v2(const float *__restrict__ in, long in_bs, float *__restrict__ w_out, long w_bs, long w_ss,
                   float *__restrict__ c_out, long c_bs, int n, int boundary, int tiles_x, int tiles_per_map,
@@ -480,7 +482,7 @@ __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3)
     const int ty0 = (t / tiles_x) * TS;
     const int tx0 = (t % tiles_x) * TS;
     const float *src = in + b * in_bs;
-    const bool vok = vec_ok != 0;
+    constexpr bool vok = VOK;
 
     const bool interior = vok && ty0 >= HP && tx0 >= HP && ty0 + TS + HP <= n && tx0 + TS + HP <= n;
     if (use_tma & 1) {
@@ -1147,7 +1149,7 @@ static int tile32_launch(const float *in, float *w_out, long w_bs, long w_ss, fl
     const int tiles_x = (n + TS - 1) / TS;
     const int tiles_per_map = tiles_x * tiles_x;
     if (variant == 1) {
-        auto k = k_st_tile32v2<F>;
+        auto k = vec_ok ? k_st_tile32v2<F, true> : k_st_tile32v2<F, false>;
         const size_t smem2 = tile2_smem<F>();
         FM_CUDA_TRY(fm::smem_attr((const void *)k, smem2));
         CUtensorMap map;
