@@ -318,8 +318,11 @@ int fm_device_error(void);
 
 /* Tuning knobs (process-wide; value < 0 restores the default):
  *   FM_TUNE_CHUNK_BYTES  budget of one chunk's intermediates in batched
- *                        KS + starlet calls (default 80 MiB, so two chunks in
- *                        flight keep most of them in L2); 0 = no chunking
+ *                        KS + starlet calls (3 n^2 values a map: the FFT
+ *                        work buffer, which also holds the starlet's scratch
+ *                        maps, and kappa; default 48 MiB, four 1024^2 fp32
+ *                        maps, so two chunks in flight stay in L2); 0 = no
+ *                        chunking
  *   FM_TUNE_GRAPHS       1 = replay batched calls from cached CUDA graphs
  *                        (default), 0 = launch every kernel each call
  *   FM_TUNE_CHUNK_STREAMS number of streams chunks alternate on (1 to 4,

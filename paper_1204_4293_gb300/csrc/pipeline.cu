@@ -55,9 +55,14 @@ struct ChunkPlan {
     size_t work_b = 0, kap_b = 0, st_b = 0, slot_b = 0;
 };
 
-// measured on GB300 (32 x 1024^2, J = 7): 2 streams x 80 MB chunks with graph
-// replay 0.89 ms per batch, unchunked 1.05 ms, 40 MB 1.06 ms, 100 MB 0.97 ms
-constexpr int64_t kDefaultChunkBytes = 80ll << 20;
+// A chunk's intermediates: the FFT work buffer (2 n^2 per map), kappa (n^2)
+// and, where they do not fit in the work buffer (dead once kappa is formed),
+// the starlet's scratch maps.  Measured on GB300 (32 x 1024^2, J = 7), with
+// the scratch in its own buffer (20 MB a map): 2 streams x 80 MB chunks with
+// graph replay 0.89 ms per batch, unchunked 1.05 ms, 40 MB 1.06 ms, 100 MB
+// 0.97 ms; four maps a chunk stayed the best choice as the kernels changed.
+// With the scratch in the work buffer (12 MB a map) four maps take 48 MB.
+constexpr int64_t kDefaultChunkBytes = 48ll << 20;
 std::atomic<int64_t> g_chunk_bytes{kDefaultChunkBytes};
 std::atomic<int> g_chunk_bytes_set{0};  // set by fm_tune: overrides the autotuned budget
 std::atomic<int> g_chunk_streams{2};
@@ -74,7 +79,9 @@ ChunkPlan plan_chunks(int n, int J, int batch, const fm_config &cfg)
 {
     const size_t es = cfg.precision == FM_F64 ? 8 : 4;
     const size_t nn = (size_t)n * n;
-    const size_t per_map = nn * 3 * es + starlet_scratch_elems(n, J, 1, cfg) * es;
+    // the starlet's scratch maps go to the work buffer when they fit there
+    const bool st_in_work = starlet_scratch_elems(n, J, 1, cfg) <= 2 * nn;
+    const size_t per_map = nn * 3 * es + (st_in_work ? 0 : starlet_scratch_elems(n, J, 1, cfg) * es);
     ChunkPlan p;
     int64_t budget = g_chunk_bytes.load();
     TunedPlan tp;
@@ -87,7 +94,7 @@ ChunkPlan plan_chunks(int n, int J, int batch, const fm_config &cfg)
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     p.work_b = up((size_t)p.C * nn * 2 * es);
     p.kap_b = up((size_t)p.C * nn * es);
-    p.st_b = up(starlet_scratch_elems(n, J, p.C, cfg) * es);
+    p.st_b = st_in_work ? 0 : up(starlet_scratch_elems(n, J, p.C, cfg) * es);
     p.slot_b = p.work_b + p.kap_b + p.st_b;
     return p;
 }
@@ -100,7 +107,9 @@ int run_chunk(const char *g1, const char *g2, char *pyr, int n, int J, int b0, i
 {
     const size_t es = cfg.precision == FM_F64 ? 8 : 4;
     const size_t nn = (size_t)n * n;
-    char *work = slot, *kap = slot + p.work_b, *st = kap + p.kap_b;
+    // the starlet's scratch: its own buffer, or the work buffer, which the
+    // starlet kernels (later on the same stream) find dead
+    char *work = slot, *kap = slot + p.work_b, *st = p.st_b ? kap + p.kap_b : work;
     const size_t in_off = rotate ? 0 : b0 * nn * es;
     int r = launch_ks(g1 + in_off, g2 + in_off, rotate ? 0 : (long)nn, kap, nullptr, work, n, bc, cfg.precision, false,
                       seed, r0, rotate, s, true);

@@ -199,7 +199,7 @@ int fm_autotune(int n, int J, int batch, const fm_config *cfgp, fm_plan *best)
     TunedPlan cur = base;
     double cur_ms = base_ms;
     const int fmax = std::min(cfg.precision == FM_F64 ? 3 : 4, J - 1);
-    const int chunks[] = {40, 60, 80, 120};
+    const int chunks[] = {24, 36, 48, 64, 96};
     for (int sweep = 0; sweep < 2; ++sweep) {
         for (int dim = 0; dim < 4; ++dim) {
             std::vector<TunedPlan> cand;

@@ -27,7 +27,7 @@ def test_autotuned_plan_is_used_and_matches_oracle(fm, n, J, batch, dtype):
     plan = fm.fm_autotune(n, J, batch, precision=prec)
     fmax = min(4 if dtype == np.float32 else 3, J - 1)
     assert 1 <= plan["fuse_depth"] <= fmax and plan["large_path"] in (1, 3, 4) and plan["tile"] in (0, 1)
-    assert plan["chunk_mb"] in (40, 60, 80, 120)
+    assert plan["chunk_mb"] in (24, 36, 48, 64, 96)
     assert 0 < plan["ms"] <= plan["default_ms"]  # the built-in plan is the first candidate
     assert fm.fm_autotune_get(n, J, prec) == plan
     assert fm.fm_starlet_fuse_depth(n, J, precision=prec) == plan["fuse_depth"]
