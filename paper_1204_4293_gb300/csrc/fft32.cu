@@ -358,7 +358,9 @@ __global__ void __launch_bounds__(512) k_cols_ks32(float2 *__restrict__ work, co
                 const int den = k1 * k1 + k2 * k2;
                 d = make_float2(0.f, 0.f);
                 if (den != 0) {
-                    const float inv = 1.f / (float)den;
+                    // the pipeline's instantiation: the fast reciprocal (2 ulp, no
+                    // division subroutine in the unrolled loop)
+                    const float inv = KSINV ? __fdividef(1.f, (float)den) : 1.f / (float)den;
                     const float im = (float)(2 * k1 * k2) * inv;
                     d = make_float2((float)(k1 * k1 - k2 * k2) * inv, op == FFT_OP_KS_FWD ? im : -im);
                 }
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(PlanE<LOGN>::NT, PlanE<LOGN>::MINB)
             for (int r = 0; r < P::RL; ++r) {
                 const int e = m * P::RL + r, yi = j + m * P::TV + r * P::NSL;
                 const int k2 = yi < N / 2 ? yi : yi - N;
-                const float inv = 1.f / (float)(k1 * k1 + k2 * k2);
+                const float inv = __fdividef(1.f, (float)(k1 * k1 + k2 * k2));  // 2 ulp
                 const float dr = (float)(k1 * k1 - k2 * k2) * inv, di = (float)(2 * k1 * k2) * inv;
                 const float2 a = v[e], g = R2[e * NH + t];
                 v[e] = yi == N / 2 ? make_float2(dr * a.x + di * a.y, dr * a.y - di * a.x)  // conj(D) Gamma1
@@ -529,7 +531,7 @@ __global__ void __launch_bounds__(PlanE<LOGN>::NT, PlanE<LOGN>::MINB)
                     // kx = 0: D = -1 (0 at k = 0)
                     const float2 kz = yi == 0 ? make_float2(0.f, 0.f) : make_float2(-a1.x, -a1.y);
                     // kx = n/2 (k1 = -n/2)
-                    const float inv = 1.f / (float)(N / 2 * (N / 2) + k2 * k2);
+                    const float inv = __fdividef(1.f, (float)(N / 2 * (N / 2) + k2 * k2));
                     const float dr = (float)(N / 2 * (N / 2) - k2 * k2) * inv, di = (float)(-N * k2) * inv;
                     const float2 kh = (yi == 0 || yi == N / 2)
                                           ? make_float2(dr * b1.x + di * b2.x, dr * b1.y + di * b2.y)

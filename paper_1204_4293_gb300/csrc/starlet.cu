@@ -799,8 +799,9 @@ __global__ void __launch_bounds__(128) k_st_scale(const float *c_prev, float *c_
                 const float4 p = ctr[(k + 2) % 3];
                 alignas(16) float w[4] = {p.x - cj[0], p.y - cj[1], p.z - cj[2], p.w - cj[3]};
                 const long px = (long)y * n + x;
-                emit_band<float>(w, w_out + b * w_bs, px, y, x, n, true);
-                if (c_next) emit_band<float>(cj, c_next + b * next_bs, px, y, x, n, true, true);
+                // n is a multiple of 512: the whole vector is inside
+                st16cs(w_out + b * w_bs + px, w);
+                if (c_next) st16(c_next + b * next_bs + px, cj);
             }
         }
     }
