@@ -504,15 +504,28 @@ __global__ void __launch_bounds__(256, F >= 4 ? 1 : 3)
             // and a ragged last tile starts at most n - 1); it came with the
             // copy and is not itself rewritten here.  Periodic positions, and
             // far ones of a ragged tile, load from global memory.
+            // The outside positions are enumerated directly: whole box rows
+            // above or below the map, then the columns left or right of it in
+            // the other rows.
             const int oy = ty0 - HP, ox = tx0 - HP;
-            for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
-                const int i = e / P, q = e - (e / P) * P;
-                const int gy = oy + i, gx = ox + q;
-                if (gy >= 0 && gy < n && gx >= 0 && gx < n) continue;
-                const int fy = fold_index(gy, n, boundary), fx = fold_index(gx, n, boundary);
+            const int rt = oy < 0 ? -oy : 0, rb = oy + P > n ? oy + P - n : 0;
+            const int cl = ox < 0 ? -ox : 0, cr = ox + P > n ? ox + P - n : 0, cw = cl + cr;
+            auto fix = [&](int i, int q) {
+                const int fy = fold_index(oy + i, n, boundary), fx = fold_index(ox + q, n, boundary);
                 const int si = fy - oy, sq = fx - ox;
-                b0[e] = boundary != FM_PERIODIC && si >= 0 && si < P && sq >= 0 && sq < P ? b0[si * P + sq]
-                                                                                          : src[(long)fy * n + fx];
+                b0[i * P + q] = boundary != FM_PERIODIC && si >= 0 && si < P && sq >= 0 && sq < P
+                                    ? b0[si * P + sq]
+                                    : src[(long)fy * n + fx];
+            };
+            for (int e = threadIdx.x; e < (rt + rb) * P; e += blockDim.x) {
+                const int k = e / P, q = e - k * P;
+                fix(k < rt ? k : P - rb + (k - rt), q);
+            }
+            if (cw > 0) {
+                for (int e = threadIdx.x; e < (P - rt - rb) * cw; e += blockDim.x) {
+                    const int k = e / cw, c = e - k * cw;
+                    fix(rt + k, c < cl ? c : P - cr + (c - cl));
+                }
             }
         }
     } else if (interior) {
@@ -751,12 +764,26 @@ __global__ void __launch_bounds__(128) k_st_scale(const float *c_prev, float *c_
         }
     }
     if (!tma_wait_all(&bar, 0)) return;  // the copies never completed (flagged)
-    if (x0 - 2 * s < 0 || x0 + 512 + 2 * s > n) {
-        // halo columns outside the map (the copies filled them with zeros).
-        // Mirrored, they fold onto columns inside the map that this CTA
-        // staged itself (2s < 512 <= n: one reflection, within x0 - 2s ..
-        // x0 + 512 + 2s); periodic ones wrap to the map's other edge and come
-        // from global memory.
+    if ((x0 == 0 || x0 + 512 == n) && boundary != FM_PERIODIC) {
+        // halo columns outside the map (the copies filled them with zeros):
+        // with 2s <= 256 < 512 only the first CTA's left halo and the last
+        // one's right halo leave the map.  Mirrored, staged column 2s + x of
+        // map column x (x0 = 0) gets column -x, and map column n + h
+        // (x0 = n - 512) gets n - 2 - h; both lie inside the map and were
+        // staged by this CTA.
+        const bool lo = x0 == 0, hi = x0 + 512 == n;
+        for (int h = threadIdx.x; h < 2 * s; h += blockDim.x) {
+#pragma unroll
+            for (int t = 0; t < KR + 4; ++t) {
+                float *row = sw + t * RW;
+                if (lo) row[h] = row[4 * s - h];
+                if (hi) row[512 + 2 * s + h] = row[510 + 2 * s - h];
+            }
+        }
+        __syncthreads();
+    } else if (x0 - 2 * s < 0 || x0 + 512 + 2 * s > n) {
+        // periodic: halo columns outside the map wrap to its other edge and
+        // come from global memory
         for (int e = threadIdx.x; e < (KR + 4) * 4 * s; e += blockDim.x) {
             const int t = e / (4 * s), h = e % (4 * s);
             const int xl = h < 2 * s ? h : 512 + h;  // left halo, then right halo
