@@ -756,9 +756,13 @@ __global__ void __launch_bounds__(128) k_st_scale(const float *c_prev, float *c_
     const float *cb = c_prev + b * (long)n * n;
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_expect_tx(&bar, (uint32_t)((KR + 4) * (512 + 4 * s) * sizeof(float)));
-        for (int t = 0; t < KR + 4; ++t) {
+    // one window row per lane of the first warp, after lane 0 announced the bytes
+    static_assert(KR + 4 <= 32, "window rows per warp");
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) mbar_expect_tx(&bar, (uint32_t)((KR + 4) * (512 + 4 * s) * sizeof(float)));
+        __syncwarp();
+        const int t = threadIdx.x;
+        if (t < KR + 4) {
             const int y = fold_index(r0 + s * (mb + t - 2), n, boundary);
             tma_load_3d(sw + t * RW, &mc, 0, x0 / (2 * s) - 1, (int)(b * n + y), &bar);
         }
@@ -1309,12 +1313,16 @@ static int starlet_impl(const T *kappa, T *pyr, long pyr_bs, int n, int J, int b
                 for (int j = f + 1; j <= J - 1; ++j) {
                     const int sp = 1 << (j - 1);
                     const long dst_bs = j == J - 1 ? pyr_bs : nn;
-                    const size_t ssm = 128 + (size_t)(KRS + 4) * ((512 + 4 * sp + 31) & ~31) * sizeof(float);
-                    FM_CUDA_TRY(fm::smem_attr((const void *)k_st_scale<KRS>, ssm));
-                    const unsigned gys = (unsigned)(sp * ((((n + sp - 1) / sp) + KRS - 1) / KRS));
-                    FM_LAUNCH(FM_K_STARLET_COL, k_st_scale<KRS>, dim3(n / 512, gys, batch), 128, ssm, s,
-                              (const float *)srcs[j], (float *)dsts[j], dst_bs, (float *)(pyr + (long)(j - 1) * nn),
-                              pyr_bs, n, sp, bnd, maps[j]);
+                    // wide halos (s >= 32): 16 output rows a CTA, so that the
+                    // window's four extra rows are re-read less often
+                    const int kr = sp >= 32 ? 16 : KRS;
+                    auto ksc = kr == 16 ? k_st_scale<16> : k_st_scale<KRS>;
+                    const size_t ssm = 128 + (size_t)(kr + 4) * ((512 + 4 * sp + 31) & ~31) * sizeof(float);
+                    FM_CUDA_TRY(fm::smem_attr((const void *)ksc, ssm));
+                    const unsigned gys = (unsigned)(sp * ((((n + sp - 1) / sp) + kr - 1) / kr));
+                    FM_LAUNCH(FM_K_STARLET_COL, ksc, dim3(n / 512, gys, batch), 128, ssm, s, (const float *)srcs[j],
+                              (float *)dsts[j], dst_bs, (float *)(pyr + (long)(j - 1) * nn), pyr_bs, n, sp, bnd,
+                              maps[j]);
                 }
                 return FM_OK;
             }
