@@ -112,6 +112,14 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b)
     return cmake<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return cmake<V>(a.x * s, a.y * s); }
+// fp32: one packed two-lane instruction each (add.rn.f32x2; a - b as
+// fma.rn.f32x2(b, -1, a), exact in the product, so the same rounding as the
+// scalar forms)
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
 
 // ---- index folding at the map edge ------------------------------------------------
 // Mirror: whole-sample symmetric extension (period 2(n-1)); periodic: mod n.
