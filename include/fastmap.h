@@ -358,10 +358,9 @@ int fm_device_error(void);
  *                        Hermitian half of kappa_E's spectrum (real-output
  *                        column and row passes; fp32, n >= 64, kappa_E
  *                        16-byte aligned), 0 = the complex inverse and its
- *                        real part; default: the real output for
- *                        fm_ks_invert with n >= 64 and for the batched
- *                        pipeline's chunks of maps from 4096^2 up (the
- *                        sizes where it measured faster)
+ *                        real part; default: the real output from
+ *                        n = 512 up, in fm_ks_invert and in the batched
+ *                        pipeline's chunks (where it measured faster)
  *   FM_TUNE_SERVE_MERGE  servers: most maps that one merged run of queued
  *                        pyramid-only requests (R = 0, n <= 1024) of one
  *                        shape may hold (default 16; 1 = every request runs

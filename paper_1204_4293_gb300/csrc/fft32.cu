@@ -627,21 +627,22 @@ __global__ void __launch_bounds__(256, 2) k_rows_inv32_c2r(float *kap, long tota
 
 std::atomic<int> g_ks_real{-1};
 
-// Measured on GB300 (ms, complex / real-output inverse): the inverse alone,
-// 32 x 1024^2 0.320 / 0.298, 16 x 2048^2 0.840 / 0.755, 16 x 4096^2 4.20 /
-// 3.81, 64 x 512^2 0.171 / 0.163, 1 x 8192^2 1.454 / 1.426 (one-slot strips
-// by bulk copies since the slots are stored as 16-byte pairs; 2.03 with
-// per-thread loads); inside the batched KS + starlet chunks (two streams,
-// one pass per large scale) 32 x 1024^2 0.685 / 0.707, 16 x 2048^2 1.735 /
-// 1.770, 16 x 4096^2 8.45 / 8.25, 1 x 8192^2 2.544 / 2.497: at 1024^2 and
-// 2048^2 the split row pass and the column pass, whose second half of
-// threads idles through the inverse, overlap worse with the other stream's
-// kernels; on maps larger than L2 the saved bytes win.
+// Measured on GB300 (ms, complex / real-output inverse), KS + starlet in
+// the batched chunks (two streams, one pass per large scale, packed adds and
+// the fast reciprocal in the KS multiply): 32 x 1024^2 0.599 / 0.574,
+// 16 x 2048^2 1.494 / 1.466, 64 x 512^2 0.303 / 0.291, 16 x 4096^2 8.03 /
+// 7.53, 1 x 8192^2 2.47 / 2.41; the inverse alone 32 x 1024^2 0.296 / 0.266,
+// 16 x 4096^2 3.98 / 3.49.  (Before the fast reciprocal the real column
+// pass, with its per-element divisions, lost inside the 512^2-2048^2
+// pipelines: 32 x 1024^2 0.652 / 0.658.)  Below 512^2 the complex inverse
+// stays ahead: 128 x 256^2 J = 6 0.204 / 0.206, 256 x 128^2 J = 5 0.138 /
+// 0.145 (the inverse alone 0.046 / 0.054).
 bool ks_real_for(int n, bool batched)
 {
     const int mode = g_ks_real.load(std::memory_order_relaxed);
+    (void)batched;
     if (mode >= 0) return mode == 1 && n >= 64;
-    return batched ? n >= 4096 : n >= 64;
+    return n >= 512;
 }
 
 // ---------------------------------------------------------------------------
