@@ -47,8 +47,12 @@ static int check_J(int n, int J)
 
 size_t map_starlet_scratch_bytes(int n, int J, int batch, const fm_config &cfg)
 {
+    // the FFT work buffer (2 n^2 a map) and kappa (n^2); the starlet's
+    // scratch maps live in the work buffer when they fit there (the chunk
+    // plan's rule), else in their own buffer
     const size_t es = esize(cfg), nn = (size_t)n * n;
-    return (size_t)batch * nn * 3 * es + starlet_scratch_elems(n, J, batch, cfg) * es + 3 * 256;
+    const size_t st = starlet_scratch_elems(n, J, 1, cfg) <= 2 * nn ? 0 : starlet_scratch_elems(n, J, batch, cfg) * es;
+    return (size_t)batch * nn * 3 * es + st + 3 * 256;
 }
 
 }  // namespace fm

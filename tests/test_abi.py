@@ -108,6 +108,15 @@ def test_request_scratch_bytes_is_monotone(fm):
     assert 0 < small < big <= noisy
 
 
+def test_request_scratch_bytes_counts_work_buffer_and_kappa(fm):
+    # a single map's KS + starlet scratch: the complex FFT work buffer (2 n^2
+    # values), which also holds the starlet's two scratch maps, and kappa
+    # (n^2), each rounded to 256 bytes
+    for n, J, prec, es in ((1024, 7, fm.FM_F32, 4), (512, 6, fm.FM_F64, 8), (4096, 9, fm.FM_F32, 4)):
+        got = fm.Server.scratch_bytes(n, J, precision=prec)
+        assert 3 * n * n * es <= got <= 3 * n * n * es + 3 * 256, (n, got)
+
+
 def test_fuse_depth_rule(fm):
     """The automatic fused depth (host only): two scales for fp32 maps of
     512^2 to 2048^2, three otherwise; bounded by J - 1 and the tile's
@@ -195,3 +204,20 @@ def test_autotune_json_is_tolerant_of_layout(fm, tmp_path):
             fm.fm_autotune_load(missing)
     finally:
         fm.fm_autotune_clear()
+
+
+def test_ks_real_output_size_rule(fm):
+    """Host rule of the inverse KS form (no GPU needed): the real-output
+    (half spectrum) inverse from 512^2 up, in fm_ks_invert and in the
+    batched pipeline alike, the complex one below; FM_TUNE_KS_REAL forces
+    either (the real form exists from 64^2 up)."""
+    try:
+        for batched in (False, True):
+            assert [fm.fm_ks_real_output(n, batched) for n in (64, 128, 256, 512, 1024, 4096, 8192)] == \
+                [False, False, False, True, True, True, True]
+        fm.fm_tune(fm.FM_TUNE_KS_REAL, 1)
+        assert fm.fm_ks_real_output(64) and fm.fm_ks_real_output(256) and not fm.fm_ks_real_output(32)
+        fm.fm_tune(fm.FM_TUNE_KS_REAL, 0)
+        assert not any(fm.fm_ks_real_output(n) for n in (512, 1024, 8192))
+    finally:
+        fm.fm_tune(fm.FM_TUNE_KS_REAL, -1)
