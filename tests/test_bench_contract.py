@@ -85,3 +85,22 @@ def test_roofline_one_pass_scales_take_the_dominant_kernel():
     assert r["dominant_kernel"] == "starlet_col" and r["kernel"].startswith("starlet_large_scale")
     assert abs(r["achieved"] - 12 * px / 8 / ((0.48 / 32) * 1e-3) / 1e9) < 1e-6
     assert r["kernel_bytes_per_launch"] == 12 * px / 8
+
+
+def test_roofline_real_output_ks_kernel_bytes():
+    """With the real-output KS inverse (the default from 512^2 up) the three
+    KS passes move 16 + 12 + 8 = 36 B/px (the column pass writes, and the
+    row inverse reads, the half spectrum) against 44 for the complex
+    inverse; the method bytes credited to the group stay 12 B/px."""
+    sys.path.insert(0, ROOT)
+    import bench
+    kinds = ("fft_rows_fwd", "fft_cols_ks", "fft_rows_inv")
+    assert [bench.algo_bytes_per_px_launch(k, 2, ks_real=True) for k in kinds] == [16, 12, 8]
+    assert [bench.algo_bytes_per_px_launch(k, 2, ks_real=False) for k in kinds] == [16, 16, 12]
+    px = 32 * 1024 * 1024
+    per_kind = {"fft_rows_fwd": (0.175, 8), "fft_cols_ks": (0.183, 8), "fft_rows_inv": (0.102, 8),
+                "starlet_tile": (0.167, 8), "starlet_col": (0.436, 32)}
+    r = bench.step_roofline(per_kind, px, 7, 2, 0.572, 6776.6, "measured", ks_real=True)
+    ks = r["groups"]["ks"]
+    assert ks["method_bytes_per_px"] == 12 and ks["kernel_bytes_per_launch"] == 36 * px / 8
+    assert abs(r["step"]["frac"] - 44 * px / 0.572e-3 / 1e9 / 6776.6) < 1e-12
